@@ -1,0 +1,427 @@
+"""Pins the FP64 oracle to things other than itself: hand-derived closed forms,
+Gaussian integrals, a library multivariate-normal density, a separately
+written kernel density estimate, invariances, finite differences and
+torch.optim.Adam. CPU only."""
+
+import math
+import zlib
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+from scipy.stats import chi2, multivariate_normal, norm
+
+import oracle
+from golden_util import load_constants, load_examples
+
+
+def _fwd(f, q, **kw):
+    return oracle.radiance_fwd(f["mean"], f["quat"], f["logscale"], f["spectrum"],
+                               q["x"], q["n"], q["wo"], **kw)
+
+
+def _sigma_from_library(quat_wxyz, scale):
+    """Covariance R S S^T R^T with R from scipy (scalar-last quaternion)."""
+    w, x, y, z = quat_wxyz
+    R = Rotation.from_quat([x, y, z, w]).as_matrix()
+    return R @ np.diag(np.asarray(scale) ** 2) @ R.T
+
+
+def _rand_field(rng, n, c=3, spread=1.0, lmean=-2.0, lstd=0.4):
+    q = rng.standard_normal((4, n))
+    return {"mean": rng.uniform(0, spread, (3, n)), "quat": q,
+            "logscale": rng.normal(lmean, lstd, (3, n)), "spectrum": rng.uniform(0.1, 1.0, (c, n))}
+
+
+def _facing(m):
+    n = np.zeros((3, m)); n[2] = 1.0
+    return n, n.copy()
+
+
+# --------------------------------------------------------------------------- worked examples
+
+def test_worked_examples_closed_forms():
+    examples, _ = load_examples()
+    for name, ex in examples.items():
+        res = oracle.radiance_fwd(ex["mean"], ex["quat"], ex["logscale"], ex["spectrum"],
+                                  ex["x"], ex["n"], ex["wo"], albedo=ex["albedo"],
+                                  mode=ex["mode"], r_max=ex["r_max"],
+                                  cutoff_sigma=ex["cutoff_sigma"])
+        # inputs are rounded to float32, so the closed form holds to ~1e-6
+        np.testing.assert_allclose(res["out"], ex["expected"], rtol=2e-6, atol=1e-12,
+                                   err_msg=name)
+
+
+def test_worked_gradient_closed_forms():
+    examples, grads = load_examples()
+    for name, g in grads.items():
+        ex = examples[g["example"]]
+        res = oracle.radiance_bwd(ex["mean"], ex["quat"], ex["logscale"], ex["spectrum"],
+                                  ex["x"], ex["n"], ex["wo"], g["grad_out"], albedo=ex["albedo"],
+                                  mode=ex["mode"], r_max=ex["r_max"],
+                                  cutoff_sigma=ex["cutoff_sigma"])
+        for k, exp in g["expected"].items():
+            np.testing.assert_allclose(res[k], exp, rtol=5e-6, atol=1e-7, err_msg=f"{name}:{k}")
+
+
+def test_paper_constants_fixture():
+    c = load_constants()
+    assert c["query_radius_r"] == 0.02 and c["normalisation_eps"] == 1e-6
+    assert c["adam_lr"] == 5e-4 and c["k_min"] == 3
+
+
+# --------------------------------------------------------------------------- weight vs library density
+
+def test_single_gaussian_weight_is_scaled_normal_density():
+    """w(x) = (2 pi)^{3/2} sqrt(det Sigma) N(x; mu, Sigma) with Sigma built by scipy's
+    quaternion convention; catches a transposed R, a wrong quaternion order or a
+    scale used as a variance."""
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        q = rng.standard_normal(4)
+        s = np.exp(rng.normal(-2, 0.7, 3))
+        mu = rng.uniform(-1, 1, 3)
+        x = mu + rng.normal(0, 1.5 * s.max(), (5, 3))
+        f = {"mean": mu[:, None], "quat": q[:, None], "logscale": np.log(s)[:, None],
+             "spectrum": np.ones((1, 1))}
+        n, wo = _facing(5)
+        res = _fwd(f, {"x": x.T, "n": n, "wo": wo}, cutoff_sigma=math.inf)
+        Sig = _sigma_from_library(q / np.linalg.norm(q), s)
+        ref = (2 * np.pi) ** 1.5 * np.sqrt(np.linalg.det(Sig)) * \
+            multivariate_normal(mean=mu, cov=Sig).pdf(x)
+        np.testing.assert_allclose(res["out"][0], ref, rtol=1e-9, atol=1e-300)
+
+
+# --------------------------------------------------------------------------- integrals (P1, P2)
+
+def _grid3(center, half, k):
+    ax = [np.linspace(c - half, c + half, k) for c in center]
+    h = ax[0][1] - ax[0][0]
+    X, Y, Z = np.meshgrid(*ax, indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()]), h ** 3
+
+
+@pytest.mark.parametrize("cutoff,factor,rtol", [(math.inf, 1.0, 1e-8),
+                                               (3.0, chi2.cdf(9.0, 3), 3e-3)])
+def test_volume_integral_of_one_gaussian(cutoff, factor, rtol):
+    """Integral over R^3 of w = (2 pi)^{3/2} s1 s2 s3 (the unnormalised form of
+    the unit 3D integral the paper contrasts with surfaces, Sec. 2); truncated
+    to Q <= 9 it is scaled by P(chi^2_3 <= 9) = 0.970709."""
+    q = np.array([0.8, -0.3, 0.5, 0.2])
+    s = np.array([0.12, 0.07, 0.05])
+    mu = np.array([0.3, -0.2, 0.1])
+    half = (6.0 if math.isinf(cutoff) else 3.05) * s.max()
+    k = 121 if math.isinf(cutoff) else 161
+    X, dv = _grid3(mu, half, k)
+    f = {"mean": mu[:, None], "quat": q[:, None], "logscale": np.log(s)[:, None],
+         "spectrum": np.ones((1, 1))}
+    n, wo = _facing(X.shape[1])
+    res = _fwd(f, {"x": X, "n": n, "wo": wo}, cutoff_sigma=cutoff)
+    integral = res["out"][0].sum() * dv
+    exact = (2 * np.pi) ** 1.5 * np.prod(s) * factor
+    assert abs(integral / exact - 1.0) < rtol
+
+
+def test_plane_integral_depends_on_orientation():
+    """Over a plane through mu with unit normal n: integral of w dA =
+    2 pi s1 s2 s3 / sqrt(n^T Sigma n) (the surface integral of a 3D Gaussian
+    depends on the surface's pose, Sec. 2)."""
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        q = rng.standard_normal(4)
+        s = np.exp(rng.normal(-2.3, 0.5, 3))
+        mu = rng.uniform(-0.5, 0.5, 3)
+        nrm = rng.standard_normal(3); nrm /= np.linalg.norm(nrm)
+        t1 = np.cross(nrm, [1.0, 0.0, 0.0] if abs(nrm[0]) < 0.9 else [0.0, 1.0, 0.0])
+        t1 /= np.linalg.norm(t1)
+        t2 = np.cross(nrm, t1)
+        half, k = 7.0 * s.max(), 401
+        a = np.linspace(-half, half, k)
+        A, B = np.meshgrid(a, a, indexing="ij")
+        X = mu[:, None] + t1[:, None] * A.ravel() + t2[:, None] * B.ravel()
+        f = {"mean": mu[:, None], "quat": q[:, None], "logscale": np.log(s)[:, None],
+             "spectrum": np.ones((1, 1))}
+        n, wo = _facing(X.shape[1])
+        res = _fwd(f, {"x": X, "n": n, "wo": wo}, cutoff_sigma=math.inf)
+        integral = res["out"][0].sum() * (a[1] - a[0]) ** 2
+        Sig = _sigma_from_library(q / np.linalg.norm(q), s)
+        exact = 2 * np.pi * np.prod(s) / np.sqrt(nrm @ Sig @ nrm)
+        assert abs(integral / exact - 1.0) < 1e-7
+
+
+# --------------------------------------------------------------------------- isotropic collapse (P3)
+
+def _kde2d(points, weights, h, xq):
+    """Weighted 2D Gaussian-kernel density estimate with bandwidth h (a kernel
+    density estimate as in the photon-density background of Sec. 2.2, with a
+    smooth kernel in place of the disk): sum_i W_i N(x; p_i, h^2 I)."""
+    out = np.zeros(xq.shape[0])
+    for p, wgt in zip(points, weights):
+        out += wgt * norm.pdf(xq[:, 0], p[0], h) * norm.pdf(xq[:, 1], p[1], h)
+    return out
+
+
+def test_isotropic_field_on_a_plane_is_a_kde():
+    rng = np.random.default_rng(5)
+    n, m, h = 60, 80, 0.07
+    mu = np.zeros((3, n)); mu[:2] = rng.uniform(0, 1, (2, n))
+    spec = rng.uniform(0.1, 1.0, (3, n))
+    f = {"mean": mu, "quat": rng.standard_normal((4, n)),
+         "logscale": np.full((3, n), np.log(h)), "spectrum": spec}
+    x = np.zeros((3, m)); x[:2] = rng.uniform(0, 1, (2, m))
+    nn, wo = _facing(m)
+    res = _fwd(f, {"x": x, "n": nn, "wo": wo}, cutoff_sigma=math.inf)
+    for c in range(3):
+        ref = 2 * np.pi * h * h * _kde2d(mu[:2].T, spec[c], h, x[:2].T)
+        np.testing.assert_allclose(res["out"][c], ref, rtol=1e-10)
+
+
+# --------------------------------------------------------------------------- invariances (P4, P5, P7)
+
+def test_isotropic_gaussian_ignores_rotation():
+    rng = np.random.default_rng(8)
+    n, m = 40, 50
+    f = _rand_field(rng, n)
+    f["logscale"] = np.tile(rng.normal(-2.5, 0.3, n), (3, 1))
+    x = rng.uniform(0, 1, (3, m)); nn, wo = _facing(m)
+    a = _fwd(f, {"x": x, "n": nn, "wo": wo}, r_max=0.1, cutoff_sigma=3.0)
+    f2 = dict(f); f2["quat"] = rng.standard_normal((4, n))
+    b = _fwd(f2, {"x": x, "n": nn, "wo": wo}, r_max=0.1, cutoff_sigma=3.0)
+    np.testing.assert_allclose(a["out"], b["out"], rtol=1e-11, atol=1e-300)
+
+
+def test_normalized_single_contributor_returns_its_flux():
+    rng = np.random.default_rng(9)
+    f = _rand_field(rng, 1)
+    x = f["mean"] + rng.normal(0, 0.05, (3, 7)); nn, wo = _facing(7)
+    res = _fwd(f, {"x": x, "n": nn, "wo": wo}, mode=oracle.GPF_NORMALIZED,
+               cutoff_sigma=math.inf)
+    big = res["Z"] > 1e-6
+    assert big.sum() >= 3
+    np.testing.assert_allclose(res["out"][:, big], np.repeat(f["spectrum"], big.sum(), 1),
+                               rtol=1e-12)
+
+
+def test_normalized_constant_flux_returns_it():
+    rng = np.random.default_rng(10)
+    f = _rand_field(rng, 30, spread=0.3)
+    f["spectrum"] = np.tile(np.array([[0.3], [1.7], [2.2]]), (1, 30))
+    x = rng.uniform(0, 0.3, (3, 25)); nn, wo = _facing(25)
+    res = _fwd(f, {"x": x, "n": nn, "wo": wo}, mode=oracle.GPF_NORMALIZED,
+               cutoff_sigma=math.inf)
+    big = res["Z"] > 1e-6
+    np.testing.assert_allclose(res["out"][:, big],
+                               np.tile([[0.3], [1.7], [2.2]], (1, big.sum())), rtol=1e-12)
+
+
+def test_permutation_and_translation_invariance():
+    rng = np.random.default_rng(12)
+    n, m = 50, 40
+    f = _rand_field(rng, n)
+    x = rng.uniform(0, 1, (3, m)); nn, wo = _facing(m)
+    kw = dict(r_max=0.08, cutoff_sigma=3.0)
+    a = _fwd(f, {"x": x, "n": nn, "wo": wo}, **kw)
+    p = rng.permutation(n)
+    fp = {k: v[:, p] for k, v in f.items()}
+    b = _fwd(fp, {"x": x, "n": nn, "wo": wo}, **kw)
+    np.testing.assert_allclose(a["out"], b["out"], rtol=1e-12, atol=1e-300)
+    shift = np.array([[0.25], [-0.5], [1.0]])     # exactly representable shift
+    ft = dict(f); ft["mean"] = f["mean"] + shift
+    c = _fwd(ft, {"x": x + shift, "n": nn, "wo": wo}, **kw)
+    np.testing.assert_allclose(a["out"], c["out"], rtol=1e-9, atol=1e-300)
+
+
+def test_hemisphere_gate_and_valid_mask():
+    rng = np.random.default_rng(13)
+    f = _rand_field(rng, 20, spread=0.2)
+    m = 30
+    x = rng.uniform(0, 0.2, (3, m))
+    nn = rng.standard_normal((3, m)); wo = rng.standard_normal((3, m))
+    valid = (rng.uniform(0, 1, m) < 0.7).astype(np.uint8)
+    res = _fwd(f, {"x": x, "n": nn, "wo": wo}, valid=valid, cutoff_sigma=math.inf)
+    facing = np.sum(nn * wo, axis=0) > 0
+    on = facing & valid.astype(bool)
+    assert np.all(res["out"][:, ~on] == 0.0)
+    assert np.all(res["out"][:, on] > 0.0)
+
+
+# --------------------------------------------------------------------------- falloff psi
+
+def test_falloff_special_values():
+    r = 0.02
+    assert oracle.falloff_psi(np.array([0.0, r / 2, r]), r).tolist() == [1.0, 1.0, 1.0]
+    np.testing.assert_allclose(oracle.falloff_psi(np.array([2 * r]), r), [math.exp(-3.0)],
+                               rtol=1e-14)
+    np.testing.assert_allclose(oracle.falloff_psi(np.array([r * (1 + 1 / math.sqrt(3))]), r),
+                               [math.exp(-1.0)], rtol=1e-14)
+    d = np.linspace(0, 5 * r, 1001)
+    p = oracle.falloff_psi(d, r)
+    assert np.all(np.diff(p) <= 0.0)
+    assert abs(oracle.falloff_psi(np.array([r * (1 + 1e-9)]), r)[0] - 1.0) < 1e-15
+    assert np.all(oracle.falloff_psi(d, math.inf) == 1.0)
+
+
+def test_falloff_uses_euclidean_distance():
+    """Anisotropic Gaussian, point 2r away along the long local axis: the
+    falloff sees the Euclidean distance (t = 1, psi = e^-3) and the Gaussian
+    sees the Mahalanobis one."""
+    r = 0.02
+    q = np.array([math.cos(math.pi / 8), 0, 0, math.sin(math.pi / 8)])
+    s = np.array([0.5, 0.01, 0.01])
+    axis = np.array([math.cos(math.pi / 4), math.sin(math.pi / 4), 0.0])
+    x = (2 * r * axis)[:, None]
+    f = {"mean": np.zeros((3, 1)), "quat": q[:, None], "logscale": np.log(s)[:, None],
+         "spectrum": np.ones((1, 1))}
+    nn, wo = _facing(1)
+    res = _fwd(f, {"x": x, "n": nn, "wo": wo}, r_max=r, cutoff_sigma=math.inf)
+    exact = math.exp(-0.5 * (2 * r / 0.5) ** 2) * math.exp(-3.0)
+    np.testing.assert_allclose(res["out"][0, 0], exact, rtol=1e-12)
+
+
+# --------------------------------------------------------------------------- gradients (P8)
+
+def _objective(f, q, G, kw):
+    out = oracle.radiance_fwd(f["mean"], f["quat"], f["logscale"], f["spectrum"],
+                              q["x"], q["n"], q["wo"], albedo=q.get("albedo"), **kw)["out"]
+    return float(np.sum(G * out))
+
+
+def _fd(f, q, G, kw, key, h):
+    g = np.zeros_like(f[key])
+    for idx in np.ndindex(*f[key].shape):
+        fp = {k: v.copy() for k, v in f.items()}
+        fm = {k: v.copy() for k, v in f.items()}
+        fp[key][idx] += h
+        fm[key][idx] -= h
+        g[idx] = (_objective(fp, q, G, kw) - _objective(fm, q, G, kw)) / (2 * h)
+    return g
+
+
+FD_CASES = [
+    ("sum_plain", dict(mode=oracle.GPF_SUM, r_max=math.inf, cutoff_sigma=math.inf)),
+    ("sum_falloff", dict(mode=oracle.GPF_SUM, r_max=0.06, cutoff_sigma=math.inf)),
+    ("sum_cutoff", dict(mode=oracle.GPF_SUM, r_max=0.06, cutoff_sigma=3.0)),
+    ("norm_plain", dict(mode=oracle.GPF_NORMALIZED, r_max=math.inf, cutoff_sigma=math.inf)),
+    ("norm_falloff_cutoff", dict(mode=oracle.GPF_NORMALIZED, r_max=0.05, cutoff_sigma=3.0)),
+]
+
+
+@pytest.mark.parametrize("name,kw", FD_CASES, ids=[c[0] for c in FD_CASES])
+def test_analytic_gradient_matches_central_differences(name, kw):
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    n, m, c = 5, 36, 3
+    f = {"mean": rng.uniform(0, 0.25, (3, n)), "quat": rng.standard_normal((4, n)),
+         "logscale": rng.normal(-2.2, 0.3, (3, n)), "spectrum": rng.uniform(-0.5, 1.0, (c, n))}
+    x = rng.uniform(-0.05, 0.3, (3, m))
+    nn = rng.standard_normal((3, m)); wo = rng.standard_normal((3, m))
+    q = {"x": x, "n": nn, "wo": wo, "albedo": rng.uniform(0.3, 1.0, (c, m))}
+    G = rng.standard_normal((c, m))
+    fwd = oracle.radiance_fwd(f["mean"], f["quat"], f["logscale"], f["spectrum"], x, nn, wo,
+                              albedo=q["albedo"], band=1e-2, **kw)
+    if math.isfinite(kw["cutoff_sigma"]):
+        assert not fwd["near_cutoff"].any(), "FD point too close to the cutoff"
+    if kw["mode"] == oracle.GPF_NORMALIZED:
+        assert np.all(np.abs(fwd["Z"] - 1e-6) > 1e-8)
+    an = oracle.radiance_bwd(f["mean"], f["quat"], f["logscale"], f["spectrum"], x, nn, wo, G,
+                             albedo=q["albedo"], **kw)
+    for key, h in (("mean", 1e-6), ("quat", 1e-6), ("logscale", 1e-6), ("spectrum", 1e-6)):
+        num = _fd(f, q, G, kw, key, h)
+        err = np.linalg.norm(num - an[key]) / max(np.linalg.norm(an[key]), 1e-300)
+        assert err < 1e-6, (name, key, err)
+        assert np.linalg.norm(an[key]) > 0.0
+
+
+def test_gradient_of_the_worked_example_by_differences():
+    examples, grads = load_examples()
+    g = grads["axis_aligned_single_grad"]
+    ex = examples[g["example"]]
+    f = {k: ex[k].astype(np.float64) for k in ("mean", "quat", "logscale", "spectrum")}
+    q = {"x": ex["x"], "n": ex["n"], "wo": ex["wo"]}
+    kw = dict(mode=ex["mode"], r_max=ex["r_max"], cutoff_sigma=ex["cutoff_sigma"])
+    for key, exp in g["expected"].items():
+        num = _fd(f, q, g["grad_out"], kw, key, 1e-7)
+        np.testing.assert_allclose(num, exp, rtol=1e-5, atol=1e-7)
+
+
+# --------------------------------------------------------------------------- loss and Adam (P10)
+
+def test_mse_loss_and_gradient():
+    rng = np.random.default_rng(21)
+    O = rng.standard_normal((3, 40)); T = rng.standard_normal((3, 40))
+    valid = (rng.uniform(0, 1, 40) < 0.6).astype(np.uint8)
+    nv = valid.sum()
+    ref = sum(np.sum((O[:, i] - T[:, i]) ** 2) for i in range(40) if valid[i]) / nv
+    assert abs(oracle.mse_loss(O, T, valid) - ref) < 1e-12
+    g = oracle.mse_loss_grad(O, T, valid)
+    h = 1e-6
+    for idx in [(0, 0), (1, 5), (2, 17), (0, 33)]:
+        Op, Om = O.copy(), O.copy()
+        Op[idx] += h; Om[idx] -= h
+        num = (oracle.mse_loss(Op, T, valid) - oracle.mse_loss(Om, T, valid)) / (2 * h)
+        assert abs(num - g[idx]) < 1e-7
+    assert oracle.mse_loss(O, T, np.zeros(40, np.uint8)) == 0.0
+
+
+def test_adam_matches_torch_optim_adam():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(22)
+    p0 = rng.standard_normal(257)
+    tp = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=5e-4, betas=(0.9, 0.999), eps=1e-8)
+    p, m, v = p0.copy(), np.zeros(257), np.zeros(257)
+    for step in range(1, 201):
+        g = rng.standard_normal(257) * (1.0 + step % 7)
+        tp.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+        p, m, v = oracle.adam_step(p, g, m, v, step, lr=5e-4)
+    np.testing.assert_allclose(p, tp.detach().numpy(), rtol=0, atol=1e-12)
+
+
+# --------------------------------------------------------------------------- planted mistakes
+
+def _expect_failure(fn, *args):
+    try:
+        fn(*args)
+    except AssertionError:
+        return
+    raise AssertionError(f"{fn.__name__} did not notice the planted mistake")
+
+
+def test_pins_catch_a_transposed_rotation(monkeypatch):
+    import oracle.gpf_oracle as go
+    good = go.quat_to_rotmat
+    monkeypatch.setattr(go, "quat_to_rotmat", lambda q: np.swapaxes(good(q), -1, -2))
+    _expect_failure(test_single_gaussian_weight_is_scaled_normal_density)
+    _expect_failure(test_worked_examples_closed_forms)
+    _expect_failure(test_plane_integral_depends_on_orientation)
+
+
+def test_pins_catch_falloff_on_the_wrong_distance(monkeypatch):
+    import oracle.gpf_oracle as go
+    good = go.falloff_psi
+    monkeypatch.setattr(go, "falloff_psi", lambda d, r: good(d * d / max(r, 1e-6), r))
+    _expect_failure(test_falloff_uses_euclidean_distance)
+    _expect_failure(test_worked_examples_closed_forms)
+
+
+def test_pins_catch_a_wrong_gradient_term(monkeypatch):
+    import oracle.gpf_oracle as go
+    good = go._falloff_dpsi_ddist
+    monkeypatch.setattr(go, "_falloff_dpsi_ddist", lambda d, r: -good(d, r))
+    _expect_failure(test_analytic_gradient_matches_central_differences, *FD_CASES[1])
+    monkeypatch.setattr(go, "_falloff_dpsi_ddist", good)
+    goodp = go._rotmat_partials
+    def swapped(qh):
+        P = goodp(qh)
+        return P[:, [0, 2, 1, 3]]
+    monkeypatch.setattr(go, "_rotmat_partials", swapped)
+    _expect_failure(test_analytic_gradient_matches_central_differences, *FD_CASES[0])
+    _expect_failure(test_worked_gradient_closed_forms)
+
+
+def test_pins_catch_a_wrong_cutoff(monkeypatch):
+    import oracle.gpf_oracle as go
+    good = go._pairs
+    monkeypatch.setattr(go, "_pairs", lambda P, xs, r, c: good(P, xs, r, c * c if math.isfinite(c) else c))
+    _expect_failure(test_volume_integral_of_one_gaussian, 3.0, chi2.cdf(9.0, 3), 3e-3)
+    _expect_failure(test_worked_examples_closed_forms)
