@@ -1,0 +1,418 @@
+"""Benchmark of the Gaussian Photon Field hit-point radiance path on GB300.
+
+One step = the whole hot path over one batch of hit points:
+    gpf_build_index -> gpf_radiance_fwd -> gpf_mse_loss_grad
+    -> gpf_radiance_bwd -> gpf_adam_step
+on the paper-scale synthetic workload: 1,000,000 Gaussians from a caustic-like
+photon map on an analytic floor + sphere scene, one 1024 x 1024 pinhole view
+(hit points by analytic ray intersection), 3-sigma truncation, falloff radius
+r = 0.02, MSE against a target rendered from a perturbed copy of the field,
+Adam with lr 5e-4.
+
+Prints one JSON line. --impl reference times the FP64 CPU oracle instead.
+Multi-GPU (torchrun): every rank renders its own view of the same field and
+the gradients are summed over ranks before the Adam step.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_PHOTONS = 1_000_000
+VIEW = 1024
+R_MAX = 0.02
+CUTOFF = 3.0
+CELL = 0.02          # edge of the hit-point grid cells the planner aims for
+LR = 5e-4
+EYE0 = (0.0, -6.0, 4.0)
+LOOK_AT = (0.0, 0.0, 0.5)
+L2_BYTES = 129 * 1024 * 1024
+METRIC = "hit-point radiance queries/sec (fwd, fwd+bwd) at 1M Gaussians; % of HBM/SFU roofline"
+WORKLOAD = "caustic floor+sphere scene, 1,000,000 Gaussians, 1024x1024 view, 3-sigma grid, r=0.02"
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def view_eye(rank: int):
+    """Rank 0 uses the reference camera; other ranks orbit it in azimuth."""
+    if rank == 0:
+        return EYE0
+    a = -math.pi / 2 + rank * (2 * math.pi / 8)
+    return (6.0 * math.cos(a), 6.0 * math.sin(a), 4.0)
+
+
+def make_inputs(rank: int):
+    import synth
+    pos, flux = synth.caustic_photons(N_PHOTONS, seed=0)
+    fnp = synth.field_from_photons(pos, flux, seed=0)
+    tgt = synth.perturbed_copy(fnp, seed=1)
+    qnp = synth.pinhole_hitpoints(view_eye(rank), LOOK_AT, VIEW, VIEW)
+    return fnp, tgt, qnp
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz_max: float, sms: int = 152) -> float:
+    """FP32 lane peak: SMs x 128 FP32 lanes x 2 flops (FMA) x max SM clock."""
+    return sms * 128 * 2 * sm_mhz_max * 1e6 / 1e12
+
+
+def cpu_baseline(fnp, tgt_out_fn, qnp, budget_s: float = 15.0):
+    """The FP64 oracle (as it stands) on a bounded sample of the same workload:
+    forward + backward of single hit points over all Gaussians, repeated until
+    the time budget is spent. Returns queries/s and the sample description."""
+    import oracle
+    rng = np.random.default_rng(123)
+    act = np.flatnonzero(qnp.valid.astype(bool))
+    done, t0 = 0, time.perf_counter()
+    chunk = 4
+    while time.perf_counter() - t0 < budget_s:
+        sel = rng.choice(act, size=chunk, replace=False)
+        x, n, wo = qnp.x[:, sel], qnp.n[:, sel], qnp.wo[:, sel]
+        fo = oracle.radiance_fwd(fnp.mean, fnp.quat, fnp.logscale, fnp.spectrum, x, n, wo, None,
+                                 qnp.valid[sel], r_max=R_MAX, cutoff_sigma=CUTOFF)
+        target = tgt_out_fn(sel)
+        g = oracle.mse_loss_grad(fo["out"], target, qnp.valid[sel])
+        oracle.radiance_bwd(fnp.mean, fnp.quat, fnp.logscale, fnp.spectrum, x, n, wo, g, None,
+                            qnp.valid[sel], r_max=R_MAX, cutoff_sigma=CUTOFF)
+        done += chunk
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle timed on the host cores."""
+    if rank != 0:
+        return
+    fnp, tgt, qnp = make_inputs(0)
+    tgt_fn = lambda sel: np.zeros((3, len(sel)))  # noqa: E731  (target values do not change the work)
+    steps = []
+    for _ in range(args.warmup):
+        cpu_baseline(fnp, tgt_fn, qnp, budget_s=2.0)
+    for _ in range(args.steps):
+        rate, done, dt = cpu_baseline(fnp, tgt_fn, qnp, budget_s=args.ref_budget)
+        steps.append((rate, done, dt))
+    rate = sum(s[1] for s in steps) / sum(s[2] for s in steps)
+    n_active = int(qnp.valid.sum())
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "queries/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * n_active / rate, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": n_active, "seq_len": None,
+                   "parallelism": "cpu", "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": rate, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sum(s[1] for s in steps)} random valid hit points, fwd+bwd "
+                                   "each over all 1,000,000 Gaussians (numpy float64, one thread); "
+                                   "ms_per_step extrapolates to the full view"},
+        "e2e": {"value": rate, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    global N_PHOTONS, VIEW, WORKLOAD
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpf", choices=["gpf", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--photons", type=int, default=N_PHOTONS,
+                    help="Gaussians (smaller cases are for profiling only)")
+    ap.add_argument("--view", type=int, default=VIEW, help="view side in pixels")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if (args.photons, args.view) != (N_PHOTONS, VIEW):
+        N_PHOTONS, VIEW = args.photons, args.view
+        WORKLOAD = (f"caustic floor+sphere scene, {N_PHOTONS:,} Gaussians, {VIEW}x{VIEW} view, "
+                    "3-sigma grid, r=0.02 (reduced profiling case)")
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    import paper_2512_12459_gb300 as gpf
+    from paper_2512_12459_gb300.setup_index import make_index
+
+    fnp, tgt_np, qnp = make_inputs(rank)
+    field = gpf.Field.from_numpy(fnp)
+    queries = gpf.Queries.from_numpy(qnp)
+    tgt_field = gpf.Field.from_numpy(tgt_np)
+    n_active = int(qnp.valid.sum())
+
+    # target radiance: the perturbed field rendered through the same path (outside timing)
+    tidx = make_index(tgt_field, queries, query_cell=CELL, cutoff_sigma=CUTOFF)
+    tidx.build(tgt_field, queries)
+    target, _ = gpf.gpf_radiance_fwd(tidx, tgt_field, queries, gpf.GPF_SUM, r_max=R_MAX)
+    target = target.clone()
+    del tidx
+
+    # headroom for the pairs to grow as Adam moves the Gaussians
+    idx = make_index(field, queries, query_cell=CELL, cutoff_sigma=CUTOFF, headroom=1.25)
+    state = gpf.AdamState.zeros_like(field)
+    grads = gpf.Field(*(torch.empty_like(t) for t in field.tensors()))
+    out = torch.empty((3, queries.m), device="cuda")
+    z = torch.empty((queries.m,), device="cuda")
+    gout = torch.empty_like(out)
+    loss = torch.empty((1,), device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    ev = {k: [] for k in ("step", "build", "fwd", "loss", "bwd", "adam")}
+
+    def step(timed: bool):
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(6)] if timed else None
+        if timed:
+            marks[0].record(stream)
+        idx.build(field, queries)
+        if timed:
+            marks[1].record(stream)
+        gpf.gpf_radiance_fwd(idx, field, queries, gpf.GPF_SUM, r_max=R_MAX, out=out, z=z)
+        if timed:
+            marks[2].record(stream)
+        gpf.gpf_mse_loss_grad(out, target, queries.valid, loss=loss, grad=gout)
+        if timed:
+            marks[3].record(stream)
+        gpf.gpf_radiance_bwd(idx, field, queries, gout, out, z, gpf.GPF_SUM, r_max=R_MAX,
+                             grads=grads)
+        if world > 1:
+            for t in grads.tensors():
+                dist.all_reduce(t)
+        if timed:
+            marks[4].record(stream)
+        gpf.gpf_adam_step(field, grads, state, lr=LR)
+        if timed:
+            marks[5].record(stream)
+        return marks
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    st = idx.stats()
+    if st["overflow"]:
+        raise RuntimeError(f"pair buffer overflow in warm-up: {st}")
+    launches0 = gpf.gpf_launch_count()
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    all_marks = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)          # evict L2 between timed steps (not timed)
+        all_marks.append(step(True))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = gpf.gpf_launch_count() - launches0
+
+    per = {k: [] for k in ("build", "fwd", "loss", "bwd", "adam", "step")}
+    for mk in all_marks:
+        names = ("build", "fwd", "loss", "bwd", "adam")
+        for i, nm in enumerate(names):
+            per[nm].append(mk[i].elapsed_time(mk[i + 1]))
+        per["step"].append(mk[0].elapsed_time(mk[5]))
+    ms = {k: float(np.mean(v)) for k, v in per.items()}
+    step_ms = ms["step"]
+    if world > 1:
+        t = torch.tensor([step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+        nact = torch.tensor([n_active], device="cuda", dtype=torch.float64)
+        dist.all_reduce(nact)
+        total_q = float(nact.item())
+    else:
+        total_q = float(n_active)
+    value = total_q / (step_ms / 1000.0)
+
+    # pair counts for the roofline (outside timing)
+    pairs = gpf.gpf_count_pairs(idx, field, queries)
+
+    # end to end through the public API with host buffers: H2D of this step's
+    # hit points and targets from pinned memory, the step, D2H of the loss
+    host = {k: torch.as_tensor(v).pin_memory() for k, v in
+            (("x", qnp.x), ("n", qnp.n), ("wo", qnp.wo), ("valid", qnp.valid))}
+    host["target"] = target.cpu().pin_memory()
+    loss_host = torch.empty((1,), dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = loss_host.numel() * 4
+    e2e_times = []
+    for i in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        queries.x.copy_(host["x"], non_blocking=True)
+        queries.normal.copy_(host["n"], non_blocking=True)
+        queries.wo.copy_(host["wo"], non_blocking=True)
+        queries.valid.copy_(host["valid"], non_blocking=True)
+        target.copy_(host["target"], non_blocking=True)
+        step(False)
+        loss_host.copy_(loss, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = float(np.mean(e2e_times))
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    peaks, peaks_src = measured_peaks()
+    smax = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = fp32_peak_tflops(smax)
+    C = fnp.channels
+    roof = None
+    extra = {}
+    if pairs is not None:
+        inc = pairs["included"]
+        fwd_flops = inc * (25 + 2 * C)       # per included pair, FMA = 2 flops
+        bwd_flops = inc * (55 + 4 * C)
+        fwd_ach = fwd_flops / (ms["fwd"] / 1e3) / 1e12
+        bwd_ach = bwd_flops / (ms["bwd"] / 1e3) / 1e12
+        dom = "bwd" if ms["bwd"] >= ms["fwd"] else "fwd"
+        ach = bwd_ach if dom == "bwd" else fwd_ach
+        roof = {"bound": "alu", "kernel": "radiance_" + dom, "achieved": ach, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {smax:.0f} MHz ({peaks_src} max clock)"}
+        extra = {"included_pairs": inc, "candidate_pairs": pairs["candidates"],
+                 "fwd_alu_frac": fwd_ach / fp32_peak, "bwd_alu_frac": bwd_ach / fp32_peak}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        tgt_out = target.cpu().numpy().astype(np.float64)
+        rate, done, dt = cpu_baseline(fnp, lambda sel: tgt_out[:, sel], qnp,
+                                      budget_s=args.cpu_budget)
+        cpu = {"value": rate, "unit": "queries/s", "cores": 1, "kind": "oracle",
+               "sample": f"{done} random valid hit points of the same view, fwd+bwd each over all "
+                         f"1,000,000 Gaussians, {dt:.1f} s (numpy float64, one thread)"}
+        del oracle
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": int(total_q), "seq_len": None,
+                       "parallelism": f"dp{world}", "hit_points_per_gpu": n_active,
+                       "gaussians": fnp.n, "query_cell": CELL, "levels": idx.grid.levels, "finest_cell": idx.grid.cell_size, "l2": "flushed between steps"},
+            "fwd_queries_per_s": n_active / (ms["fwd"] / 1e3),
+            "fwd_bwd_queries_per_s": n_active / ((ms["fwd"] + ms["bwd"] + ms["loss"]) / 1e3),
+            "ms_breakdown": {k: v for k, v in ms.items() if k != "step"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": total_q / (e2e_ms / 1e3), "unit": "queries/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "index": {"n_pairs": st["n_pairs"], "max_pairs": idx.grid.max_pairs},
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,326 @@
+/*
+ * gpf.h - C ABI of the Gaussian Photon Field hit-point radiance library
+ * (libgpf.so, CUDA, sm_103a).
+ *
+ * The library evaluates the radiance a Gaussian Photon Field (arxiv
+ * 2512.12459) returns at camera-ray hit points, its gradient with respect to
+ * every Gaussian parameter, the MSE loss that supervises it and the Adam step
+ * that optimises it:
+ *
+ *   Gaussian i: mean mu_i, rotation q_i (quaternion (w,x,y,z), normalised by
+ *   the library), log-scale l_i (scale s_i = exp(l_i)), spectral flux Phi_i
+ *   (C channels). Sec. 3.1: Sigma_i = R S S^T R^T, contribution
+ *   Phi_i exp(-1/2 d^T Sigma_i^-1 d).
+ *
+ *   Hit point x with normal n, direction to the viewer w_o, albedo rho:
+ *     u_i = S_i^-1 R_i^T (x - mu_i),  Q_i = u_i . u_i
+ *     psi = 1 if |x - mu_i| <= r else exp(-3 t^2), t = (|x - mu_i| - r)/max(r, 1e-6)
+ *     w_i = exp(-Q_i / 2) psi                 (Sec. 3.2, aggregation)
+ *     L = sum_{i : Q_i <= k^2} w_i Phi_i,  Z = sum_{i : Q_i <= k^2} w_i
+ *     O = rho * L * [n.w_o > 0]                  (GPF_SUM)
+ *     O = rho * L / max(Z, eps) * [n.w_o > 0]    (GPF_NORMALIZED; the soft
+ *                                                  normalisation of the
+ *                                                  supplementary query listing)
+ *   k is the truncation in standard deviations (3: the 3-sigma ellipsoid; an
+ *   infinite k sums every Gaussian).
+ *
+ * Conventions for every call:
+ *   - Arrays are float32 structure-of-arrays, row-major [rows, count], one row
+ *     per component (mean [3,N] = all x, then all y, then all z).
+ *   - Every array pointer is a DEVICE pointer owned by the caller, contiguous
+ *     and 4-byte aligned. The library never allocates device memory: scratch
+ *     comes from a caller-provided workspace (256-byte aligned) whose size the
+ *     library reports.
+ *   - Every call that takes a stream enqueues its work on that stream and
+ *     returns without synchronising (gpf_index_stats excepted). A NULL stream
+ *     is the legacy default stream.
+ *   - Every call returns a gpf_status. Arguments are validated on the host
+ *     before anything is enqueued; on an error nothing is enqueued and
+ *     gpf_last_error() describes it. No call aborts or throws.
+ *   - Problems found on the device (a full pair buffer) set a flag in the
+ *     index workspace. Kernels that see it leave their outputs untouched;
+ *     gpf_index_stats() reads it back and reports GPF_ERR_CAPACITY.
+ */
+#ifndef GPF_H
+#define GPF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (cudaStream_t); NULL is the legacy default stream. */
+typedef struct CUstream_st *gpf_stream;
+
+typedef enum gpf_status {
+  GPF_OK = 0,
+  GPF_ERR_INVALID_ARG = 1,        /* bad pointer, size, alignment or mode      */
+  GPF_ERR_CUDA = 2,               /* a CUDA runtime call or launch failed      */
+  GPF_ERR_WORKSPACE_TOO_SMALL = 3,/* workspace smaller than the reported size  */
+  GPF_ERR_CAPACITY = 4,           /* the (cell, Gaussian) pair buffer was full */
+  GPF_ERR_NOT_BUILT = 5,          /* index used before gpf_build_index         */
+  GPF_ERR_MISMATCH = 6            /* field/queries differ from those indexed   */
+} gpf_status;
+
+typedef enum gpf_mode { GPF_SUM = 0, GPF_NORMALIZED = 1 } gpf_mode;
+
+/* Maximum number of spectral channels C. */
+#define GPF_MAX_CHANNELS 8
+/* Maximum cells per axis of the hit-point grid. */
+#define GPF_MAX_DIM 1024
+/* Maximum number of grid levels. */
+#define GPF_MAX_LEVELS 16
+
+/* The Gaussian Photon Field (Sec. 3.1). All arrays [rows, n], float32. */
+typedef struct gpf_field {
+  int64_t n;             /* number of Gaussians N >= 0                       */
+  int32_t channels;      /* C, 1..GPF_MAX_CHANNELS                           */
+  int32_t reserved;      /* must be 0                                        */
+  const float *mean;     /* [3,N] mu                                         */
+  const float *quat;     /* [4,N] (w,x,y,z), any non-zero norm               */
+  const float *logscale; /* [3,N] l, scale s = exp(l)                        */
+  const float *spectrum; /* [C,N] Phi                                        */
+} gpf_field;
+
+/* Camera-ray hit points (first diffuse hits, Sec. 3.2). */
+typedef struct gpf_queries {
+  int64_t m;             /* number of hit points M >= 0                      */
+  const float *x;        /* [3,M] positions                                  */
+  const float *normal;   /* [3,M] surface normals                            */
+  const float *wo;       /* [3,M] directions towards the viewer              */
+  const float *albedo;   /* [C,M] BSDF albedo rho, or NULL for rho = 1       */
+  const uint8_t *valid;  /* [M] non-zero = supervised/valid, or NULL = all   */
+} gpf_queries;
+
+/* Query parameters. */
+typedef struct gpf_query_params {
+  int32_t mode;          /* gpf_mode                                         */
+  float r_max;           /* falloff radius r (paper: 0.02); +INF disables psi */
+  float eps;             /* normalisation floor (paper: 1e-6)                */
+  int32_t reserved;      /* must be 0                                        */
+} gpf_query_params;
+
+/* Multi-level uniform grid and capacities of an index.
+ * Level L (0 <= L < levels) has cubic cells of edge cell_size * 2^L, all
+ * levels sharing the origin. A Gaussian is listed on the finest level on which
+ * its k-sigma bounds span at most max_span cells per axis, in the cells of
+ * that box which hold hit points. Hit points are sorted by their cell on
+ * query_level, a dims[0] x dims[1] x dims[2] grid. Points outside the grid
+ * are clamped into its border cells, which keeps the result exact (only
+ * slower). */
+typedef struct gpf_grid_config {
+  float origin[3];       /* lower corner shared by all levels                */
+  float cell_size;       /* c0: cell edge on the finest level, > 0           */
+  int32_t levels;        /* 1..GPF_MAX_LEVELS                                */
+  int32_t max_span;      /* S, 1..64                                         */
+  int32_t query_level;   /* K, 0..15; dims[k] * 2^K <= 2^20                  */
+  int32_t dims[3];       /* hit-point grid cells per axis, 1..GPF_MAX_DIM    */
+  int32_t hash_bits;     /* 2^hash_bits buckets hold the Gaussian lists, 8..28 */
+  int32_t channels;      /* C of the fields this index will hold             */
+  float cutoff_sigma;    /* truncation k: Q <= k^2 (3 = 3 sigma); +INF = no
+                            truncation (every Gaussian, no cell lists)       */
+  int32_t brute_force;   /* 1: no cell lists; every Gaussian is tested with
+                            Q <= k^2 (used to check the culled path)         */
+  int64_t max_gaussians; /* capacity N_max                                   */
+  int64_t max_queries;   /* capacity M_max                                   */
+  int64_t max_pairs;     /* capacity of (cell, Gaussian) entries             */
+} gpf_grid_config;
+
+/* Opaque host-side handle. It holds sizes and pointers into the workspace;
+ * the device data live in the caller's workspace. */
+typedef struct gpf_index gpf_index;
+
+/* Counters read back by gpf_index_stats. */
+typedef struct gpf_index_stats_t {
+  int64_t n_pairs;       /* (cell, Gaussian) entries the last build needed   */
+  int64_t n_active;      /* hit points that are valid and face the viewer    */
+  int64_t n_occupied;    /* reserved (0)                                     */
+  int32_t overflow;      /* 1 if n_pairs exceeded max_pairs                  */
+  int32_t reserved;
+} gpf_index_stats_t;
+
+/* Gradients, each [rows, N] float32, device pointers owned by the caller. */
+typedef struct gpf_field_grad {
+  float *mean;           /* [3,N] d/d mu                                     */
+  float *quat;           /* [4,N] d/d q (raw, through the normalisation)     */
+  float *logscale;       /* [3,N] d/d l                                      */
+  float *spectrum;       /* [C,N] d/d Phi                                    */
+  int32_t accumulate;    /* 0: overwrite, 1: add to the existing values      */
+  int32_t reserved;
+} gpf_field_grad;
+
+/* Adam hyper-parameters (Sec. S1.2: Adam, learning rate 5e-4). */
+typedef struct gpf_adam_hparams {
+  float lr[4];           /* learning rate per group: mean, quat, logscale,
+                            spectrum                                         */
+  float beta1, beta2, eps;
+  int32_t step;          /* 1-based index of the update being applied        */
+} gpf_adam_hparams;
+
+/* ------------------------------------------------------------------------ */
+
+/* Version string of the library. */
+const char *gpf_version(void);
+
+/* Short name of a status code. Never NULL. */
+const char *gpf_status_string(gpf_status s);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *gpf_last_error(void);
+
+/*
+ * gpf_index_create - validate a grid configuration and make a handle.
+ *   cfg  host pointer, read during the call only.
+ *   out  receives the handle; release it with gpf_index_destroy.
+ * Errors: GPF_ERR_INVALID_ARG (NULL pointer, cell_size <= 0 or not finite,
+ * dims outside 1..GPF_MAX_DIM or more than 2^28 cells, channels outside
+ * 1..GPF_MAX_CHANNELS, cutoff_sigma <= 0, brute_force not 0/1, negative
+ * capacities).
+ * Allocates host memory only.
+ */
+gpf_status gpf_index_create(const gpf_grid_config *cfg, gpf_index **out);
+
+/* Release a handle (NULL is ignored). The workspace stays the caller's. */
+void gpf_index_destroy(gpf_index *index);
+
+/*
+ * gpf_index_workspace_size - device bytes gpf_build_index needs.
+ *   bytes receives the size for the handle's capacities.
+ */
+gpf_status gpf_index_workspace_size(const gpf_index *index, size_t *bytes);
+
+/*
+ * gpf_build_index - the spatial index of one (field, hit point set) pair.
+ *
+ * Preprocesses every Gaussian (normalised rotation, M = S^-1 R^T, the
+ * axis-aligned bounds of its k-sigma ellipsoid: half-extent
+ * k sqrt(sum_j R_kj^2 s_j^2) per axis), sorts the hit points by grid cell,
+ * then emits one (cell, Gaussian) entry for every cell that the Gaussian's
+ * bounds overlap and that holds at least one active hit point, and
+ * radix-sorts the entries by cell into per-cell Gaussian lists. It replaces
+ * the paper's periodically rebuilt KD-tree over the centres (Sec. S1.2) and
+ * bounds the neighbourhood by the k-sigma ellipsoid (Sec. 3.2, Neighborhood
+ * Search, read as {i : Q_i <= k^2}).
+ *
+ *   index      handle from gpf_index_create.
+ *   field      N <= max_gaussians, C = the handle's channels.
+ *   queries    M <= max_queries; the set later passed to fwd/bwd.
+ *   workspace  device buffer of at least gpf_index_workspace_size bytes,
+ *              256-byte aligned, owned by the caller, kept alive and
+ *              unmodified until the last fwd/bwd that uses this build.
+ * With cutoff_sigma = +INF or brute_force = 1 no cell lists are built and
+ * fwd/bwd test every Gaussian against every hit point.
+ * The index records the field and query pointers and sizes; fwd/bwd given
+ * others return GPF_ERR_MISMATCH. A pair count above max_pairs sets the
+ * overflow flag (see gpf_index_stats).
+ * Errors: GPF_ERR_INVALID_ARG, GPF_ERR_WORKSPACE_TOO_SMALL, GPF_ERR_CUDA.
+ */
+gpf_status gpf_build_index(gpf_index *index, const gpf_field *field,
+                           const gpf_queries *queries, void *workspace,
+                           size_t workspace_bytes, gpf_stream stream);
+
+/*
+ * gpf_index_stats - synchronise the stream and read the device counters of
+ * the last build. Returns GPF_ERR_CAPACITY if the pair buffer overflowed.
+ */
+gpf_status gpf_index_stats(const gpf_index *index, gpf_index_stats_t *stats,
+                           gpf_stream stream);
+
+/*
+ * gpf_radiance_fwd - radiance O at every hit point (Sec. 3.2, aggregation
+ * equation; the soft falloff and normalisation of the supplementary query
+ * listing; the BSDF modulation read as albedo times a hemisphere gate).
+ *
+ *   index, field, queries  as given to the last gpf_build_index.
+ *   params  host pointer: mode, r_max (+INF: psi = 1), eps.
+ *   out     [C,M] float32 device, written for every hit point (0 where the
+ *           point is invalid or n.w_o <= 0).
+ *   z_out   [M] float32 device or NULL: Z = sum_i w_i for active points, 0
+ *           elsewhere. Keep it for gpf_radiance_bwd in GPF_NORMALIZED mode.
+ * Sums run in float32 in a fixed order: results are bitwise reproducible
+ * for a given build.
+ * Errors: GPF_ERR_INVALID_ARG, GPF_ERR_NOT_BUILT, GPF_ERR_MISMATCH, GPF_ERR_CUDA.
+ */
+gpf_status gpf_radiance_fwd(const gpf_index *index, const gpf_field *field,
+                            const gpf_queries *queries,
+                            const gpf_query_params *params, float *out,
+                            float *z_out, gpf_stream stream);
+
+/*
+ * gpf_count_pairs - the work of gpf_radiance_fwd for the last build, without
+ * computing radiance: counts[0] = (hit point, candidate Gaussian) pairs the
+ * pair loop evaluates after culling, counts[1] = pairs with Q <= k^2 (the
+ * neighbourhood of Sec. 3.2 read as the k-sigma ellipsoid; the algorithmic
+ * work of the query).
+ *   counts  device array of 2 uint64, 8-byte aligned, overwritten.
+ * Errors: as gpf_radiance_fwd.
+ */
+gpf_status gpf_count_pairs(const gpf_index *index, const gpf_field *field,
+                           const gpf_queries *queries, uint64_t *counts,
+                           gpf_stream stream);
+
+/*
+ * gpf_launch_count - number of CUDA kernels this library has launched in the
+ * process so far (host-side counter; memsets and copies are not counted).
+ */
+uint64_t gpf_launch_count(void);
+
+/*
+ * gpf_radiance_bwd - gradient of sum_{c,m} grad_out[c,m] O[c,m] with respect
+ * to mu, q (raw), l and Phi (Sec. 3.2, Differentiable Accumulation). The
+ * exponentials are recomputed, not stored. Contributions are reduced per
+ * Gaussian inside one warp (no global atomics), so results are bitwise
+ * reproducible.
+ *
+ *   grad_out  [C,M] device, upstream gradient d loss / d O.
+ *   out, z    [C,M] and [M] device: the outputs of the matching forward
+ *             (read only in GPF_NORMALIZED mode; may be NULL in GPF_SUM).
+ *   grads     host struct of device pointers [3,N], [4,N], [3,N], [C,N];
+ *             accumulate = 0 overwrites, 1 adds.
+ * Errors: as gpf_radiance_fwd.
+ */
+gpf_status gpf_radiance_bwd(const gpf_index *index, const gpf_field *field,
+                            const gpf_queries *queries,
+                            const gpf_query_params *params,
+                            const float *grad_out, const float *out,
+                            const float *z, const gpf_field_grad *grads,
+                            gpf_stream stream);
+
+/*
+ * gpf_mse_loss_grad - the MSE loss of Sec. 3.3 and its gradient:
+ *   loss = (1/|V|) sum_{m valid} sum_c (out[c,m] - target[c,m])^2
+ *   grad[c,m] = 2 (out - target) / |V| on valid points, 0 elsewhere.
+ *   out, target  [C,M] float32 device; valid [M] uint8 device or NULL.
+ *   loss         float32 device scalar (written); grad [C,M] device.
+ *   workspace    device scratch of gpf_mse_workspace_size(m) bytes.
+ * The reduction order is fixed (bitwise reproducible). |V| = 0 gives 0.
+ */
+gpf_status gpf_mse_workspace_size(int64_t m, size_t *bytes);
+gpf_status gpf_mse_loss_grad(int64_t m, int32_t channels, const float *out,
+                             const float *target, const uint8_t *valid,
+                             float *loss, float *grad, void *workspace,
+                             size_t workspace_bytes, gpf_stream stream);
+
+/*
+ * gpf_adam_step - one bias-corrected Adam update (Sec. S1.2) of the four
+ * parameter tensors in place:
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2
+ *   p -= lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps)
+ *   params  the field's arrays, written in place (the const pointers of
+ *           gpf_field are cast away: pass writable buffers).
+ *   grads   gradients from gpf_radiance_bwd.
+ *   m, v    first and second moments, same layout as params (a gpf_field_grad
+ *           each; zero them before step 1).
+ *   hp      host struct; hp->step >= 1.
+ */
+gpf_status gpf_adam_step(const gpf_field *params, const gpf_field_grad *grads,
+                         const gpf_field_grad *m, const gpf_field_grad *v,
+                         const gpf_adam_hparams *hp, gpf_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPF_H */

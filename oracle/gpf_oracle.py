@@ -152,7 +152,8 @@ def radiance_fwd(mean, quat, logscale, spectrum, x, n, wo, albedo=None, valid=No
     (sum_i w_i), n_pairs [M] (included pairs), denom [C,M] (rho * sum_i w_i
     |Phi_i|, the scale of the relative error), near_cutoff [M] (True when some
     pair has |Q - cutoff^2| < band, where float32 and float64 may classify the
-    pair differently) and mask [M] (valid and n.w_o > 0)."""
+    pair differently), mask [M] (valid and n.w_o > 0) and logw_max [M] (log of
+    the largest weight, -inf if none)."""
     P = _Prepared(mean, quat, logscale, spectrum)
     X = np.asarray(x, dtype=_F64).T
     M, C = X.shape[0], P.c
@@ -161,6 +162,7 @@ def radiance_fwd(mean, quat, logscale, spectrum, x, n, wo, albedo=None, valid=No
     Z = np.zeros(M)
     npairs = np.zeros(M, dtype=np.int64)
     near = np.zeros(M, dtype=bool)
+    logw_max = np.full(M, -np.inf)
     cut2 = cutoff_sigma * cutoff_sigma
     step = _chunk(P.n)
     for a in range(0, M, step):
@@ -170,6 +172,8 @@ def radiance_fwd(mean, quat, logscale, spectrum, x, n, wo, albedo=None, valid=No
         Lab[a:b] = w @ np.abs(P.phi)
         Z[a:b] = w.sum(axis=1)
         npairs[a:b] = inc.sum(axis=1)
+        with np.errstate(divide="ignore"):
+            logw_max[a:b] = np.log(w.max(axis=1)) if P.n else -np.inf
         if math.isfinite(cutoff_sigma):
             near[a:b] = np.any(np.abs(Q - cut2) < band, axis=1)
     mask = _query_mask(n, wo, valid, M)
@@ -186,7 +190,7 @@ def radiance_fwd(mean, quat, logscale, spectrum, x, n, wo, albedo=None, valid=No
         denom = denom / np.maximum(Z, eps)[:, None]
     denom = np.where(mask[:, None], denom, 0.0)
     return {"out": out.T.copy(), "L": L.T.copy(), "Z": Z, "n_pairs": npairs,
-            "denom": denom.T.copy(), "near_cutoff": near, "mask": mask}
+            "denom": denom.T.copy(), "near_cutoff": near, "mask": mask, "logw_max": logw_max}
 
 
 def radiance_bwd(mean, quat, logscale, spectrum, x, n, wo, grad_out, albedo=None,

@@ -1,0 +1,22 @@
+"""GB300-native hit-point radiance of a Gaussian Photon Field (arxiv 2512.12459).
+
+The compute path is libgpf.so (CUDA, sm_103a; C ABI in include/gpf.h). This
+package is its Python binding: PyTorch tensors for memory and streams,
+ctypes for the calls. The library is loaded at the first call; every call
+raises if libgpf.so has not been built (there is no fallback path)."""
+
+from . import _abi
+from ._abi import GPFError, LIB_PATH, load
+from .api import (GPF_NORMALIZED, GPF_SUM, PAPER_EPS, PAPER_LR, PAPER_R, AdamState, Field,
+                  GridConfig, Index, Queries, gpf_adam_step, gpf_count_pairs,
+                  gpf_launch_count, gpf_mse_loss_grad, gpf_radiance_bwd, gpf_radiance_fwd,
+                  grid_for_bounds)
+from .autograd import GPFRadiance, gpf_radiance
+
+__all__ = [
+    "GPFError", "LIB_PATH", "load", "GPF_NORMALIZED", "GPF_SUM", "PAPER_EPS", "PAPER_LR",
+    "PAPER_R", "AdamState", "Field", "GridConfig", "Index", "Queries", "gpf_adam_step",
+    "gpf_mse_loss_grad", "gpf_radiance_bwd", "gpf_radiance_fwd", "grid_for_bounds",
+    "gpf_count_pairs", "gpf_launch_count",
+    "GPFRadiance", "gpf_radiance", "_abi",
+]

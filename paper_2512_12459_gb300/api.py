@@ -1,0 +1,354 @@
+"""Python binding of libgpf with the same names as the C ABI.
+
+PyTorch supplies device memory and streams; every step of the radiance path
+runs in libgpf's CUDA kernels. The functions here only check tensor
+properties and marshal pointers."""
+
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+from typing import Optional, Sequence
+
+import torch
+
+from . import _abi
+from ._abi import GPF_NORMALIZED, GPF_SUM, GPFError, check, load
+
+__all__ = [
+    "GPF_SUM", "GPF_NORMALIZED", "GPFError", "GridConfig", "Field", "Queries", "Index",
+    "grid_for_bounds", "gpf_radiance_fwd", "gpf_radiance_bwd", "gpf_mse_loss_grad",
+    "gpf_adam_step", "AdamState", "PAPER_R", "PAPER_EPS", "PAPER_LR",
+]
+
+# Hyper-parameters the paper prints (Sec. S1.2 and the supplementary query listing).
+PAPER_R = 0.02
+PAPER_EPS = 1e-6
+PAPER_LR = 5e-4
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _need(t: torch.Tensor, name: str, rows: int, count: int, dtype=torch.float32):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must live on a CUDA device")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    want = (rows, count) if rows else (count,)
+    if tuple(t.shape) != want:
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {want}")
+
+
+@dataclasses.dataclass
+class Field:
+    """N Gaussians as float32 CUDA tensors: mean [3,N], quat [4,N] (w,x,y,z),
+    logscale [3,N], spectrum [C,N]."""
+
+    mean: torch.Tensor
+    quat: torch.Tensor
+    logscale: torch.Tensor
+    spectrum: torch.Tensor
+
+    @property
+    def n(self) -> int:
+        return int(self.mean.shape[1])
+
+    @property
+    def channels(self) -> int:
+        return int(self.spectrum.shape[0])
+
+    def c_struct(self) -> _abi.gpf_field:
+        n, c = self.n, self.channels
+        _need(self.mean, "mean", 3, n)
+        _need(self.quat, "quat", 4, n)
+        _need(self.logscale, "logscale", 3, n)
+        _need(self.spectrum, "spectrum", c, n)
+        return _abi.gpf_field(n, c, 0, _ptr(self.mean), _ptr(self.quat), _ptr(self.logscale),
+                              _ptr(self.spectrum))
+
+    def tensors(self):
+        return [self.mean, self.quat, self.logscale, self.spectrum]
+
+    @staticmethod
+    def zeros_like(f: "Field") -> "Field":
+        return Field(*(torch.zeros_like(t) for t in f.tensors()))
+
+    @staticmethod
+    def from_numpy(f, device="cuda") -> "Field":
+        return Field(*(torch.as_tensor(a, dtype=torch.float32, device=device).contiguous()
+                       for a in (f.mean, f.quat, f.logscale, f.spectrum)))
+
+
+@dataclasses.dataclass
+class Queries:
+    """M hit points as CUDA tensors: x, normal, wo [3,M] float32; albedo [C,M]
+    float32 or None; valid [M] uint8 or None."""
+
+    x: torch.Tensor
+    normal: torch.Tensor
+    wo: torch.Tensor
+    albedo: Optional[torch.Tensor] = None
+    valid: Optional[torch.Tensor] = None
+
+    @property
+    def m(self) -> int:
+        return int(self.x.shape[1])
+
+    def c_struct(self, channels: Optional[int] = None) -> _abi.gpf_queries:
+        m = self.m
+        _need(self.x, "x", 3, m)
+        _need(self.normal, "normal", 3, m)
+        _need(self.wo, "wo", 3, m)
+        if self.albedo is not None:
+            _need(self.albedo, "albedo", channels or int(self.albedo.shape[0]), m)
+        if self.valid is not None:
+            _need(self.valid, "valid", 0, m, torch.uint8)
+        return _abi.gpf_queries(m, _ptr(self.x), _ptr(self.normal), _ptr(self.wo),
+                                _ptr(self.albedo), _ptr(self.valid))
+
+    @staticmethod
+    def from_numpy(q, device="cuda") -> "Queries":
+        t = lambda a, dt=torch.float32: None if a is None else torch.as_tensor(  # noqa: E731
+            a, dtype=dt, device=device).contiguous()
+        return Queries(t(q.x), t(q.n), t(q.wo), t(q.albedo), t(q.valid, torch.uint8))
+
+
+@dataclasses.dataclass
+class GridConfig:
+    """Multi-level grid and capacities of an index (gpf_grid_config): level L
+    has cells of edge cell_size * 2^L; hit points are sorted on query_level,
+    a dims grid; Gaussian lists live in 2^hash_bits buckets."""
+
+    origin: Sequence[float]
+    cell_size: float
+    levels: int
+    max_span: int
+    query_level: int
+    dims: Sequence[int]
+    hash_bits: int
+    channels: int
+    cutoff_sigma: float = 3.0
+    max_gaussians: int = 0
+    max_queries: int = 0
+    max_pairs: int = 0
+    brute_force: bool = False
+
+    def c_struct(self) -> _abi.gpf_grid_config:
+        return _abi.gpf_grid_config((ctypes.c_float * 3)(*self.origin), float(self.cell_size),
+                                    int(self.levels), int(self.max_span), int(self.query_level),
+                                    (ctypes.c_int32 * 3)(*[int(d) for d in self.dims]),
+                                    int(self.hash_bits), int(self.channels),
+                                    float(self.cutoff_sigma), 1 if self.brute_force else 0,
+                                    int(self.max_gaussians), int(self.max_queries),
+                                    int(self.max_pairs))
+
+
+def grid_for_bounds(lo: Sequence[float], hi: Sequence[float], cell_size: float, channels: int,
+                    max_gaussians: int, max_queries: int, max_pairs: int,
+                    cutoff_sigma: float = 3.0, levels: int = 1, max_span: int = 4,
+                    query_level: int = 0, hash_bits: int = 20) -> GridConfig:
+    """A grid whose query level covers [lo, hi] with cells of cell_size *
+    2^query_level (points outside are clamped into the border cells, which
+    stays exact)."""
+    cq = cell_size * (1 << query_level)
+    dims = [max(1, min(_abi.GPF_MAX_DIM, int(math.ceil((float(h) - float(l)) / cq))))
+            for l, h in zip(lo, hi)]
+    return GridConfig([float(v) for v in lo], cell_size, levels, max_span, query_level, dims,
+                      hash_bits, channels, cutoff_sigma, max_gaussians, max_queries, max_pairs)
+
+
+class Index:
+    """gpf_index handle plus the device workspace it lives in (a uint8 CUDA
+    tensor owned by this object)."""
+
+    def __init__(self, grid: GridConfig, device="cuda"):
+        lib = load()
+        self._lib = lib
+        self.grid = grid
+        self._cfg = grid.c_struct()
+        h = ctypes.c_void_p()
+        check(lib.gpf_index_create(ctypes.byref(self._cfg), ctypes.byref(h)), "gpf_index_create")
+        self._h = h
+        sz = ctypes.c_size_t()
+        check(lib.gpf_index_workspace_size(h, ctypes.byref(sz)), "gpf_index_workspace_size")
+        self.workspace_bytes = int(sz.value)
+        self.workspace = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8,
+                                     device=device)
+        self._field = None
+        self._queries = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.gpf_index_destroy(h)
+            self._h = None
+
+    def build(self, field: Field, queries: Queries, stream=None) -> None:
+        """gpf_build_index for (field, queries)."""
+        fs = field.c_struct()
+        qs = queries.c_struct(field.channels)
+        check(self._lib.gpf_build_index(self._h, ctypes.byref(fs), ctypes.byref(qs),
+                                        self.workspace.data_ptr(), self.workspace_bytes,
+                                        _stream(stream)), "gpf_build_index")
+        self._field, self._queries = field, queries
+
+    def stats(self, stream=None) -> dict:
+        """gpf_index_stats (synchronises the stream)."""
+        st = _abi.gpf_index_stats_t()
+        status = self._lib.gpf_index_stats(self._h, ctypes.byref(st), _stream(stream))
+        out = {"n_pairs": st.n_pairs, "n_active": st.n_active, "overflow": bool(st.overflow)}
+        if status not in (_abi.GPF_OK, _abi.GPF_ERR_CAPACITY):
+            check(status, "gpf_index_stats")
+        return out
+
+
+def _params(mode, r_max, eps) -> _abi.gpf_query_params:
+    return _abi.gpf_query_params(int(mode), float(r_max), float(eps), 0)
+
+
+def gpf_radiance_fwd(index: Index, field: Field, queries: Queries, mode: int = GPF_SUM,
+                     r_max: float = math.inf, eps: float = PAPER_EPS,
+                     out: Optional[torch.Tensor] = None, z: Optional[torch.Tensor] = None,
+                     want_z: bool = True, stream=None):
+    """Radiance O [C,M] (and Z [M]) at the hit points the index was built for."""
+    m, c = queries.m, field.channels
+    dev = queries.x.device
+    if out is None:
+        out = torch.empty((c, m), dtype=torch.float32, device=dev)
+    if z is None and want_z:
+        z = torch.empty((m,), dtype=torch.float32, device=dev)
+    _need(out, "out", c, m)
+    if z is not None:
+        _need(z, "z", 0, m)
+    fs, qs, ps = field.c_struct(), queries.c_struct(c), _params(mode, r_max, eps)
+    check(index._lib.gpf_radiance_fwd(index.handle, ctypes.byref(fs), ctypes.byref(qs),
+                                      ctypes.byref(ps), out.data_ptr(), _ptr(z),
+                                      _stream(stream)), "gpf_radiance_fwd")
+    return out, z
+
+
+def gpf_count_pairs(index: Index, field: Field, queries: Queries, stream=None) -> dict:
+    """Pairs the forward evaluates after culling ("candidates") and pairs with
+    Q <= k^2 ("included"); synchronises the stream to read them."""
+    counts = torch.zeros(2, dtype=torch.int64, device=queries.x.device)
+    fs, qs = field.c_struct(), queries.c_struct(field.channels)
+    check(index._lib.gpf_count_pairs(index.handle, ctypes.byref(fs), ctypes.byref(qs),
+                                     counts.data_ptr(), _stream(stream)), "gpf_count_pairs")
+    c = counts.cpu().tolist()
+    return {"candidates": int(c[0]), "included": int(c[1])}
+
+
+def gpf_launch_count() -> int:
+    """Kernels libgpf has launched in this process."""
+    return int(load().gpf_launch_count())
+
+
+def gpf_radiance_bwd(index: Index, field: Field, queries: Queries, grad_out: torch.Tensor,
+                     out: Optional[torch.Tensor] = None, z: Optional[torch.Tensor] = None,
+                     mode: int = GPF_SUM, r_max: float = math.inf, eps: float = PAPER_EPS,
+                     grads: Optional[Field] = None, accumulate: bool = False,
+                     stream=None) -> Field:
+    """Gradients (a Field of tensors) of sum(grad_out * O) w.r.t. mean, quat,
+    logscale and spectrum."""
+    m, c = queries.m, field.channels
+    _need(grad_out, "grad_out", c, m)
+    if grads is None:
+        grads = Field.zeros_like(field) if accumulate else Field(
+            *(torch.empty_like(t) for t in field.tensors()))
+    for name, g, t in zip(("grad_mean", "grad_quat", "grad_logscale", "grad_spectrum"),
+                          grads.tensors(), field.tensors()):
+        _need(g, name, t.shape[0], t.shape[1])
+    if mode == GPF_NORMALIZED:
+        if out is None or z is None:
+            raise ValueError("GPF_NORMALIZED backward needs the forward's out and z")
+        _need(out, "out", c, m)
+        _need(z, "z", 0, m)
+    fs, qs, ps = field.c_struct(), queries.c_struct(c), _params(mode, r_max, eps)
+    gs = _abi.gpf_field_grad(_ptr(grads.mean), _ptr(grads.quat), _ptr(grads.logscale),
+                             _ptr(grads.spectrum), 1 if accumulate else 0, 0)
+    check(index._lib.gpf_radiance_bwd(index.handle, ctypes.byref(fs), ctypes.byref(qs),
+                                      ctypes.byref(ps), grad_out.data_ptr(), _ptr(out), _ptr(z),
+                                      ctypes.byref(gs), _stream(stream)), "gpf_radiance_bwd")
+    return grads
+
+
+class _MseWorkspace:
+    cache = {}
+
+    @classmethod
+    def get(cls, m: int, device) -> torch.Tensor:
+        key = (m, str(device))
+        ws = cls.cache.get(key)
+        if ws is None:
+            sz = ctypes.c_size_t()
+            check(load().gpf_mse_workspace_size(m, ctypes.byref(sz)), "gpf_mse_workspace_size")
+            ws = torch.empty(max(int(sz.value), 256), dtype=torch.uint8, device=device)
+            cls.cache = {key: ws}
+        return ws
+
+
+def gpf_mse_loss_grad(out: torch.Tensor, target: torch.Tensor,
+                      valid: Optional[torch.Tensor] = None, loss: Optional[torch.Tensor] = None,
+                      grad: Optional[torch.Tensor] = None, stream=None):
+    """MSE loss (a 1-element CUDA tensor) and its gradient with respect to out."""
+    c, m = int(out.shape[0]), int(out.shape[1])
+    _need(out, "out", c, m)
+    _need(target, "target", c, m)
+    if valid is not None:
+        _need(valid, "valid", 0, m, torch.uint8)
+    if loss is None:
+        loss = torch.empty((1,), dtype=torch.float32, device=out.device)
+    if grad is None:
+        grad = torch.empty_like(out)
+    ws = _MseWorkspace.get(m, out.device)
+    check(load().gpf_mse_loss_grad(m, c, out.data_ptr(), target.data_ptr(), _ptr(valid),
+                                   loss.data_ptr(), grad.data_ptr(), ws.data_ptr(), ws.numel(),
+                                   _stream(stream)), "gpf_mse_loss_grad")
+    return loss, grad
+
+
+@dataclasses.dataclass
+class AdamState:
+    m: Field
+    v: Field
+    step: int = 0
+
+    @staticmethod
+    def zeros_like(f: Field) -> "AdamState":
+        return AdamState(Field.zeros_like(f), Field.zeros_like(f), 0)
+
+
+def _grad_struct(f: Field) -> _abi.gpf_field_grad:
+    return _abi.gpf_field_grad(_ptr(f.mean), _ptr(f.quat), _ptr(f.logscale), _ptr(f.spectrum), 0, 0)
+
+
+def gpf_adam_step(params: Field, grads: Field, state: AdamState, lr=PAPER_LR, beta1: float = 0.9,
+                  beta2: float = 0.999, eps: float = 1e-8, stream=None) -> None:
+    """One Adam update of params in place; state.step is incremented first."""
+    lrs = list(lr) if isinstance(lr, (list, tuple)) else [float(lr)] * 4
+    for g, p in zip(grads.tensors() + state.m.tensors() + state.v.tensors(), params.tensors() * 3):
+        _need(g, "adam tensor", p.shape[0], p.shape[1])
+    state.step += 1
+    fs = params.c_struct()
+    hp = _abi.gpf_adam_hparams((ctypes.c_float * 4)(*lrs), beta1, beta2, eps, state.step)
+    g, m, v = _grad_struct(grads), _grad_struct(state.m), _grad_struct(state.v)
+    check(load().gpf_adam_step(ctypes.byref(fs), ctypes.byref(g), ctypes.byref(m),
+                               ctypes.byref(v), ctypes.byref(hp), _stream(stream)),
+          "gpf_adam_step")

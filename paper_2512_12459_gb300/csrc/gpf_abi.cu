@@ -1,0 +1,449 @@
+// The C ABI of libgpf (include/gpf.h): argument validation, workspace
+// layout, error reporting, and the launches of the kernel files.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <new>
+#include <string>
+
+#include "gpf_internal.h"
+
+using namespace gpf;
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+
+gpf_status fail(gpf_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+gpf_status fail(gpf_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+gpf_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(GPF_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+#define GPF_CHECK_PTR(p, what)                                                              \
+  do {                                                                                      \
+    if ((p) == nullptr) return fail(GPF_ERR_INVALID_ARG, "%s is NULL", what);               \
+    if (!aligned((p), 4)) return fail(GPF_ERR_INVALID_ARG, "%s is not 4-byte aligned", what); \
+  } while (0)
+
+}  // namespace
+
+void gpf::note_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+struct gpf_index {
+  gpf_grid_config cfg;
+  IndexDims dims;
+  size_t ws_bytes;
+  IndexBuffers buf;
+  bool built;
+  // identity of the last build
+  gpf_field field;
+  gpf_queries queries;
+};
+
+namespace {
+
+// Carves the workspace; with base == nullptr only computes the size.
+size_t layout(const gpf_index* ix, char* base, IndexBuffers* b) {
+  const IndexDims& d = ix->dims;
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off += align_up(bytes);
+    return p;
+  };
+  IndexBuffers t{};
+  const int64_t N = d.n_max, M = d.m_max, P = d.brute ? 0 : d.p_max;
+  const size_t ncp = (size_t)d.grid.n_keys + 2;
+  const size_t nb = d.brute ? 1 : (size_t)d.grid.n_buckets;
+  t.header = reinterpret_cast<DeviceHeader*>(take(sizeof(DeviceHeader)));
+  t.rec = reinterpret_cast<float*>(take(sizeof(float) * N * rec_stride(d.channels)));
+  t.box = reinterpret_cast<uint4*>(take(sizeof(uint4) * N));
+  t.gcount = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * N));
+  t.goffset = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * N));
+  for (int k = 0; k < 2; ++k) {
+    t.okey[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * N));
+    t.oval[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * N));
+  }
+  for (int k = 0; k < 2; ++k) {
+    t.qkey[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * M));
+    t.qval[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * M));
+  }
+  t.qstart = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * ncp));
+  t.qrec = reinterpret_cast<float*>(take(sizeof(float) * M * qrec_stride(d.channels)));
+  for (int k = 0; k < 2; ++k) {
+    t.gkey[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (P > 0 ? P : 1)));
+    t.gval[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (P > 0 ? P : 1)));
+  }
+  t.occ = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * ((nb + 31) / 32)));
+  t.brange = reinterpret_cast<uint2*>(take(sizeof(uint2) * nb));
+  t.scan_ws = take(scan_workspace_bytes(std::max<int64_t>(std::max<int64_t>(N, 1), ncp)));
+  t.qsort_ws = take(radix_sort_workspace_bytes(M > 0 ? M : 1));
+  t.gsort_ws = take(radix_sort_workspace_bytes(P > 0 ? P : 1));
+  t.osort_ws = take(radix_sort_workspace_bytes(N > 0 ? N : 1));
+  t.qsorted = radix_sort_passes(d.grid.key_bits) % 2;
+  t.osorted = t.qsorted;
+  t.gsorted = radix_sort_passes(d.grid.hash_bits) % 2;
+  if (b) *b = t;
+  return off;
+}
+
+gpf_status check_field(const gpf_index* ix, const gpf_field* f) {
+  if (!f) return fail(GPF_ERR_INVALID_ARG, "field is NULL");
+  if (f->n < 0) return fail(GPF_ERR_INVALID_ARG, "field.n = %lld < 0", (long long)f->n);
+  if (f->n > ix->dims.n_max)
+    return fail(GPF_ERR_INVALID_ARG, "field.n = %lld exceeds max_gaussians = %lld",
+                (long long)f->n, (long long)ix->dims.n_max);
+  if (f->n >= (int64_t)kIdMask) return fail(GPF_ERR_INVALID_ARG, "field.n too large");
+  if (f->channels != ix->dims.channels)
+    return fail(GPF_ERR_INVALID_ARG, "field.channels = %d but the index holds %d channels",
+                f->channels, ix->dims.channels);
+  if (f->reserved != 0) return fail(GPF_ERR_INVALID_ARG, "field.reserved must be 0");
+  if (f->n > 0) {
+    GPF_CHECK_PTR(f->mean, "field.mean");
+    GPF_CHECK_PTR(f->quat, "field.quat");
+    GPF_CHECK_PTR(f->logscale, "field.logscale");
+    GPF_CHECK_PTR(f->spectrum, "field.spectrum");
+  }
+  return GPF_OK;
+}
+
+gpf_status check_queries(const gpf_index* ix, const gpf_queries* q) {
+  if (!q) return fail(GPF_ERR_INVALID_ARG, "queries is NULL");
+  if (q->m < 0) return fail(GPF_ERR_INVALID_ARG, "queries.m = %lld < 0", (long long)q->m);
+  if (q->m > ix->dims.m_max)
+    return fail(GPF_ERR_INVALID_ARG, "queries.m = %lld exceeds max_queries = %lld",
+                (long long)q->m, (long long)ix->dims.m_max);
+  if (q->m > 0) {
+    GPF_CHECK_PTR(q->x, "queries.x");
+    GPF_CHECK_PTR(q->normal, "queries.normal");
+    GPF_CHECK_PTR(q->wo, "queries.wo");
+    if (q->albedo && !aligned(q->albedo, 4))
+      return fail(GPF_ERR_INVALID_ARG, "queries.albedo is not 4-byte aligned");
+  }
+  return GPF_OK;
+}
+
+gpf_status check_params(const gpf_query_params* p) {
+  if (!p) return fail(GPF_ERR_INVALID_ARG, "params is NULL");
+  if (p->mode != GPF_SUM && p->mode != GPF_NORMALIZED)
+    return fail(GPF_ERR_INVALID_ARG, "params.mode = %d is not GPF_SUM or GPF_NORMALIZED", p->mode);
+  if (isnan(p->r_max) || p->r_max < 0.0f)
+    return fail(GPF_ERR_INVALID_ARG, "params.r_max must be >= 0 or +INF");
+  if (!(p->eps > 0.0f) || !isfinite(p->eps))
+    return fail(GPF_ERR_INVALID_ARG, "params.eps must be finite and > 0");
+  if (p->reserved != 0) return fail(GPF_ERR_INVALID_ARG, "params.reserved must be 0");
+  return GPF_OK;
+}
+
+gpf_status check_same(const gpf_index* ix, const gpf_field* f, const gpf_queries* q) {
+  if (!ix->built) return fail(GPF_ERR_NOT_BUILT, "gpf_build_index has not run on this index");
+  const gpf_field& a = ix->field;
+  const gpf_queries& b = ix->queries;
+  if (a.n != f->n || a.mean != f->mean || a.quat != f->quat || a.logscale != f->logscale ||
+      a.spectrum != f->spectrum)
+    return fail(GPF_ERR_MISMATCH, "field differs from the one given to gpf_build_index");
+  if (b.m != q->m || b.x != q->x || b.normal != q->normal || b.wo != q->wo ||
+      b.valid != q->valid)
+    return fail(GPF_ERR_MISMATCH, "queries differ from the ones given to gpf_build_index");
+  return GPF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gpf_version(void) { return "gpf 0.1 (sm_103a)"; }
+
+const char* gpf_status_string(gpf_status s) {
+  switch (s) {
+    case GPF_OK: return "GPF_OK";
+    case GPF_ERR_INVALID_ARG: return "GPF_ERR_INVALID_ARG";
+    case GPF_ERR_CUDA: return "GPF_ERR_CUDA";
+    case GPF_ERR_WORKSPACE_TOO_SMALL: return "GPF_ERR_WORKSPACE_TOO_SMALL";
+    case GPF_ERR_CAPACITY: return "GPF_ERR_CAPACITY";
+    case GPF_ERR_NOT_BUILT: return "GPF_ERR_NOT_BUILT";
+    case GPF_ERR_MISMATCH: return "GPF_ERR_MISMATCH";
+  }
+  return "GPF_ERR_UNKNOWN";
+}
+
+const char* gpf_last_error(void) { return g_last_error.c_str(); }
+
+gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
+  if (!cfg || !out) return fail(GPF_ERR_INVALID_ARG, "cfg or out is NULL");
+  *out = nullptr;
+  if (!(cfg->cell_size > 0.0f) || !isfinite(cfg->cell_size))
+    return fail(GPF_ERR_INVALID_ARG, "cell_size must be finite and > 0");
+  if (cfg->levels < 1 || cfg->levels > GPF_MAX_LEVELS)
+    return fail(GPF_ERR_INVALID_ARG, "levels = %d outside 1..%d", cfg->levels, GPF_MAX_LEVELS);
+  if (cfg->max_span < 1 || cfg->max_span > 64)
+    return fail(GPF_ERR_INVALID_ARG, "max_span = %d outside 1..64", cfg->max_span);
+  if (cfg->query_level < 0 || cfg->query_level > 15)
+    return fail(GPF_ERR_INVALID_ARG, "query_level = %d outside 0..15", cfg->query_level);
+  if (cfg->hash_bits < 8 || cfg->hash_bits > 28)
+    return fail(GPF_ERR_INVALID_ARG, "hash_bits = %d outside 8..28", cfg->hash_bits);
+  for (int k = 0; k < 3; ++k) {
+    if (!isfinite(cfg->origin[k])) return fail(GPF_ERR_INVALID_ARG, "origin must be finite");
+    if (cfg->dims[k] < 1 || cfg->dims[k] > GPF_MAX_DIM)
+      return fail(GPF_ERR_INVALID_ARG, "dims[%d] = %d outside 1..%d", k, cfg->dims[k],
+                  GPF_MAX_DIM);
+    if (((int64_t)cfg->dims[k] << cfg->query_level) > (int64_t(1) << kCoordBits))
+      return fail(GPF_ERR_INVALID_ARG, "dims[%d] * 2^query_level exceeds 2^%d finest cells", k,
+                  kCoordBits);
+  }
+  if (cfg->channels < 1 || cfg->channels > GPF_MAX_CHANNELS)
+    return fail(GPF_ERR_INVALID_ARG, "channels = %d outside 1..%d", cfg->channels,
+                GPF_MAX_CHANNELS);
+  if (!(cfg->cutoff_sigma > 0.0f))
+    return fail(GPF_ERR_INVALID_ARG, "cutoff_sigma must be > 0 (or +INF)");
+  if (cfg->brute_force != 0 && cfg->brute_force != 1)
+    return fail(GPF_ERR_INVALID_ARG, "brute_force must be 0 or 1");
+  if (cfg->max_gaussians < 0 || cfg->max_queries < 0 || cfg->max_pairs < 0)
+    return fail(GPF_ERR_INVALID_ARG, "capacities must be >= 0");
+  if (cfg->max_gaussians >= (int64_t)kIdMask || cfg->max_queries >= (int64_t)0xffffffffLL ||
+      cfg->max_pairs >= (int64_t)0xffffffffLL)
+    return fail(GPF_ERR_INVALID_ARG, "capacities must be below 2^31 (Gaussians) / 2^32");
+  const uint64_t cells = (uint64_t)cfg->dims[0] * cfg->dims[1] * cfg->dims[2];
+  if (cells > (1ull << 28))
+    return fail(GPF_ERR_INVALID_ARG, "grid has %llu cells, more than 2^28",
+                (unsigned long long)cells);
+  gpf_index* ix = new (std::nothrow) gpf_index();
+  if (!ix) return fail(GPF_ERR_INVALID_ARG, "out of host memory");
+  ix->cfg = *cfg;
+  IndexDims& d = ix->dims;
+  d.grid.ox = cfg->origin[0];
+  d.grid.oy = cfg->origin[1];
+  d.grid.oz = cfg->origin[2];
+  d.grid.cell0 = cfg->cell_size;
+  d.grid.inv_cell0 = 1.0f / cfg->cell_size;
+  d.grid.levels = cfg->levels;
+  d.grid.max_span = cfg->max_span;
+  d.grid.qlevel = cfg->query_level;
+  d.grid.hash_bits = cfg->hash_bits;
+  d.grid.n_buckets = 1u << cfg->hash_bits;
+  d.grid.max0x = ((uint32_t)cfg->dims[0] << cfg->query_level) - 1;
+  d.grid.max0y = ((uint32_t)cfg->dims[1] << cfg->query_level) - 1;
+  d.grid.max0z = ((uint32_t)cfg->dims[2] << cfg->query_level) - 1;
+  {
+    int ib = 1;
+    while (ib < 31 && (int64_t(1) << ib) < cfg->max_gaussians) ++ib;
+    d.grid.id_bits = ib;
+    d.grid.id_mask = (uint32_t)((uint64_t(1) << ib) - 1);
+  }
+  d.grid.dx = cfg->dims[0];
+  d.grid.dy = cfg->dims[1];
+  d.grid.dz = cfg->dims[2];
+  d.grid.n_keys = (uint32_t)cells;
+  d.grid.key_inactive = (uint32_t)cells;
+  int bits = 0;
+  while ((1ull << bits) <= cells) ++bits;
+  d.grid.key_bits = bits;
+  d.channels = cfg->channels;
+  d.cutoff = cfg->cutoff_sigma;
+  d.brute = isinf(cfg->cutoff_sigma) || cfg->brute_force == 1;
+  d.n_max = cfg->max_gaussians;
+  d.m_max = cfg->max_queries;
+  d.p_max = d.brute ? 0 : cfg->max_pairs;
+  ix->ws_bytes = layout(ix, nullptr, nullptr);
+  ix->built = false;
+  *out = ix;
+  return GPF_OK;
+}
+
+void gpf_index_destroy(gpf_index* index) { delete index; }
+
+gpf_status gpf_index_workspace_size(const gpf_index* index, size_t* bytes) {
+  if (!index || !bytes) return fail(GPF_ERR_INVALID_ARG, "index or bytes is NULL");
+  *bytes = index->ws_bytes;
+  return GPF_OK;
+}
+
+gpf_status gpf_build_index(gpf_index* index, const gpf_field* field, const gpf_queries* queries,
+                           void* workspace, size_t workspace_bytes, gpf_stream stream) {
+  if (!index) return fail(GPF_ERR_INVALID_ARG, "index is NULL");
+  gpf_status s;
+  if ((s = check_field(index, field)) != GPF_OK) return s;
+  if ((s = check_queries(index, queries)) != GPF_OK) return s;
+  if (!workspace) return fail(GPF_ERR_INVALID_ARG, "workspace is NULL");
+  if (!aligned(workspace, 256)) return fail(GPF_ERR_INVALID_ARG, "workspace is not 256-byte aligned");
+  if (workspace_bytes < index->ws_bytes)
+    return fail(GPF_ERR_WORKSPACE_TOO_SMALL, "workspace has %zu bytes, needs %zu", workspace_bytes,
+                index->ws_bytes);
+  layout(index, static_cast<char*>(workspace), &index->buf);
+  index->built = false;
+  cudaError_t e = launch_build(index->dims, index->buf, *field, *queries,
+                               reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "gpf_build_index");
+  index->field = *field;
+  index->queries = *queries;
+  index->built = true;
+  return GPF_OK;
+}
+
+gpf_status gpf_index_stats(const gpf_index* index, gpf_index_stats_t* stats, gpf_stream stream) {
+  if (!index || !stats) return fail(GPF_ERR_INVALID_ARG, "index or stats is NULL");
+  if (!index->built) return fail(GPF_ERR_NOT_BUILT, "gpf_build_index has not run on this index");
+  DeviceHeader h;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(&h, index->buf.header, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "gpf_index_stats");
+  memset(stats, 0, sizeof(*stats));
+  stats->n_pairs = h.n_pairs;
+  stats->n_active = h.n_active;
+  stats->overflow = (int32_t)h.overflow;
+  if (h.overflow)
+    return fail(GPF_ERR_CAPACITY, "pair buffer overflow: %u entries needed, capacity %lld",
+                h.n_pairs, (long long)index->dims.p_max);
+  return GPF_OK;
+}
+
+gpf_status gpf_radiance_fwd(const gpf_index* index, const gpf_field* field,
+                            const gpf_queries* queries, const gpf_query_params* params,
+                            float* out, float* z_out, gpf_stream stream) {
+  if (!index) return fail(GPF_ERR_INVALID_ARG, "index is NULL");
+  gpf_status s;
+  if ((s = check_field(index, field)) != GPF_OK) return s;
+  if ((s = check_queries(index, queries)) != GPF_OK) return s;
+  if ((s = check_params(params)) != GPF_OK) return s;
+  if ((s = check_same(index, field, queries)) != GPF_OK) return s;
+  if (queries->m > 0) {
+    GPF_CHECK_PTR(out, "out");
+    if (z_out && !aligned(z_out, 4)) return fail(GPF_ERR_INVALID_ARG, "z_out is not aligned");
+  }
+  cudaError_t e = launch_forward(index->dims, index->buf, *queries, *params, field->n, out, z_out,
+                                 nullptr, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "gpf_radiance_fwd");
+  return GPF_OK;
+}
+
+gpf_status gpf_count_pairs(const gpf_index* index, const gpf_field* field,
+                           const gpf_queries* queries, uint64_t* counts, gpf_stream stream) {
+  if (!index) return fail(GPF_ERR_INVALID_ARG, "index is NULL");
+  gpf_status s;
+  if ((s = check_field(index, field)) != GPF_OK) return s;
+  if ((s = check_queries(index, queries)) != GPF_OK) return s;
+  if ((s = check_same(index, field, queries)) != GPF_OK) return s;
+  if (!counts || !aligned(counts, 8))
+    return fail(GPF_ERR_INVALID_ARG, "counts is NULL or not 8-byte aligned");
+  gpf_query_params p{GPF_SUM, INFINITY, 1e-6f, 0};
+  cudaError_t e = launch_forward(index->dims, index->buf, *queries, p, field->n, nullptr, nullptr,
+                                 reinterpret_cast<unsigned long long*>(counts),
+                                 reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "gpf_count_pairs");
+  return GPF_OK;
+}
+
+uint64_t gpf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+gpf_status gpf_radiance_bwd(const gpf_index* index, const gpf_field* field,
+                            const gpf_queries* queries, const gpf_query_params* params,
+                            const float* grad_out, const float* out, const float* z,
+                            const gpf_field_grad* grads, gpf_stream stream) {
+  if (!index) return fail(GPF_ERR_INVALID_ARG, "index is NULL");
+  gpf_status s;
+  if ((s = check_field(index, field)) != GPF_OK) return s;
+  if ((s = check_queries(index, queries)) != GPF_OK) return s;
+  if ((s = check_params(params)) != GPF_OK) return s;
+  if ((s = check_same(index, field, queries)) != GPF_OK) return s;
+  if (!grads) return fail(GPF_ERR_INVALID_ARG, "grads is NULL");
+  if (grads->reserved != 0) return fail(GPF_ERR_INVALID_ARG, "grads.reserved must be 0");
+  if (field->n > 0) {
+    GPF_CHECK_PTR(grads->mean, "grads.mean");
+    GPF_CHECK_PTR(grads->quat, "grads.quat");
+    GPF_CHECK_PTR(grads->logscale, "grads.logscale");
+    GPF_CHECK_PTR(grads->spectrum, "grads.spectrum");
+  }
+  if (queries->m > 0) {
+    GPF_CHECK_PTR(grad_out, "grad_out");
+    if (params->mode == GPF_NORMALIZED) {
+      GPF_CHECK_PTR(out, "out");
+      GPF_CHECK_PTR(z, "z");
+    }
+  }
+  cudaError_t e = launch_backward(index->dims, index->buf, *field, *queries, *params, grad_out, out,
+                                  z, *grads, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "gpf_radiance_bwd");
+  return GPF_OK;
+}
+
+gpf_status gpf_mse_workspace_size(int64_t m, size_t* bytes) {
+  if (m < 0 || !bytes) return fail(GPF_ERR_INVALID_ARG, "m < 0 or bytes is NULL");
+  *bytes = mse_workspace_bytes(m);
+  return GPF_OK;
+}
+
+gpf_status gpf_mse_loss_grad(int64_t m, int32_t channels, const float* out, const float* target,
+                             const uint8_t* valid, float* loss, float* grad, void* workspace,
+                             size_t workspace_bytes, gpf_stream stream) {
+  if (m < 0) return fail(GPF_ERR_INVALID_ARG, "m < 0");
+  if (channels < 1 || channels > GPF_MAX_CHANNELS)
+    return fail(GPF_ERR_INVALID_ARG, "channels = %d outside 1..%d", channels, GPF_MAX_CHANNELS);
+  GPF_CHECK_PTR(loss, "loss");
+  if (m > 0) {
+    GPF_CHECK_PTR(out, "out");
+    GPF_CHECK_PTR(target, "target");
+    GPF_CHECK_PTR(grad, "grad");
+  }
+  if (!workspace) return fail(GPF_ERR_INVALID_ARG, "workspace is NULL");
+  if (!aligned(workspace, 256)) return fail(GPF_ERR_INVALID_ARG, "workspace is not 256-byte aligned");
+  if (workspace_bytes < mse_workspace_bytes(m))
+    return fail(GPF_ERR_WORKSPACE_TOO_SMALL, "workspace has %zu bytes, needs %zu", workspace_bytes,
+                mse_workspace_bytes(m));
+  cudaError_t e = launch_mse(m, channels, out, target, valid, loss, grad, workspace,
+                             reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "gpf_mse_loss_grad");
+  return GPF_OK;
+}
+
+gpf_status gpf_adam_step(const gpf_field* params, const gpf_field_grad* grads,
+                         const gpf_field_grad* m, const gpf_field_grad* v,
+                         const gpf_adam_hparams* hp, gpf_stream stream) {
+  if (!params || !grads || !m || !v || !hp)
+    return fail(GPF_ERR_INVALID_ARG, "a pointer argument is NULL");
+  if (params->n < 0) return fail(GPF_ERR_INVALID_ARG, "params.n < 0");
+  if (params->channels < 1 || params->channels > GPF_MAX_CHANNELS)
+    return fail(GPF_ERR_INVALID_ARG, "params.channels outside 1..%d", GPF_MAX_CHANNELS);
+  if (hp->step < 1) return fail(GPF_ERR_INVALID_ARG, "hp.step = %d < 1", hp->step);
+  if (!(hp->beta1 >= 0.0f && hp->beta1 < 1.0f) || !(hp->beta2 >= 0.0f && hp->beta2 < 1.0f))
+    return fail(GPF_ERR_INVALID_ARG, "betas must lie in [0, 1)");
+  if (!(hp->eps >= 0.0f)) return fail(GPF_ERR_INVALID_ARG, "eps must be >= 0");
+  for (int k = 0; k < 4; ++k)
+    if (!isfinite(hp->lr[k]) || hp->lr[k] < 0.0f)
+      return fail(GPF_ERR_INVALID_ARG, "lr[%d] must be finite and >= 0", k);
+  if (params->n > 0) {
+    const gpf_field_grad* gs[3] = {grads, m, v};
+    const char* names[3] = {"grads", "m", "v"};
+    GPF_CHECK_PTR(params->mean, "params.mean");
+    GPF_CHECK_PTR(params->quat, "params.quat");
+    GPF_CHECK_PTR(params->logscale, "params.logscale");
+    GPF_CHECK_PTR(params->spectrum, "params.spectrum");
+    for (int k = 0; k < 3; ++k) {
+      if (!gs[k]->mean || !gs[k]->quat || !gs[k]->logscale || !gs[k]->spectrum)
+        return fail(GPF_ERR_INVALID_ARG, "%s has a NULL array", names[k]);
+    }
+  }
+  cudaError_t e = launch_adam(*params, *grads, *m, *v, *hp, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "gpf_adam_step");
+  return GPF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,484 @@
+// gpf_radiance_bwd: gradient of the hit-point radiance with respect to every
+// Gaussian parameter (Sec. 3.2, Differentiable Accumulation).
+//
+// Chain rule for a pair (Gaussian i, hit point x) with w = exp(-Q/2) psi:
+//   d loss / d w   = beta = zeta (sum_c gamma_c Phi_c - kappa)
+//       gamma_c = g_c rho_c;  SUM: zeta = 1, kappa = 0;
+//       NORMALIZED: zeta = 1/Z, kappa = sum_c g_c O_c (zeta = 1/eps, kappa = 0 when Z <= eps)
+//   d loss / d Phi_c += gamma_c zeta w
+//   dw/dl_j = w u_j^2, dw/dR_kj = -w u_j d_k / s_j, dw/dmu = w M^T u + w 6t/(r' |d|) d
+// Per Gaussian the warp accumulates
+//   A = sum beta w u u^T (6 floats), B = sum beta w u, D = sum beta w 6t/(r'|d|) d, dPhi
+// and the epilogue turns them into gradients, using d = R S u:
+//   d mu = M^T B + D,  d l_j = A_jj,  dR_kj = -(1/s_j) sum_m R_km s_m A_jm,
+//   dq from dR through R(qhat) and qhat = q/|q|.
+// Traversal is Gaussian-major: one warp per Gaussian, Gaussians in the order
+// of the query-level cell of their mean (neighbouring warps share hit points
+// in cache). The warp visits the hit points of every query-level cell that
+// the Gaussian's k-sigma bounds overlap, so each pair is seen exactly once,
+// and the sums are reduced inside the warp: no global atomics, bitwise
+// reproducible.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "gpf_internal.h"
+
+namespace gpf {
+
+namespace {
+
+constexpr int kBwdWarps = 4;
+constexpr int kBwdThreads = kBwdWarps * kWarp;
+
+struct BwdArgs {
+  Grid grid;
+  const DeviceHeader* header;
+  const uint32_t* qval;
+  const uint32_t* qstart;
+  const float* x;
+  const float* albedo;
+  const float* grad_out;
+  const float* out;
+  const float* z;
+  int64_t m;
+  float* qrec;
+  const float* rec;
+  const uint4* box;
+  const uint32_t* order;  // Gaussian ids in mean-cell order
+  int64_t n;
+  const float* quat;
+  const float* logscale;
+  int mode;
+  float r, r2, inv_rr, eps, cut, cut2;
+  gpf_field_grad g;
+};
+
+template <int C>
+__global__ void pack_qrec_kernel(BwdArgs a) {
+  constexpr int QS = qrec_stride(C);
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (int64_t)a.header->n_active) return;
+  const uint32_t q = a.qval[k];
+  float gam[C];
+  float kappa = 0.0f, zeta = 1.0f;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const float g = a.grad_out[(int64_t)c * a.m + q];
+    gam[c] = g * (a.albedo ? a.albedo[(int64_t)c * a.m + q] : 1.0f);
+  }
+  if (a.mode == GPF_NORMALIZED) {
+    const float Z = a.z[q];
+    if (Z > a.eps) {
+      zeta = 1.0f / Z;
+#pragma unroll
+      for (int c = 0; c < C; ++c) kappa = fmaf(a.grad_out[(int64_t)c * a.m + q], a.out[(int64_t)c * a.m + q], kappa);
+    } else {
+      zeta = 1.0f / a.eps;
+    }
+  }
+  float* r = a.qrec + k * QS;
+  r[0] = a.x[q];
+  r[1] = a.x[a.m + q];
+  r[2] = a.x[2 * a.m + q];
+  r[3] = zeta;
+  r[4] = kappa;
+#pragma unroll
+  for (int c = 0; c < C; ++c) r[5 + c] = gam[c];
+#pragma unroll
+  for (int c = 5 + C; c < QS; ++c) r[c] = 0.0f;
+}
+
+template <int C>
+struct Acc {
+  float A00, A01, A02, A11, A12, A22;
+  float B0, B1, B2;
+  float D0, D1, D2;
+  float P[C];
+  __device__ void zero() {
+    A00 = A01 = A02 = A11 = A12 = A22 = 0.f;
+    B0 = B1 = B2 = 0.f;
+    D0 = D1 = D2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < C; ++c) P[c] = 0.f;
+  }
+  __device__ void warp_sum() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      A00 += __shfl_xor_sync(kFullMask, A00, o);
+      A01 += __shfl_xor_sync(kFullMask, A01, o);
+      A02 += __shfl_xor_sync(kFullMask, A02, o);
+      A11 += __shfl_xor_sync(kFullMask, A11, o);
+      A12 += __shfl_xor_sync(kFullMask, A12, o);
+      A22 += __shfl_xor_sync(kFullMask, A22, o);
+      B0 += __shfl_xor_sync(kFullMask, B0, o);
+      B1 += __shfl_xor_sync(kFullMask, B1, o);
+      B2 += __shfl_xor_sync(kFullMask, B2, o);
+      D0 += __shfl_xor_sync(kFullMask, D0, o);
+      D1 += __shfl_xor_sync(kFullMask, D1, o);
+      D2 += __shfl_xor_sync(kFullMask, D2, o);
+#pragma unroll
+      for (int c = 0; c < C; ++c) P[c] += __shfl_xor_sync(kFullMask, P[c], o);
+    }
+  }
+};
+
+struct GaussianRegs {
+  float mx, my, mz;
+  float M[9];
+};
+
+// One (Gaussian, hit point) pair of the backward.
+template <int C, bool PSI>
+__device__ __forceinline__ void bwd_pair(const GaussianRegs& G, const float (&phi)[C],
+                                         const float* __restrict__ qr, const BwdArgs& a,
+                                         Acc<C>& acc) {
+  constexpr int QS = qrec_stride(C);
+  const float4 q0 = __ldg(reinterpret_cast<const float4*>(qr));
+  const float dx = q0.x - G.mx, dy = q0.y - G.my, dz = q0.z - G.mz;
+  const float u0 = fmaf(G.M[0], dx, fmaf(G.M[1], dy, G.M[2] * dz));
+  const float u1 = fmaf(G.M[3], dx, fmaf(G.M[4], dy, G.M[5] * dz));
+  const float u2 = fmaf(G.M[6], dx, fmaf(G.M[7], dy, G.M[8] * dz));
+  const float Q = fmaf(u0, u0, fmaf(u1, u1, u2 * u2));
+  if (!(Q <= a.cut2)) return;
+  float qv[QS - 4];
+#pragma unroll
+  for (int v = 0; v < (QS - 4) / 4; ++v) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(qr + 4 + 4 * v));
+    qv[4 * v] = t.x; qv[4 * v + 1] = t.y; qv[4 * v + 2] = t.z; qv[4 * v + 3] = t.w;
+  }
+  float e = -0.5f * Q;
+  float pcoef = 0.0f;  // 6 t / (r' |d|), the falloff's share of dw/dmu per unit w
+  if (PSI) {
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (d2 > a.r2) {
+      const float dist = sqrtf(d2);
+      const float t = (dist - a.r) * a.inv_rr;
+      e = fmaf(-3.0f * t, t, e);
+      pcoef = 6.0f * t * a.inv_rr / dist;
+    }
+  }
+  const float w = ex2_approx(e * kLog2e);
+  const float zeta = q0.w, kappa = qv[0];
+  float gp = 0.0f;
+#pragma unroll
+  for (int c = 0; c < C; ++c) gp = fmaf(qv[1 + c], phi[c], gp);
+  const float bw = zeta * (gp - kappa) * w;
+  const float b0 = bw * u0, b1 = bw * u1, b2 = bw * u2;
+  acc.A00 = fmaf(b0, u0, acc.A00);
+  acc.A01 = fmaf(b0, u1, acc.A01);
+  acc.A02 = fmaf(b0, u2, acc.A02);
+  acc.A11 = fmaf(b1, u1, acc.A11);
+  acc.A12 = fmaf(b1, u2, acc.A12);
+  acc.A22 = fmaf(b2, u2, acc.A22);
+  acc.B0 += b0;
+  acc.B1 += b1;
+  acc.B2 += b2;
+  if (PSI) {
+    const float pc = bw * pcoef;
+    acc.D0 = fmaf(pc, dx, acc.D0);
+    acc.D1 = fmaf(pc, dy, acc.D1);
+    acc.D2 = fmaf(pc, dz, acc.D2);
+  }
+  const float wz = w * zeta;
+#pragma unroll
+  for (int c = 0; c < C; ++c) acc.P[c] = fmaf(qv[1 + c], wz, acc.P[c]);
+}
+
+// Gradients of one Gaussian from its reduced sums (runs on one lane).
+template <int C>
+__device__ void bwd_epilogue(const BwdArgs& a, int64_t gi, const Frame& fr, const Acc<C>& acc) {
+  const int64_t n = a.n;
+  const float (&R)[3][3] = fr.R;
+  const float (&s)[3] = fr.s;
+  const float qw = fr.qhat[0], qx = fr.qhat[1], qy = fr.qhat[2], qz = fr.qhat[3];
+  const float iq = fr.inv_qn;
+  const float A[3][3] = {{acc.A00, acc.A01, acc.A02}, {acc.A01, acc.A11, acc.A12},
+                         {acc.A02, acc.A12, acc.A22}};
+  const float B[3] = {acc.B0, acc.B1, acc.B2};
+  const float D[3] = {acc.D0, acc.D1, acc.D2};
+  float dmu[3], dl[3], dR[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    dmu[k] = D[k];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dmu[k] = fmaf(R[k][j] / s[j], B[j], dmu[k]);
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) dl[j] = A[j][j];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float t = 0.0f;
+#pragma unroll
+      for (int mm = 0; mm < 3; ++mm) t = fmaf(R[k][mm] * s[mm], A[j][mm], t);
+      dR[k][j] = -t / s[j];
+    }
+  // d loss / d qhat through the entries of R(qhat)
+  const float gw = 2.0f * (-qz * dR[0][1] + qy * dR[0][2] + qz * dR[1][0] - qx * dR[1][2] -
+                           qy * dR[2][0] + qx * dR[2][1]);
+  const float gx = 2.0f * (qy * dR[0][1] + qz * dR[0][2] + qy * dR[1][0] - 2.0f * qx * dR[1][1] -
+                           qw * dR[1][2] + qz * dR[2][0] + qw * dR[2][1] - 2.0f * qx * dR[2][2]);
+  const float gy = 2.0f * (-2.0f * qy * dR[0][0] + qx * dR[0][1] + qw * dR[0][2] + qx * dR[1][0] +
+                           qz * dR[1][2] - qw * dR[2][0] + qz * dR[2][1] - 2.0f * qy * dR[2][2]);
+  const float gz = 2.0f * (-2.0f * qz * dR[0][0] - qw * dR[0][1] + qx * dR[0][2] + qw * dR[1][0] -
+                           2.0f * qz * dR[1][1] + qy * dR[1][2] + qx * dR[2][0] + qy * dR[2][1]);
+  // through qhat = q / |q|
+  const float dot = qw * gw + qx * gx + qy * gy + qz * gz;
+  const float dq[4] = {(gw - qw * dot) * iq, (gx - qx * dot) * iq, (gy - qy * dot) * iq,
+                       (gz - qz * dot) * iq};
+  const bool accu = a.g.accumulate != 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float* p = a.g.mean + k * n + gi;
+    *p = accu ? *p + dmu[k] : dmu[k];
+    float* pl = a.g.logscale + k * n + gi;
+    *pl = accu ? *pl + dl[k] : dl[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float* p = a.g.quat + k * n + gi;
+    *p = accu ? *p + dq[k] : dq[k];
+  }
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    float* p = a.g.spectrum + (int64_t)c * n + gi;
+    *p = accu ? *p + acc.P[c] : acc.P[c];
+  }
+}
+
+template <int C>
+__device__ __forceinline__ void load_gaussian(const BwdArgs& a, int64_t gi, GaussianRegs& G,
+                                              float (&phi)[C]) {
+  constexpr int RS = rec_stride(C);
+  const float* r = a.rec + gi * RS;
+  const float4 r0 = *reinterpret_cast<const float4*>(r);
+  const float4 r1 = *reinterpret_cast<const float4*>(r + 4);
+  const float4 r2 = *reinterpret_cast<const float4*>(r + 8);
+  G.mx = r0.x; G.my = r0.y; G.mz = r0.z;
+  G.M[0] = r1.x; G.M[1] = r1.y; G.M[2] = r1.z; G.M[3] = r1.w;
+  G.M[4] = r2.x; G.M[5] = r2.y; G.M[6] = r2.z; G.M[7] = r2.w;
+  G.M[8] = r[12];
+#pragma unroll
+  for (int c = 0; c < C; ++c) phi[c] = r[13 + c];
+}
+
+// One lane runs one small Gaussian (bounds within 2 x 2 x 2 query-level
+// cells) alone: no reduction across lanes, the epilogues run side by side.
+template <int C, bool PSI>
+__device__ void bwd_lane_gaussian(const BwdArgs& a, int64_t gi) {
+  constexpr int QS = qrec_stride(C);
+  const Grid& Gd = a.grid;
+  GaussianRegs G;
+  float phi[C];
+  load_gaussian<C>(a, gi, G, phi);
+  const Frame fr = gaussian_frame(a.quat, a.logscale, a.n, gi);
+  const float mu[3] = {G.mx, G.my, G.mz};
+  uint32_t lo[3], hi[3];
+  gaussian_cells0(Gd, fr, mu, a.cut, lo, hi);
+  const int K = Gd.qlevel;
+  const uint32_t lx = lo[0] >> K, hx = hi[0] >> K, ly = lo[1] >> K, hy = hi[1] >> K,
+                 lz = lo[2] >> K, hz = hi[2] >> K;
+  Acc<C> acc;
+  acc.zero();
+  for (uint32_t iz = lz; iz <= hz; ++iz)
+    for (uint32_t iy = ly; iy <= hy; ++iy) {
+      const uint32_t key = qkey_of(Gd, lx, iy, iz);
+      const uint32_t e = a.qstart[key + (hx - lx) + 1];
+      for (uint32_t k = a.qstart[key]; k < e; ++k)
+        bwd_pair<C, PSI>(G, phi, a.qrec + (int64_t)k * QS, a, acc);
+    }
+  bwd_epilogue<C>(a, gi, fr, acc);
+}
+
+// Grid path. The Gaussians come in mean-cell order, the small ones first:
+// the first ceil(n_small / 32) warps give each lane one small Gaussian; every
+// later warp runs one large Gaussian over the hit points of every
+// query-level cell its k-sigma bounds overlap. Gaussians whose level box
+// holds no hit point come last and are skipped (zero gradient).
+template <int C, bool PSI>
+__global__ void __launch_bounds__(kBwdThreads)
+bwd_grid_kernel(BwdArgs a) {
+  constexpr int QS = qrec_stride(C);
+  const int lane = threadIdx.x & 31;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (a.header->overflow) return;
+  const int64_t n_small = a.header->n_small, n_live = a.header->n_live;
+  const int64_t small_warps = (n_small + kWarp - 1) / kWarp;
+  if (w < small_warps) {
+    const int64_t idx = w * kWarp + lane;
+    if (idx < n_small) bwd_lane_gaussian<C, PSI>(a, a.order[idx]);
+    return;
+  }
+  const int64_t j = n_small + (w - small_warps);
+  if (j >= n_live) return;
+  const Grid& Gd = a.grid;
+  const int64_t gi = a.order[j];
+  GaussianRegs G;
+  float phi[C];
+  load_gaussian<C>(a, gi, G, phi);
+  const Frame fr = gaussian_frame(a.quat, a.logscale, a.n, gi);
+  const float mu[3] = {G.mx, G.my, G.mz};
+  uint32_t lo[3], hi[3];
+  gaussian_cells0(Gd, fr, mu, a.cut, lo, hi);
+  const int K = Gd.qlevel;
+  const int lx = (int)(lo[0] >> K), ly = (int)(lo[1] >> K), lz = (int)(lo[2] >> K);
+  const int nx = (int)(hi[0] >> K) - lx + 1, ny = (int)(hi[1] >> K) - ly + 1,
+            nz = (int)(hi[2] >> K) - lz + 1;
+  const float cut_keep = a.cut * 1.0001f;
+  const float cellK = Gd.cell0 * (float)(1u << K);
+  const float half = 0.5f * cellK * 1.001f;
+  // the cells lx..hx of one (iy, iz) row have consecutive keys, so the row's
+  // hit points are one contiguous range of the sorted order
+  const int rows = ny * nz;
+  const bool xborder = lx == 0 || lx + nx - 1 == Gd.dx - 1;
+  const float rcx = Gd.ox + (lx + 0.5f * nx) * cellK, rhx = 0.5f * nx * cellK * 1.001f;
+  Acc<C> acc;
+  acc.zero();
+  for (int rb = 0; rb < rows; rb += kWarp) {
+    const int ri = rb + lane;
+    uint32_t qs = 0, cnt = 0;
+    if (ri < rows) {
+      const int iy = ly + ri % ny, iz = lz + ri / ny;
+      const uint32_t key = qkey_of(Gd, lx, iy, iz);
+      qs = a.qstart[key];
+      cnt = a.qstart[key + nx] - qs;
+      // border cells also hold the clamped points outside the grid: no cull
+      const bool border = xborder || iy == 0 || iz == 0 || iy == Gd.dy - 1 || iz == Gd.dz - 1;
+      if (cnt > 0 && !border) {
+        const float ccy = Gd.oy + (iy + 0.5f) * cellK;
+        const float ccz = Gd.oz + (iz + 0.5f) * cellK;
+        const float lb = mahalanobis_lower_bound(G.M, G.mx, G.my, G.mz, rcx, ccy, ccz, rhx,
+                                                 half, half);
+        if (lb > cut_keep) cnt = 0;
+      }
+    }
+    // flatten the hit points of these (up to 32) cells over the lanes
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(kFullMask, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const uint32_t tot = __shfl_sync(kFullMask, incl, 31);
+    const uint32_t excl = incl - cnt;
+    for (uint32_t f0 = 0; f0 < tot; f0 += kWarp) {
+      const uint32_t f = f0 + lane;
+      int src = 0;
+#pragma unroll
+      for (int st = 16; st > 0; st >>= 1) {
+        const uint32_t vv = __shfl_sync(kFullMask, incl, src + st - 1);
+        if (vv <= f) src += st;
+      }
+      const uint32_t qs_s = __shfl_sync(kFullMask, qs, src);
+      const uint32_t ex_s = __shfl_sync(kFullMask, excl, src);
+      if (f < tot) {
+        const int64_t k = (int64_t)qs_s + (f - ex_s);
+        bwd_pair<C, PSI>(G, phi, a.qrec + k * QS, a, acc);
+      }
+    }
+  }
+  acc.warp_sum();
+  if (lane == 0) bwd_epilogue<C>(a, gi, fr, acc);
+}
+
+// Brute-force path (no cell lists): one warp per Gaussian over all active hit points.
+template <int C, bool PSI>
+__global__ void __launch_bounds__(kBwdThreads)
+bwd_brute_kernel(BwdArgs a) {
+  constexpr int QS = qrec_stride(C);
+  const int lane = threadIdx.x & 31;
+  const int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gi >= a.n) return;
+  const int64_t n_act = a.header->n_active;
+  GaussianRegs G;
+  float phi[C];
+  load_gaussian<C>(a, gi, G, phi);
+  Acc<C> acc;
+  acc.zero();
+  for (int64_t k = lane; k < n_act; k += kWarp) bwd_pair<C, PSI>(G, phi, a.qrec + k * QS, a, acc);
+  acc.warp_sum();
+  if (lane == 0) {
+    const Frame fr = gaussian_frame(a.quat, a.logscale, a.n, gi);
+    bwd_epilogue<C>(a, gi, fr, acc);
+  }
+}
+
+template <int C>
+cudaError_t launch_c(const BwdArgs& a, const IndexDims& d, bool psi, cudaStream_t stream) {
+  const unsigned pblocks = (unsigned)((a.m + 255) / 256);
+  pack_qrec_kernel<C><<<pblocks, 256, 0, stream>>>(a);
+  note_launches(1);
+  if (a.n == 0) return cudaGetLastError();
+  // brute force: a warp per Gaussian; grid: up to n / 32 lane warps + n warps
+  const int64_t warps = d.brute ? a.n : a.n + (a.n + kWarp - 1) / kWarp;
+  const unsigned blocks = (unsigned)((warps + kBwdWarps - 1) / kBwdWarps);
+  if (d.brute) {
+    if (psi) bwd_brute_kernel<C, true><<<blocks, kBwdThreads, 0, stream>>>(a);
+    else bwd_brute_kernel<C, false><<<blocks, kBwdThreads, 0, stream>>>(a);
+  } else {
+    if (psi) bwd_grid_kernel<C, true><<<blocks, kBwdThreads, 0, stream>>>(a);
+    else bwd_grid_kernel<C, false><<<blocks, kBwdThreads, 0, stream>>>(a);
+  }
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_backward(const IndexDims& d, const IndexBuffers& b, const gpf_field& f,
+                            const gpf_queries& q, const gpf_query_params& p,
+                            const float* grad_out, const float* out, const float* z,
+                            const gpf_field_grad& g, cudaStream_t stream) {
+  const int64_t n = f.n;
+  if (!g.accumulate && n > 0) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(g.mean, 0, sizeof(float) * 3 * n, stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(g.quat, 0, sizeof(float) * 4 * n, stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(g.logscale, 0, sizeof(float) * 3 * n, stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(g.spectrum, 0, sizeof(float) * d.channels * n, stream)) != cudaSuccess)
+      return e;
+  }
+  if (q.m == 0 || n == 0) return cudaGetLastError();
+  BwdArgs a;
+  a.grid = d.grid;
+  a.header = b.header;
+  a.qval = b.qval[b.qsorted];
+  a.qstart = b.qstart;
+  a.x = q.x;
+  a.albedo = q.albedo;
+  a.grad_out = grad_out;
+  a.out = out;
+  a.z = z;
+  a.m = q.m;
+  a.qrec = b.qrec;
+  a.rec = b.rec;
+  a.box = b.box;
+  a.order = b.oval[b.osorted];
+  a.n = n;
+  a.quat = f.quat;
+  a.logscale = f.logscale;
+  a.mode = p.mode;
+  const bool psi = isfinite(p.r_max);
+  a.r = psi ? p.r_max : 0.0f;
+  a.r2 = psi ? p.r_max * p.r_max : 0.0f;
+  a.inv_rr = psi ? 1.0f / fmaxf(p.r_max, 1e-6f) : 0.0f;
+  a.eps = p.eps;
+  a.cut = d.cutoff;
+  a.cut2 = isinf(d.cutoff) ? INFINITY : d.cutoff * d.cutoff;
+  a.g = g;
+  switch (d.channels) {
+    case 1: return launch_c<1>(a, d, psi, stream);
+    case 2: return launch_c<2>(a, d, psi, stream);
+    case 3: return launch_c<3>(a, d, psi, stream);
+    case 4: return launch_c<4>(a, d, psi, stream);
+    case 5: return launch_c<5>(a, d, psi, stream);
+    case 6: return launch_c<6>(a, d, psi, stream);
+    case 7: return launch_c<7>(a, d, psi, stream);
+    case 8: return launch_c<8>(a, d, psi, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace gpf

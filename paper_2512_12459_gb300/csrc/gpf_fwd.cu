@@ -1,0 +1,384 @@
+// gpf_radiance_fwd: radiance at hit points (Sec. 3.2, aggregation equation;
+// the soft falloff and soft normalisation of the supplementary query listing).
+//
+// One warp per tile of 32 consecutive hit points in cell-sorted order. For
+// every grid level that holds Gaussians, the lanes find their cell on that
+// level and group equal cells (__match_any_sync):
+//   * few distinct cells (the Gaussians of this level are large next to the
+//     tile): warp-cooperative mode. The lanes walk the lists of those cells
+//     together, 32 entries at a time; each lane vets one candidate (it belongs
+//     to this level and cell, it was not already taken from an earlier cell of
+//     the tile, and neither its bounding sphere nor a lower bound of its
+//     Mahalanobis distance rules out the tile's box of hit points). Survivors
+//     are staged in shared memory and every lane evaluates all of them.
+//   * many distinct cells (the Gaussians are small next to the spacing of the
+//     hit points): per-lane mode. Each lane walks its own cell's list.
+// Every lane applies the exact predicate Q <= k^2, so the result equals the
+// brute-force sum over {i : Q_i <= k^2}. With no cell lists (k = +INF or
+// brute force) the candidates are all Gaussians, in index order.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "gpf_internal.h"
+
+namespace gpf {
+
+namespace {
+
+constexpr int kFwdWarps = 8;
+constexpr int kFwdThreads = kFwdWarps * kWarp;
+// A tile whose hit points fall in at most this many cells of a level walks
+// that level cooperatively.
+constexpr int kUnionMax = 4;
+
+struct FwdArgs {
+  Grid grid;
+  const uint32_t* qkey;    // sorted query-level keys of hit points
+  const uint32_t* qval;    // sorted hit point ids
+  const DeviceHeader* header;
+  const float* x;          // [3,M]
+  const float* albedo;     // [C,M] or null
+  int64_t m;
+  const float* rec;
+  const uint4* box;
+  const uint2* brange;     // [n_buckets] [start, end) of each bucket's list
+  const uint32_t* gval;    // sorted entries (Gaussian ids)
+  int64_t n;               // Gaussians (brute force)
+  int mode;
+  float r, r2, inv_rr;     // falloff radius, its square, 1/max(r, 1e-6)
+  float eps;
+  float cut, cut2;         // k, k^2
+  float* out;              // [C,M]
+  float* z;                // [M] or null
+  unsigned long long* counts;  // count mode: [candidates, included]
+};
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFullMask, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFullMask, v, o));
+  return v;
+}
+
+// Accumulate one Gaussian record r into this lane's sums (or count it).
+template <int C, bool PSI, bool COUNT>
+__device__ __forceinline__ void eval_pair(const float* __restrict__ r, float px, float py, float pz,
+                                          const FwdArgs& a, float (&L)[C], float& Z,
+                                          uint32_t& n_eval, uint32_t& n_inc) {
+  const float dx = px - r[0], dy = py - r[1], dz = pz - r[2];
+  const float u0 = fmaf(r[4], dx, fmaf(r[5], dy, r[6] * dz));
+  const float u1 = fmaf(r[7], dx, fmaf(r[8], dy, r[9] * dz));
+  const float u2 = fmaf(r[10], dx, fmaf(r[11], dy, r[12] * dz));
+  const float Q = fmaf(u0, u0, fmaf(u1, u1, u2 * u2));
+  if (COUNT) {
+    ++n_eval;
+    n_inc += Q <= a.cut2 ? 1u : 0u;
+    return;
+  }
+  if (Q <= a.cut2) {
+    float e = -0.5f * Q;
+    if (PSI) {
+      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      if (d2 > a.r2) {
+        // correctly rounded: the exponent's sensitivity to |d| is 6 t (t + 1) / |d|
+        const float dist = sqrtf(d2);
+        const float t = (dist - a.r) * a.inv_rr;
+        e = fmaf(-3.0f * t, t, e);
+      }
+    }
+    const float w = ex2_approx(e * kLog2e);
+#pragma unroll
+    for (int c = 0; c < C; ++c) L[c] = fmaf(w, r[13 + c], L[c]);
+    Z += w;
+  }
+}
+
+template <int RS>
+__device__ __forceinline__ void load_rec(const float* __restrict__ rec, uint32_t g, float (&r)[RS]) {
+  const float4* src = reinterpret_cast<const float4*>(rec + (int64_t)g * RS);
+#pragma unroll
+  for (int v = 0; v < RS / 4; ++v) {
+    const float4 t = __ldg(src + v);
+    r[4 * v] = t.x; r[4 * v + 1] = t.y; r[4 * v + 2] = t.z; r[4 * v + 3] = t.w;
+  }
+}
+
+// COUNT: count the evaluated and included pairs instead of summing radiance.
+template <int C, bool BRUTE, bool PSI, bool COUNT>
+__global__ void __launch_bounds__(kFwdThreads)
+fwd_kernel(FwdArgs a) {
+  constexpr int RS = rec_stride(C);
+  __shared__ __align__(16) float s_rec[kFwdWarps][kWarp * RS];
+  __shared__ unsigned long long s_cell[kFwdWarps][kWarp];
+
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t tile = (int64_t)blockIdx.x * kFwdWarps + wib;
+  const int64_t base = tile * kWarp;
+  if (base >= a.m) return;
+  if (a.header->overflow) return;
+  const int64_t n_act = a.header->n_active;
+  const int64_t k = base + lane;
+  const bool in_range = k < a.m;
+  const bool active = k < n_act;
+  const uint32_t q = in_range ? a.qval[k] : 0u;
+  if (!COUNT && in_range && !active) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) a.out[(int64_t)c * a.m + q] = 0.0f;
+    if (a.z) a.z[q] = 0.0f;
+  }
+  if (base >= n_act) return;  // warp-uniform
+
+  float px = 0.f, py = 0.f, pz = 0.f;
+  if (active) {
+    px = a.x[q];
+    py = a.x[a.m + q];
+    pz = a.x[2 * a.m + q];
+  }
+  float L[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) L[c] = 0.0f;
+  float Z = 0.0f;
+  uint32_t n_eval = 0, n_inc = 0;
+  float* my_rec = s_rec[wib];
+
+  if (BRUTE) {
+    for (int64_t g0 = 0; g0 < a.n; g0 += kWarp) {
+      const int64_t g = g0 + lane;
+      const int cnt = (int)min((int64_t)kWarp, a.n - g0);
+      if (g < a.n) {
+        const float4* src = reinterpret_cast<const float4*>(a.rec + g * RS);
+        float4* dst = reinterpret_cast<float4*>(my_rec + lane * RS);
+#pragma unroll
+        for (int v = 0; v < RS / 4; ++v) dst[v] = src[v];
+      }
+      __syncwarp();
+      if (active)
+        for (int s = 0; s < cnt; ++s)
+          eval_pair<C, PSI, COUNT>(my_rec + s * RS, px, py, pz, a, L, Z, n_eval, n_inc);
+      __syncwarp();
+    }
+  } else {
+    const Grid& G = a.grid;
+    const uint32_t c0x = coord0(px, G.ox, G.inv_cell0, G.max0x);
+    const uint32_t c0y = coord0(py, G.oy, G.inv_cell0, G.max0y);
+    const uint32_t c0z = coord0(pz, G.oz, G.inv_cell0, G.max0z);
+    // tile box of the active hit points
+    const float bx0 = warp_min(active ? px : INFINITY), bx1 = warp_max(active ? px : -INFINITY);
+    const float by0 = warp_min(active ? py : INFINITY), by1 = warp_max(active ? py : -INFINITY);
+    const float bz0 = warp_min(active ? pz : INFINITY), bz1 = warp_max(active ? pz : -INFINITY);
+    const float cx = 0.5f * (bx0 + bx1), cy = 0.5f * (by0 + by1), cz = 0.5f * (bz0 + bz1);
+    const float hx = 0.5f * (bx1 - bx0), hy = 0.5f * (by1 - by0), hz = 0.5f * (bz1 - bz0);
+    const float cut_keep = a.cut * 1.0001f;
+    const uint32_t lmask = a.header->level_mask;
+
+    for (int lev = 0; lev < G.levels; ++lev) {
+      if (!((lmask >> lev) & 1u)) continue;
+      const uint32_t lx = c0x >> lev, ly = c0y >> lev, lz = c0z >> lev;
+      const unsigned long long packed =
+          active ? ((unsigned long long)lx | ((unsigned long long)ly << 20) |
+                    ((unsigned long long)lz << 40))
+                 : ~0ull;
+      const uint32_t peers = __match_any_sync(kFullMask, packed);
+      const bool leader = active && (peers & lanemask_lt()) == 0;
+      const uint32_t uniq = __ballot_sync(kFullMask, leader);
+      const int nu = __popc(uniq);
+      if (nu <= kUnionMax) {
+        // ---- warp-cooperative mode over the tile's distinct cells
+        if (leader) s_cell[wib][__popc(uniq & lanemask_lt())] = packed;
+        __syncwarp();
+        for (int j = 0; j < nu; ++j) {
+          const unsigned long long cj = s_cell[wib][j];
+          const uint32_t ux = (uint32_t)(cj & kCoordMax), uy = (uint32_t)((cj >> 20) & kCoordMax),
+                         uz = (uint32_t)((cj >> 40) & kCoordMax);
+          const CellHash h = cell_hash(G, lev, ux, uy, uz);
+          const uint2 rg = a.brange[h.bucket];
+          for (uint32_t e0 = rg.x; e0 < rg.y; e0 += kWarp) {
+            const uint32_t e = e0 + lane;
+            bool keep = false;
+            uint32_t g = 0;
+            if (e < rg.y) {
+              const uint32_t v = __ldg(a.gval + e);
+              g = v & G.id_mask;
+              // the tag tells this cell's entries from other cells' in the
+              // bucket; a Gaussian listed twice sits on consecutive entries
+              keep = (v & ~G.id_mask) == h.tag && !(e > rg.x && __ldg(a.gval + e - 1) == v);
+              if (keep) {
+                const uint4 bw = __ldg(a.box + g);
+                const float4* src = reinterpret_cast<const float4*>(a.rec + (int64_t)g * RS);
+                const float4 r0 = __ldg(src), r1 = __ldg(src + 1), r2 = __ldg(src + 2),
+                             r3 = __ldg(src + 3);
+                const LevelBox b = unpack_box(bw);
+                // it must live on this level and cover this cell, and must not
+                // have been taken from an earlier cell of this tile
+                keep = b.level == lev && box_holds(b, ux, uy, uz);
+                for (int jj = 0; jj < j && keep; ++jj) {
+                  const unsigned long long ci = s_cell[wib][jj];
+                  keep = !box_holds(b, (uint32_t)(ci & kCoordMax),
+                                    (uint32_t)((ci >> 20) & kCoordMax),
+                                    (uint32_t)((ci >> 40) & kCoordMax));
+                }
+                if (keep) {
+                  // sphere test: distance from mu to the tile box vs k * max s
+                  const float ex = fmaxf(fmaxf(bx0 - r0.x, r0.x - bx1), 0.0f);
+                  const float ey = fmaxf(fmaxf(by0 - r0.y, r0.y - by1), 0.0f);
+                  const float ez = fmaxf(fmaxf(bz0 - r0.z, r0.z - bz1), 0.0f);
+                  keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= r0.w * r0.w;
+                }
+                if (keep) {
+                  const float Mr[9] = {r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w, r3.x};
+                  keep = mahalanobis_lower_bound(Mr, r0.x, r0.y, r0.z, cx, cy, cz, hx, hy, hz) <=
+                         cut_keep;
+                }
+              }
+            }
+            const uint32_t kb = __ballot_sync(kFullMask, keep);
+            if (keep) {
+              const float4* src = reinterpret_cast<const float4*>(a.rec + (int64_t)g * RS);
+              float4* dst = reinterpret_cast<float4*>(my_rec + __popc(kb & lanemask_lt()) * RS);
+#pragma unroll
+              for (int v = 0; v < RS / 4; ++v) dst[v] = __ldg(src + v);
+            }
+            __syncwarp();
+            const int nk = __popc(kb);
+            if (active)
+              for (int s = 0; s < nk; ++s)
+                eval_pair<C, PSI, COUNT>(my_rec + s * RS, px, py, pz, a, L, Z, n_eval, n_inc);
+            __syncwarp();
+          }
+        }
+      } else if (active) {
+        // ---- per-lane mode: each lane walks its own cell's list, four
+        // entries at a time so that their loads are in flight together
+        const CellHash h = cell_hash(G, lev, lx, ly, lz);
+        const uint2 rg = a.brange[h.bucket];
+        uint32_t prev = rg.x > 0 ? __ldg(a.gval + rg.x - 1) : 0u;
+        for (uint32_t e = rg.x; e < rg.y; e += 4) {
+          uint32_t v[4];
+          bool ok[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = e + u < rg.y ? __ldg(a.gval + e + u) : 0u;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            ok[u] = e + u < rg.y && (v[u] & ~G.id_mask) == h.tag &&
+                    v[u] != (u == 0 ? (e > rg.x ? prev : ~v[0]) : v[u - 1]);
+          }
+          prev = v[3];
+          uint4 bw[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (ok[u]) bw[u] = __ldg(a.box + (v[u] & G.id_mask));
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (!ok[u]) continue;
+            const LevelBox b = unpack_box(bw[u]);
+            if (b.level != lev || !box_holds(b, lx, ly, lz)) continue;
+            float rr[RS];
+            load_rec<RS>(a.rec, v[u] & G.id_mask, rr);
+            eval_pair<C, PSI, COUNT>(rr, px, py, pz, a, L, Z, n_eval, n_inc);
+          }
+        }
+      }
+    }
+  }
+
+  if (COUNT) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      n_eval += __shfl_xor_sync(kFullMask, n_eval, o);
+      n_inc += __shfl_xor_sync(kFullMask, n_inc, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&a.counts[0], (unsigned long long)n_eval);
+      atomicAdd(&a.counts[1], (unsigned long long)n_inc);
+    }
+    return;
+  }
+  if (active) {
+    float scale = 1.0f;
+    if (a.mode == GPF_NORMALIZED) scale = 1.0f / fmaxf(Z, a.eps);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const float rho = a.albedo ? a.albedo[(int64_t)c * a.m + q] : 1.0f;
+      a.out[(int64_t)c * a.m + q] = rho * (L[c] * scale);
+    }
+    if (a.z) a.z[q] = Z;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_forward(const IndexDims& d, const IndexBuffers& b, const gpf_queries& q,
+                           const gpf_query_params& p, int64_t n, float* out, float* z,
+                           unsigned long long* counts, cudaStream_t stream) {
+  if (counts) {
+    cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return e;
+  }
+  if (q.m == 0) return cudaSuccess;
+  FwdArgs a;
+  a.grid = d.grid;
+  a.qkey = b.qkey[b.qsorted];
+  a.qval = b.qval[b.qsorted];
+  a.header = b.header;
+  a.x = q.x;
+  a.albedo = q.albedo;
+  a.m = q.m;
+  a.rec = b.rec;
+  a.box = b.box;
+  a.brange = b.brange;
+  a.gval = b.gval[b.gsorted];
+  a.n = n;
+  a.mode = p.mode;
+  const bool psi = isfinite(p.r_max);
+  a.r = psi ? p.r_max : 0.0f;
+  a.r2 = psi ? p.r_max * p.r_max : 0.0f;
+  a.inv_rr = psi ? 1.0f / fmaxf(p.r_max, 1e-6f) : 0.0f;
+  a.eps = p.eps;
+  a.cut = d.cutoff;
+  a.cut2 = isinf(d.cutoff) ? INFINITY : d.cutoff * d.cutoff;
+  a.out = out;
+  a.z = z;
+  a.counts = counts;
+  const int64_t tiles = (q.m + kWarp - 1) / kWarp;
+  const unsigned blocks = (unsigned)((tiles + kFwdWarps - 1) / kFwdWarps);
+#define GPF_FWD_LAUNCH(CC, BR, PS, CN) fwd_kernel<CC, BR, PS, CN><<<blocks, kFwdThreads, 0, stream>>>(a)
+#define GPF_FWD_MODES(CC, BR, PS)                   \
+  do {                                              \
+    if (counts) GPF_FWD_LAUNCH(CC, BR, false, true); \
+    else GPF_FWD_LAUNCH(CC, BR, PS, false);         \
+  } while (0)
+#define GPF_FWD_CASE(CC)                                                   \
+  case CC:                                                                 \
+    if (d.brute) {                                                         \
+      if (psi) GPF_FWD_MODES(CC, true, true);                              \
+      else GPF_FWD_MODES(CC, true, false);                                 \
+    } else {                                                               \
+      if (psi) GPF_FWD_MODES(CC, false, true);                             \
+      else GPF_FWD_MODES(CC, false, false);                                \
+    }                                                                      \
+    note_launches(1);                                                      \
+    break;
+  switch (d.channels) {
+    GPF_FWD_CASE(1)
+    GPF_FWD_CASE(2)
+    GPF_FWD_CASE(3)
+    GPF_FWD_CASE(4)
+    GPF_FWD_CASE(5)
+    GPF_FWD_CASE(6)
+    GPF_FWD_CASE(7)
+    GPF_FWD_CASE(8)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef GPF_FWD_CASE
+#undef GPF_FWD_MODES
+#undef GPF_FWD_LAUNCH
+  return cudaGetLastError();
+}
+
+}  // namespace gpf

@@ -1,0 +1,280 @@
+// gpf_build_index on a multi-level hashed grid.
+//
+// Level L has cubic cells of edge c0 * 2^L. Each Gaussian lives on the finest
+// level on which its k-sigma bounds span at most S cells per axis, and is
+// listed in the (level, cell) bucket of every cell of that box that holds a
+// hit point. Lists of all levels share one array of 2^hash_bits buckets,
+// radix-sorted by bucket (stable, so a list's order is deterministic).
+// Hit points are sorted by their cell on the query level K (dense linear
+// keys), which orders the forward's tiles and gives the backward the hit
+// points of any query-level cell. Gaussians are also sorted by the
+// query-level cell of their mean, the order the backward walks them in.
+//
+// Kernels, in stream order:
+//   preprocess (records, level boxes, level mask, mean keys)
+//   query_keys (hit point keys, occupancy bits of the used levels)
+//   sort hit points, per-cell starts
+//   count entries (Gaussians without any leave the backward's order)
+//   sort Gaussians by mean cell
+//   scan -> emit (bucket, Gaussian) entries -> sort -> bucket starts
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "gpf_internal.h"
+
+namespace gpf {
+
+namespace {
+
+constexpr int kThreads = 256;
+// Boxes with more cells than this on their level are refused (overflow flag).
+constexpr int64_t kMaxBoxCells = int64_t(1) << 16;
+constexpr uint32_t kNoBox = 0xffffffffu;
+
+__global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brute,
+                                  float* __restrict__ rec, int rs, uint4* __restrict__ box,
+                                  uint32_t* __restrict__ okey, uint32_t* __restrict__ oval,
+                                  DeviceHeader* header) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = f.n;
+  uint32_t level_bit = 0;
+  if (g < n) {
+    const float mu[3] = {f.mean[g], f.mean[n + g], f.mean[2 * n + g]};
+    const Frame fr = gaussian_frame(f.quat, f.logscale, n, g);
+    float* r = rec + g * rs;
+    const float smax = fmaxf(fr.s[0], fmaxf(fr.s[1], fr.s[2]));
+    r[0] = mu[0]; r[1] = mu[1]; r[2] = mu[2];
+    // bounding sphere of the k-sigma ellipsoid, widened by 1e-4 for rounding
+    r[3] = isinf(cutoff) ? INFINITY : cutoff * smax * 1.0001f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float inv = 1.0f / fr.s[j];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) r[4 + 3 * j + k] = fr.R[k][j] * inv;
+    }
+    for (int c = 0; c < f.channels; ++c) r[13 + c] = f.spectrum[(int64_t)c * n + g];
+    for (int c = 13 + f.channels; c < rs; ++c) r[c] = 0.0f;
+    // the order the backward walks Gaussians in: class (0 = bounds within
+    // 2 x 2 x 2 query-level cells, 1 = larger; dead ones get 2 later), then
+    // the query-level cell of the mean
+    const int K = grid.qlevel;
+    const uint32_t mkey = qkey_of(grid, coord0(mu[0], grid.ox, grid.inv_cell0, grid.max0x) >> K,
+                                  coord0(mu[1], grid.oy, grid.inv_cell0, grid.max0y) >> K,
+                                  coord0(mu[2], grid.oz, grid.inv_cell0, grid.max0z) >> K);
+    okey[g] = mkey | (1u << grid.key_bits);
+    oval[g] = (uint32_t)g;
+    if (!brute) {
+      uint32_t lo[3], hi[3];
+      gaussian_cells0(grid, fr, mu, cutoff, lo, hi);
+      if ((hi[0] >> K) - (lo[0] >> K) <= 1 && (hi[1] >> K) - (lo[1] >> K) <= 1 &&
+          (hi[2] >> K) - (lo[2] >> K) <= 1)
+        okey[g] = mkey;
+      int L = 0;
+      for (; L < grid.levels - 1; ++L) {
+        const uint32_t sx = (hi[0] >> L) - (lo[0] >> L), sy = (hi[1] >> L) - (lo[1] >> L),
+                       sz = (hi[2] >> L) - (lo[2] >> L);
+        if (max(sx, max(sy, sz)) < (uint32_t)grid.max_span) break;
+      }
+      const uint32_t lx = lo[0] >> L, ly = lo[1] >> L, lz = lo[2] >> L;
+      const uint32_t sx = (hi[0] >> L) - lx, sy = (hi[1] >> L) - ly, sz = (hi[2] >> L) - lz;
+      const int64_t vol = (int64_t)(sx + 1) * (sy + 1) * (sz + 1);
+      if (sx > 255 || sy > 255 || sz > 255 || vol > kMaxBoxCells) {
+        box[g] = make_uint4(kNoBox, kNoBox, kNoBox, 0);
+        atomicExch(&header->overflow, 1u);
+      } else {
+        box[g] = make_uint4(lx | ((uint32_t)L << 20), ly, lz, sx | (sy << 8) | (sz << 16));
+        level_bit = 1u << L;
+      }
+    }
+  }
+  const uint32_t m = __reduce_or_sync(kFullMask, level_bit);
+  if ((threadIdx.x & 31) == 0 && m) atomicOr(&header->level_mask, m);
+}
+
+__global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
+                                  const float* __restrict__ nrm, const float* __restrict__ wo,
+                                  const uint8_t* __restrict__ valid, int64_t m,
+                                  uint32_t* __restrict__ key, uint32_t* __restrict__ val,
+                                  uint32_t* __restrict__ occ, int mark,
+                                  uint32_t* __restrict__ qcount, DeviceHeader* header) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool active = false;
+  if (i < m) {
+    // hemisphere gate n . w_o > 0, summed in float64 in a fixed order (the
+    // three products of float32 values are exact in float64)
+    double d = __dadd_rn(__dadd_rn(__dmul_rn((double)nrm[i], (double)wo[i]),
+                                   __dmul_rn((double)nrm[m + i], (double)wo[m + i])),
+                         __dmul_rn((double)nrm[2 * m + i], (double)wo[2 * m + i]));
+    active = d > 0.0 && (valid == nullptr || valid[i] != 0);
+    uint32_t k = grid.key_inactive;
+    if (active) {
+      const uint32_t cx = coord0(x[i], grid.ox, grid.inv_cell0, grid.max0x);
+      const uint32_t cy = coord0(x[m + i], grid.oy, grid.inv_cell0, grid.max0y);
+      const uint32_t cz = coord0(x[2 * m + i], grid.oz, grid.inv_cell0, grid.max0z);
+      const int K = grid.qlevel;
+      k = qkey_of(grid, cx >> K, cy >> K, cz >> K);
+      atomicAdd(&qcount[k], 1u);
+      if (mark) {
+        const uint32_t lm = header->level_mask;
+        for (int L = 0; L < grid.levels; ++L) {
+          if (!((lm >> L) & 1u)) continue;
+          const uint32_t b = bucket_of(grid, L, cx >> L, cy >> L, cz >> L);
+          const uint32_t bit = 1u << (b & 31u);
+          if (!(occ[b >> 5] & bit)) atomicOr(&occ[b >> 5], bit);
+        }
+      }
+    }
+    key[i] = k;
+    val[i] = (uint32_t)i;
+  }
+  const uint32_t ballot = __ballot_sync(kFullMask, active);
+  if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(&header->n_active, __popc(ballot));
+}
+
+__device__ __forceinline__ bool occupied(const uint32_t* occ, uint32_t b) {
+  return (occ[b >> 5] >> (b & 31u)) & 1u;
+}
+
+// EMIT = false: count the occupied cells of every Gaussian's level box;
+// EMIT = true: write one (bucket, Gaussian) entry per occupied cell, in the
+// box's cell order (a Gaussian whose cells share a bucket appears there on
+// consecutive entries; the pair loops take only the first).
+// Counting also retires the Gaussians without entries from the backward's
+// order (their mean key becomes the inactive key) and counts the others.
+template <bool EMIT>
+__global__ void entries_kernel(Grid grid, int64_t n, int64_t p_max, const uint4* __restrict__ box,
+                               const uint32_t* __restrict__ occ, uint32_t* __restrict__ gcount,
+                               const uint32_t* __restrict__ goffset, uint32_t* __restrict__ gkey,
+                               uint32_t* __restrict__ gval, uint32_t* __restrict__ okey,
+                               DeviceHeader* header) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (EMIT && g == 0 && (int64_t)header->n_pairs > p_max) atomicExch(&header->overflow, 1u);
+  if (!EMIT) {
+    bool live = false, small = false;
+    if (g < n) {
+      const uint4 bw = box[g];
+      uint32_t cnt = 0;
+      if (bw.x != kNoBox) {
+        const LevelBox b = unpack_box(bw);
+        for (uint32_t iz = b.lz; iz <= b.hz; ++iz)
+          for (uint32_t iy = b.ly; iy <= b.hy; ++iy)
+            for (uint32_t ix = b.lx; ix <= b.hx; ++ix)
+              cnt += occupied(occ, bucket_of(grid, b.level, ix, iy, iz)) ? 1u : 0u;
+      }
+      gcount[g] = cnt;
+      live = cnt > 0;
+      if (!live) okey[g] = 2u << grid.key_bits;
+      small = live && (okey[g] >> grid.key_bits) == 0;
+    }
+    const uint32_t ballot = __ballot_sync(kFullMask, live);
+    const uint32_t bsmall = __ballot_sync(kFullMask, small);
+    if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(&header->n_live, __popc(ballot));
+    if ((threadIdx.x & 31) == 0 && bsmall) atomicAdd(&header->n_small, __popc(bsmall));
+    return;
+  }
+  if (g >= n) return;
+  const uint4 bw = box[g];
+  if (bw.x == kNoBox) return;
+  const LevelBox b = unpack_box(bw);
+  int64_t pos = goffset[g];
+  for (uint32_t iz = b.lz; iz <= b.hz; ++iz)
+    for (uint32_t iy = b.ly; iy <= b.hy; ++iy)
+      for (uint32_t ix = b.lx; ix <= b.hx; ++ix) {
+        const CellHash h = cell_hash(grid, b.level, ix, iy, iz);
+        if (!occupied(occ, h.bucket)) continue;
+        if (pos < p_max) {
+          gkey[pos] = h.bucket;
+          gval[pos] = (uint32_t)g | h.tag;
+        }
+        ++pos;
+      }
+}
+
+// [start, end) of every non-empty bucket from the boundaries of the sorted
+// keys (the other buckets keep the [0, 0) of the memset).
+__global__ void bucket_range_kernel(const uint32_t* __restrict__ keys, const uint32_t* d_n,
+                                    int64_t n_cap, uint2* __restrict__ range) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t n = *d_n;
+  if (n > n_cap) n = n_cap;
+  if (i >= n) return;
+  const uint32_t k = keys[i];
+  if (i == 0 || keys[i - 1] != k) range[k].x = (uint32_t)i;
+  if (i == n - 1 || keys[i + 1] != k) range[k].y = (uint32_t)(i + 1);
+}
+
+inline unsigned blocks_for(int64_t n, int t = kThreads) {
+  return (unsigned)((n + t - 1) / t);
+}
+
+}  // namespace
+
+cudaError_t launch_build(const IndexDims& d, const IndexBuffers& b, const gpf_field& f,
+                         const gpf_queries& q, cudaStream_t stream) {
+  const Grid& grid = d.grid;
+  cudaError_t e = cudaMemsetAsync(b.header, 0, sizeof(DeviceHeader), stream);
+  if (e != cudaSuccess) return e;
+  if (!d.brute) {
+    e = cudaMemsetAsync(b.occ, 0, sizeof(uint32_t) * ((grid.n_buckets + 31) / 32), stream);
+    if (e != cudaSuccess) return e;
+  }
+  // hit points per query-level cell, counted by the key pass
+  e = cudaMemsetAsync(b.qstart, 0, sizeof(uint32_t) * ((size_t)grid.n_keys + 2), stream);
+  if (e != cudaSuccess) return e;
+  // 1. Gaussian records, level boxes, level mask
+  if (f.n > 0) {
+    preprocess_kernel<<<blocks_for(f.n), kThreads, 0, stream>>>(
+        f, grid, d.cutoff, d.brute ? 1 : 0, b.rec, rec_stride(d.channels), b.box, b.okey[0],
+        b.oval[0], b.header);
+    note_launches(1);
+  }
+  // 2. hit point keys and occupancy of the used levels
+  if (q.m > 0) {
+    query_keys_kernel<<<blocks_for(q.m), kThreads, 0, stream>>>(
+        grid, q.x, q.normal, q.wo, q.valid, q.m, b.qkey[0], b.qval[0], b.occ, d.brute ? 0 : 1,
+        b.qstart, b.header);
+    note_launches(1);
+  }
+  // 3. hit points sorted by query-level cell (inactive ones last), cell starts
+  e = radix_sort_pairs(b.qkey[0], b.qval[0], b.qkey[1], b.qval[1], q.m, nullptr, grid.key_bits,
+                       b.qsort_ws, stream);
+  if (e != cudaSuccess) return e;
+  // cell starts: exclusive scan of the counts (inactive points come last)
+  e = exclusive_scan_u32(b.qstart, b.qstart, (int64_t)grid.n_keys + 2, nullptr, b.scan_ws,
+                         stream);
+  if (e != cudaSuccess) return e;
+  // 4. entry counts (Gaussians without any retire from the backward's order),
+  //    then Gaussians sorted by the query-level cell of their mean
+  if (!d.brute && f.n > 0) {
+    entries_kernel<false><<<blocks_for(f.n), kThreads, 0, stream>>>(
+        grid, f.n, d.p_max, b.box, b.occ, b.gcount, nullptr, nullptr, nullptr, b.okey[0],
+        b.header);
+    note_launches(1);
+  }
+  e = radix_sort_pairs(b.okey[0], b.oval[0], b.okey[1], b.oval[1], f.n, nullptr,
+                       grid.key_bits + 2, b.osort_ws, stream);
+  if (e != cudaSuccess) return e;
+  if (d.brute || f.n == 0) return cudaGetLastError();
+  // 5. (bucket, Gaussian) entries: scan, emit, sort, bucket starts
+  e = exclusive_scan_u32(b.gcount, b.goffset, f.n, &b.header->n_pairs, b.scan_ws, stream);
+  if (e != cudaSuccess) return e;
+  entries_kernel<true><<<blocks_for(f.n), kThreads, 0, stream>>>(
+      grid, f.n, d.p_max, b.box, b.occ, b.gcount, b.goffset, b.gkey[0], b.gval[0], nullptr,
+      b.header);
+  note_launches(1);
+  e = radix_sort_pairs(b.gkey[0], b.gval[0], b.gkey[1], b.gval[1], d.p_max, &b.header->n_pairs,
+                       grid.hash_bits, b.gsort_ws, stream);
+  if (e != cudaSuccess) return e;
+  // bucket ranges from the boundaries of the sorted keys
+  e = cudaMemsetAsync(b.brange, 0, sizeof(uint2) * (size_t)grid.n_buckets, stream);
+  if (e != cudaSuccess) return e;
+  if (d.p_max > 0) {
+    bucket_range_kernel<<<blocks_for(d.p_max), kThreads, 0, stream>>>(
+        b.gkey[b.gsorted], &b.header->n_pairs, d.p_max, b.brange);
+    note_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace gpf

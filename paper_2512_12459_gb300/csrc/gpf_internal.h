@@ -1,0 +1,86 @@
+// Internal interfaces between the C ABI layer and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "gpf_common.cuh"
+
+namespace gpf {
+
+inline size_t align_up(size_t b, size_t a = 256) { return (b + a - 1) / a * a; }
+
+// Host-side count of the kernels this library has launched (gpf_launch_count).
+void note_launches(uint64_t k);
+
+// ---- scan / sort (gpf_sort.cu)
+int64_t scan_partials_count(int64_t n);
+size_t scan_workspace_bytes(int64_t n_max);
+// out[i] = sum_{j<i} in[j] for i < n (host-known n); *total_out = sum (device, may be null).
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_out,
+                               void* ws, cudaStream_t stream);
+int64_t radix_tiles(int64_t n_max);
+size_t radix_sort_workspace_bytes(int64_t n_max);
+int radix_sort_passes(int bits);
+// Stable sort of min(*d_n, n_max) pairs (n_max pairs when d_n is null) by
+// key bits [0, bits). The result is in (k0, v0) after an even number of
+// passes, in (k1, v1) after an odd one.
+cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
+                             int64_t n_max, const uint32_t* d_n, int bits, void* ws,
+                             cudaStream_t stream);
+
+// ---- index build (gpf_index.cu)
+struct IndexBuffers {
+  DeviceHeader* header;
+  float* rec;           // [N_max * rec_stride] Gaussian records
+  uint4* box;           // [N_max] level boxes
+  uint32_t* gcount;     // [N_max] entries per Gaussian
+  uint32_t* goffset;    // [N_max] exclusive scan of gcount
+  uint32_t* okey[2];    // [N_max] query-level key of each mean (sort ping-pong)
+  uint32_t* oval[2];    // [N_max] Gaussian ids in that order
+  uint32_t* qkey[2];    // [M_max] sort ping-pong of hit points
+  uint32_t* qval[2];
+  uint32_t* qstart;     // [n_keys + 2] per-cell start of the sorted hit points
+  float* qrec;          // [M_max * qrec_stride] packed hit points of the backward
+  uint32_t* occ;        // [n_buckets / 32] occupancy bits of (level, cell) buckets
+  uint32_t* gkey[2];    // [P_max] (bucket, Gaussian) entries, sort ping-pong
+  uint32_t* gval[2];
+  uint2* brange;        // [n_buckets] [start, end) of every bucket's list
+  void* scan_ws;
+  void* qsort_ws;
+  void* gsort_ws;
+  void* osort_ws;
+  int qsorted, gsorted, osorted;  // which ping-pong buffer holds the result
+};
+
+struct IndexDims {
+  Grid grid;
+  int channels;
+  float cutoff;         // k (may be +INF)
+  bool brute;           // no cell lists: every Gaussian against every hit point
+  int64_t n_max, m_max, p_max;
+};
+
+cudaError_t launch_build(const IndexDims& dims, const IndexBuffers& b, const gpf_field& f,
+                         const gpf_queries& q, cudaStream_t stream);
+
+// ---- pair loops (gpf_fwd.cu, gpf_bwd.cu)
+// With counts != null nothing is written but the pair counts (see gpf_count_pairs).
+cudaError_t launch_forward(const IndexDims& dims, const IndexBuffers& b, const gpf_queries& q,
+                           const gpf_query_params& p, int64_t n, float* out, float* z,
+                           unsigned long long* counts, cudaStream_t stream);
+cudaError_t launch_backward(const IndexDims& dims, const IndexBuffers& b, const gpf_field& f,
+                            const gpf_queries& q, const gpf_query_params& p,
+                            const float* grad_out, const float* out, const float* z,
+                            const gpf_field_grad& g, cudaStream_t stream);
+
+// ---- loss and optimiser (gpf_optim.cu)
+size_t mse_workspace_bytes(int64_t m);
+cudaError_t launch_mse(int64_t m, int channels, const float* out, const float* target,
+                       const uint8_t* valid, float* loss, float* grad, void* ws,
+                       cudaStream_t stream);
+cudaError_t launch_adam(const gpf_field& params, const gpf_field_grad& g, const gpf_field_grad& m,
+                        const gpf_field_grad& v, const gpf_adam_hparams& hp, cudaStream_t stream);
+
+}  // namespace gpf
