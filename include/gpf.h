@@ -304,6 +304,30 @@ gpf_status gpf_mse_loss_grad(int64_t m, int32_t channels, const float *out,
                              size_t workspace_bytes, gpf_stream stream);
 
 /*
+ * gpf_mse_loss_grad_noalloc - gpf_mse_loss_grad without a caller workspace.
+ * (A library convenience; the paper has no counterpart.)
+ *
+ * For callers that cannot hand the library device memory of their own: code
+ * where allocating is not permitted or not possible (a host framework that
+ * owns every device allocation and offers no hook for it, a loop that must
+ * never enter the allocator), or a plain C host without CUDA memory
+ * management. The scratch that gpf_mse_loss_grad takes from its workspace
+ * lives here in a fixed array inside the library (128 KiB of device memory on
+ * every GPU that loads the library, held until the process exits).
+ *   Arguments, outputs and results as gpf_mse_loss_grad (bitwise equal).
+ *   m <= GPF_NOALLOC_MAX_POINTS, else GPF_ERR_INVALID_ARG and nothing runs.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. Allocates no memory. All calls share the one array, which keeps the
+ * last call's partial sums; every call overwrites what it reads, but calls
+ * whose kernels may overlap on the GPU race on it: order them.
+ */
+#define GPF_NOALLOC_MAX_POINTS ((int64_t)1 << 26)
+gpf_status gpf_mse_loss_grad_noalloc(int64_t m, int32_t channels, const float *out,
+                                     const float *target, const uint8_t *valid,
+                                     float *loss, float *grad, gpf_stream stream);
+
+/*
  * gpf_adam_step - one bias-corrected Adam update (Sec. S1.2) of the four
  * parameter tensors in place:
  *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2

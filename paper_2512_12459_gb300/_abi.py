@@ -84,6 +84,7 @@ SIGNATURES = {
     "gpf_mse_workspace_size": (c_i32, [c_i64, ctypes.POINTER(ctypes.c_size_t)]),
     "gpf_mse_loss_grad": (c_i32, [c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                   ctypes.c_size_t, c_vp]),
+    "gpf_mse_loss_grad_noalloc": (c_i32, [c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "gpf_adam_step": (c_i32, [ctypes.POINTER(gpf_field), ctypes.POINTER(gpf_field_grad),
                               ctypes.POINTER(gpf_field_grad), ctypes.POINTER(gpf_field_grad),
                               ctypes.POINTER(gpf_adam_hparams), c_vp]),

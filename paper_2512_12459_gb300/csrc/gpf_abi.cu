@@ -414,6 +414,28 @@ gpf_status gpf_mse_loss_grad(int64_t m, int32_t channels, const float* out, cons
   return GPF_OK;
 }
 
+gpf_status gpf_mse_loss_grad_noalloc(int64_t m, int32_t channels, const float* out,
+                                     const float* target, const uint8_t* valid, float* loss,
+                                     float* grad, gpf_stream stream) {
+  if (m < 0) return fail(GPF_ERR_INVALID_ARG, "m < 0");
+  if (m > noalloc_max_points())
+    return fail(GPF_ERR_INVALID_ARG,
+                "m = %lld exceeds GPF_NOALLOC_MAX_POINTS = %lld; use gpf_mse_loss_grad",
+                (long long)m, (long long)noalloc_max_points());
+  if (channels < 1 || channels > GPF_MAX_CHANNELS)
+    return fail(GPF_ERR_INVALID_ARG, "channels = %d outside 1..%d", channels, GPF_MAX_CHANNELS);
+  GPF_CHECK_PTR(loss, "loss");
+  if (m > 0) {
+    GPF_CHECK_PTR(out, "out");
+    GPF_CHECK_PTR(target, "target");
+    GPF_CHECK_PTR(grad, "grad");
+  }
+  cudaError_t e = launch_mse_noalloc(m, channels, out, target, valid, loss, grad,
+                                     reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "gpf_mse_loss_grad_noalloc");
+  return GPF_OK;
+}
+
 gpf_status gpf_adam_step(const gpf_field* params, const gpf_field_grad* grads,
                          const gpf_field_grad* m, const gpf_field_grad* v,
                          const gpf_adam_hparams* hp, gpf_stream stream) {

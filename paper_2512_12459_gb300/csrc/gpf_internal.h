@@ -83,4 +83,10 @@ cudaError_t launch_mse(int64_t m, int channels, const float* out, const float* t
 cudaError_t launch_adam(const gpf_field& params, const gpf_field_grad& g, const gpf_field_grad& m,
                         const gpf_field_grad& v, const gpf_adam_hparams& hp, cudaStream_t stream);
 
+// ---- loss without caller scratch (gpf_noalloc.cu)
+int64_t noalloc_max_points();
+cudaError_t launch_mse_noalloc(int64_t m, int channels, const float* out, const float* target,
+                               const uint8_t* valid, float* loss, float* grad,
+                               cudaStream_t stream);
+
 }  // namespace gpf
