@@ -88,6 +88,7 @@ size_t layout(const gpf_index* ix, char* base, IndexBuffers* b) {
   }
   t.qstart = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * ncp));
   t.qrec = reinterpret_cast<float*>(take(sizeof(float) * M * qrec_stride(d.channels)));
+  t.gacc = reinterpret_cast<float*>(take(sizeof(float) * N * gacc_stride(d.channels)));
   for (int k = 0; k < 2; ++k) {
     t.gkey[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (P > 0 ? P : 1)));
     t.gval[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (P > 0 ? P : 1)));
@@ -99,7 +100,7 @@ size_t layout(const gpf_index* ix, char* base, IndexBuffers* b) {
   t.gsort_ws = take(radix_sort_workspace_bytes(P > 0 ? P : 1));
   t.osort_ws = take(radix_sort_workspace_bytes(N > 0 ? N : 1));
   t.qsorted = radix_sort_passes(d.grid.key_bits) % 2;
-  t.osorted = t.qsorted;
+  t.osorted = radix_sort_passes(d.grid.obits) % 2;
   t.gsorted = radix_sort_passes(d.grid.hash_bits) % 2;
   if (b) *b = t;
   return off;
@@ -256,6 +257,16 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
   int bits = 0;
   while ((1ull << bits) <= cells) ++bits;
   d.grid.key_bits = bits;
+  // the backward walks Gaussians ordered by a cell 16 x coarser than the query level
+  d.grid.oshift = std::min(cfg->query_level + 4, kCoordBits);
+  d.grid.odx = (d.grid.max0x >> d.grid.oshift) + 1;
+  d.grid.ody = (d.grid.max0y >> d.grid.oshift) + 1;
+  {
+    const uint64_t ocells = (uint64_t)d.grid.odx * d.grid.ody * ((d.grid.max0z >> d.grid.oshift) + 1);
+    int ob = 1;
+    while ((1ull << ob) < ocells) ++ob;
+    d.grid.obits = ob + 2;
+  }
   d.channels = cfg->channels;
   d.cutoff = cfg->cutoff_sigma;
   d.brute = isinf(cfg->cutoff_sigma) || cfg->brute_force == 1;

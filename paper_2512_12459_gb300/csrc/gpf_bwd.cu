@@ -43,6 +43,7 @@ struct BwdArgs {
   const float* z;
   int64_t m;
   float* qrec;
+  float* gacc;            // [N * NS] per-Gaussian sums, by position in the order
   const float* rec;
   const uint4* box;
   const uint32_t* order;  // Gaussian ids in mean-cell order
@@ -102,26 +103,50 @@ struct Acc {
 #pragma unroll
     for (int c = 0; c < C; ++c) P[c] = 0.f;
   }
-  __device__ void warp_sum() {
+  // The sums as an array of NS slots (zero padded): 16 for C <= 4, else 32.
+  static constexpr int NV = 12 + C;
+  static constexpr int NS = NV <= 16 ? 16 : 32;
+  __device__ void to_array(float (&v)[NS]) const {
+    v[0] = A00; v[1] = A01; v[2] = A02; v[3] = A11; v[4] = A12; v[5] = A22;
+    v[6] = B0; v[7] = B1; v[8] = B2; v[9] = D0; v[10] = D1; v[11] = D2;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      A00 += __shfl_xor_sync(kFullMask, A00, o);
-      A01 += __shfl_xor_sync(kFullMask, A01, o);
-      A02 += __shfl_xor_sync(kFullMask, A02, o);
-      A11 += __shfl_xor_sync(kFullMask, A11, o);
-      A12 += __shfl_xor_sync(kFullMask, A12, o);
-      A22 += __shfl_xor_sync(kFullMask, A22, o);
-      B0 += __shfl_xor_sync(kFullMask, B0, o);
-      B1 += __shfl_xor_sync(kFullMask, B1, o);
-      B2 += __shfl_xor_sync(kFullMask, B2, o);
-      D0 += __shfl_xor_sync(kFullMask, D0, o);
-      D1 += __shfl_xor_sync(kFullMask, D1, o);
-      D2 += __shfl_xor_sync(kFullMask, D2, o);
+    for (int c = 0; c < C; ++c) v[12 + c] = P[c];
 #pragma unroll
-      for (int c = 0; c < C; ++c) P[c] += __shfl_xor_sync(kFullMask, P[c], o);
-    }
+    for (int i = NV; i < NS; ++i) v[i] = 0.f;
+  }
+  __device__ void from_array(const float* v) {
+    A00 = v[0]; A01 = v[1]; A02 = v[2]; A11 = v[3]; A12 = v[4]; A22 = v[5];
+    B0 = v[6]; B1 = v[7]; B2 = v[8]; D0 = v[9]; D1 = v[10]; D2 = v[11];
+#pragma unroll
+    for (int c = 0; c < C; ++c) P[c] = v[12 + c];
   }
 };
+
+// Sum NS values over the 32 lanes of a warp, scattered: each halving
+// exchange (lane offsets 16, 8, ...) sends half of the values a lane still
+// holds and keeps the other half, so NS - 1 shuffles leave every lane with
+// one complete sum (for NS = 16 lanes l and l ^ 1 hold the same one). The
+// slot a lane ends with is returned in *slot.
+template <int NS>
+__device__ __forceinline__ float reduce_scatter(float (&v)[NS], int lane, int* slot) {
+  constexpr int kStages = NS == 16 ? 4 : 5;
+  int idx = 0;
+#pragma unroll
+  for (int st = 0; st < kStages; ++st) {
+    const int o = 16 >> st, h = NS >> (st + 1);
+    const bool up = (lane & o) != 0;
+    if (up) idx += h;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float send = up ? v[i] : v[i + h];
+      const float keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(kFullMask, send, o);
+    }
+  }
+  if (NS == 16) v[0] += __shfl_xor_sync(kFullMask, v[0], 1);
+  *slot = idx;
+  return v[0];
+}
 
 struct GaussianRegs {
   float mx, my, mz;
@@ -267,7 +292,7 @@ __device__ __forceinline__ void load_gaussian(const BwdArgs& a, int64_t gi, Gaus
 // One lane runs one small Gaussian (bounds within 2 x 2 x 2 query-level
 // cells) alone: no reduction across lanes, the epilogues run side by side.
 template <int C, bool PSI>
-__device__ void bwd_lane_gaussian(const BwdArgs& a, int64_t gi) {
+__device__ void bwd_lane_gaussian(const BwdArgs& a, int64_t pos, int64_t gi) {
   constexpr int QS = qrec_stride(C);
   const Grid& Gd = a.grid;
   GaussianRegs G;
@@ -289,7 +314,12 @@ __device__ void bwd_lane_gaussian(const BwdArgs& a, int64_t gi) {
       for (uint32_t k = a.qstart[key]; k < e; ++k)
         bwd_pair<C, PSI>(G, phi, a.qrec + (int64_t)k * QS, a, acc);
     }
-  bwd_epilogue<C>(a, gi, fr, acc);
+  float v[Acc<C>::NS];
+  acc.to_array(v);
+  float4* dst = reinterpret_cast<float4*>(a.gacc + pos * Acc<C>::NS);
+#pragma unroll
+  for (int i = 0; i < Acc<C>::NS / 4; ++i)
+    dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
 }
 
 // Grid path. The Gaussians come in mean-cell order, the small ones first:
@@ -308,7 +338,7 @@ bwd_grid_kernel(BwdArgs a) {
   const int64_t small_warps = (n_small + kWarp - 1) / kWarp;
   if (w < small_warps) {
     const int64_t idx = w * kWarp + lane;
-    if (idx < n_small) bwd_lane_gaussian<C, PSI>(a, a.order[idx]);
+    if (idx < n_small) bwd_lane_gaussian<C, PSI>(a, idx, a.order[idx]);
     return;
   }
   const int64_t j = n_small + (w - small_warps);
@@ -379,8 +409,12 @@ bwd_grid_kernel(BwdArgs a) {
       }
     }
   }
-  acc.warp_sum();
-  if (lane == 0) bwd_epilogue<C>(a, gi, fr, acc);
+  float v[Acc<C>::NS];
+  acc.to_array(v);
+  int slot;
+  const float sum = reduce_scatter<Acc<C>::NS>(v, lane, &slot);
+  if (Acc<C>::NS == 32 || (lane & 1) == 0) a.gacc[j * Acc<C>::NS + slot] = sum;
+  (void)fr;
 }
 
 // Brute-force path (no cell lists): one warp per Gaussian over all active hit points.
@@ -398,11 +432,27 @@ bwd_brute_kernel(BwdArgs a) {
   Acc<C> acc;
   acc.zero();
   for (int64_t k = lane; k < n_act; k += kWarp) bwd_pair<C, PSI>(G, phi, a.qrec + k * QS, a, acc);
-  acc.warp_sum();
-  if (lane == 0) {
-    const Frame fr = gaussian_frame(a.quat, a.logscale, a.n, gi);
-    bwd_epilogue<C>(a, gi, fr, acc);
-  }
+  float v[Acc<C>::NS];
+  acc.to_array(v);
+  int slot;
+  const float sum = reduce_scatter<Acc<C>::NS>(v, lane, &slot);
+  if (Acc<C>::NS == 32 || (lane & 1) == 0) a.gacc[gi * Acc<C>::NS + slot] = sum;
+}
+
+// Gradients of every processed Gaussian from its sums, one thread each.
+// Grid path: position j of the order holds Gaussian order[j] (j < n_live);
+// brute force: position j is Gaussian j.
+template <int C>
+__global__ void bwd_epilogue_kernel(BwdArgs a, int brute) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!brute && a.header->overflow) return;
+  const int64_t count = brute ? a.n : (int64_t)a.header->n_live;
+  if (j >= count) return;
+  const int64_t gi = brute ? j : a.order[j];
+  Acc<C> acc;
+  acc.from_array(a.gacc + j * Acc<C>::NS);
+  const Frame fr = gaussian_frame(a.quat, a.logscale, a.n, gi);
+  bwd_epilogue<C>(a, gi, fr, acc);
 }
 
 template <int C>
@@ -421,7 +471,8 @@ cudaError_t launch_c(const BwdArgs& a, const IndexDims& d, bool psi, cudaStream_
     if (psi) bwd_grid_kernel<C, true><<<blocks, kBwdThreads, 0, stream>>>(a);
     else bwd_grid_kernel<C, false><<<blocks, kBwdThreads, 0, stream>>>(a);
   }
-  note_launches(1);
+  bwd_epilogue_kernel<C><<<(unsigned)((a.n + 255) / 256), 256, 0, stream>>>(a, d.brute ? 1 : 0);
+  note_launches(2);
   return cudaGetLastError();
 }
 
@@ -453,6 +504,7 @@ cudaError_t launch_backward(const IndexDims& d, const IndexBuffers& b, const gpf
   a.z = z;
   a.m = q.m;
   a.qrec = b.qrec;
+  a.gacc = b.gacc;
   a.rec = b.rec;
   a.box = b.box;
   a.order = b.oval[b.osorted];

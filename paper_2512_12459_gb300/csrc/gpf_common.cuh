@@ -46,6 +46,10 @@ __host__ __device__ constexpr int rec_stride(int channels) {
 __host__ __device__ constexpr int qrec_stride(int channels) {
   return 4 * ((5 + channels + 3) / 4);
 }
+// Per-Gaussian sums of the backward (A 6, B 3, D 3, dPhi C), zero padded.
+__host__ __device__ constexpr int gacc_stride(int channels) {
+  return 12 + channels <= 16 ? 16 : 32;
+}
 
 // Geometry of the multi-level grid, passed by value to kernels.
 //   level L has cubic cells of edge cell0 * 2^L, all sharing the origin;
@@ -70,6 +74,9 @@ struct Grid {
   uint32_t max0x, max0y, max0z;  // largest level-0 coordinate per axis
   int id_bits;             // low bits of an entry word holding the Gaussian id
   uint32_t id_mask;        // (1 << id_bits) - 1
+  int oshift;              // level whose cells order the backward's Gaussians
+  uint32_t odx, ody;       // cells per axis on that level
+  int obits;               // bits of an order key (cell key and 2 class bits)
 };
 
 // Level-0 cell coordinate of v along one axis: floor((v - o) / c0) in float32,

@@ -114,7 +114,9 @@ __global__ void __launch_bounds__(kFwdThreads)
 fwd_kernel(FwdArgs a) {
   constexpr int RS = rec_stride(C);
   __shared__ __align__(16) float s_rec[kFwdWarps][kWarp * RS];
-  __shared__ unsigned long long s_cell[kFwdWarps][kWarp];
+  __shared__ unsigned long long s_cell[kFwdWarps][kUnionMax];
+  __shared__ int s_leader[kFwdWarps][kUnionMax];
+  __shared__ uint2 s_range[kFwdWarps][kMaxLevels][kWarp];
 
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t tile = (int64_t)blockIdx.x * kFwdWarps + wib;
@@ -175,6 +177,16 @@ fwd_kernel(FwdArgs a) {
     const float hx = 0.5f * (bx1 - bx0), hy = 0.5f * (by1 - by0), hz = 0.5f * (bz1 - bz0);
     const float cut_keep = a.cut * 1.0001f;
     const uint32_t lmask = a.header->level_mask;
+    // the lane's bucket range on every used level, all looked up at once
+#pragma unroll
+    for (int lev = 0; lev < kMaxLevels; ++lev) {
+      if (lev < G.levels && ((lmask >> lev) & 1u)) {
+        uint2 rg = make_uint2(0u, 0u);
+        if (active) rg = __ldg(a.brange + cell_hash(G, lev, c0x >> lev, c0y >> lev, c0z >> lev).bucket);
+        s_range[wib][lev][lane] = rg;
+      }
+    }
+    __syncwarp();
 
     for (int lev = 0; lev < G.levels; ++lev) {
       if (!((lmask >> lev) & 1u)) continue;
@@ -189,59 +201,61 @@ fwd_kernel(FwdArgs a) {
       const int nu = __popc(uniq);
       if (nu <= kUnionMax) {
         // ---- warp-cooperative mode over the tile's distinct cells
-        if (leader) s_cell[wib][__popc(uniq & lanemask_lt())] = packed;
+        if (leader) {
+          const int slot = __popc(uniq & lanemask_lt());
+          s_cell[wib][slot] = packed;
+          s_leader[wib][slot] = lane;
+        }
         __syncwarp();
         for (int j = 0; j < nu; ++j) {
           const unsigned long long cj = s_cell[wib][j];
           const uint32_t ux = (uint32_t)(cj & kCoordMax), uy = (uint32_t)((cj >> 20) & kCoordMax),
                          uz = (uint32_t)((cj >> 40) & kCoordMax);
-          const CellHash h = cell_hash(G, lev, ux, uy, uz);
-          const uint2 rg = a.brange[h.bucket];
+          const uint32_t tag = cell_hash(G, lev, ux, uy, uz).tag;
+          const uint2 rg = s_range[wib][lev][s_leader[wib][j]];
+          // entry words of the first chunk; each later chunk is fetched while
+          // the previous one is being vetted
+          uint32_t v = rg.x + lane < rg.y ? __ldg(a.gval + rg.x + lane) : 0u;
+          uint32_t carry = 0xffffffffu;
           for (uint32_t e0 = rg.x; e0 < rg.y; e0 += kWarp) {
             const uint32_t e = e0 + lane;
-            bool keep = false;
-            uint32_t g = 0;
-            if (e < rg.y) {
-              const uint32_t v = __ldg(a.gval + e);
-              g = v & G.id_mask;
-              // the tag tells this cell's entries from other cells' in the
-              // bucket; a Gaussian listed twice sits on consecutive entries
-              keep = (v & ~G.id_mask) == h.tag && !(e > rg.x && __ldg(a.gval + e - 1) == v);
-              if (keep) {
-                const uint4 bw = __ldg(a.box + g);
-                const float4* src = reinterpret_cast<const float4*>(a.rec + (int64_t)g * RS);
-                const float4 r0 = __ldg(src), r1 = __ldg(src + 1), r2 = __ldg(src + 2),
-                             r3 = __ldg(src + 3);
-                const LevelBox b = unpack_box(bw);
-                // it must live on this level and cover this cell, and must not
-                // have been taken from an earlier cell of this tile
-                keep = b.level == lev && box_holds(b, ux, uy, uz);
-                for (int jj = 0; jj < j && keep; ++jj) {
-                  const unsigned long long ci = s_cell[wib][jj];
-                  keep = !box_holds(b, (uint32_t)(ci & kCoordMax),
-                                    (uint32_t)((ci >> 20) & kCoordMax),
-                                    (uint32_t)((ci >> 40) & kCoordMax));
-                }
-                if (keep) {
-                  // sphere test: distance from mu to the tile box vs k * max s
-                  const float ex = fmaxf(fmaxf(bx0 - r0.x, r0.x - bx1), 0.0f);
-                  const float ey = fmaxf(fmaxf(by0 - r0.y, r0.y - by1), 0.0f);
-                  const float ez = fmaxf(fmaxf(bz0 - r0.z, r0.z - bz1), 0.0f);
-                  keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= r0.w * r0.w;
-                }
-                if (keep) {
-                  const float Mr[9] = {r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w, r3.x};
-                  keep = mahalanobis_lower_bound(Mr, r0.x, r0.y, r0.z, cx, cy, cz, hx, hy, hz) <=
-                         cut_keep;
-                }
+            const uint32_t vn = e + kWarp < rg.y ? __ldg(a.gval + e + kWarp) : 0u;
+            // a Gaussian listed twice in a bucket sits on consecutive entries
+            uint32_t vprev = __shfl_up_sync(kFullMask, v, 1);
+            if (lane == 0) vprev = carry;
+            carry = __shfl_sync(kFullMask, v, kWarp - 1);
+            bool keep = e < rg.y && (v & ~G.id_mask) == tag && v != vprev;
+            const uint32_t g = v & G.id_mask;
+            float rr[RS];
+            if (keep) {
+              const uint4 bw = __ldg(a.box + g);
+              load_rec<RS>(a.rec, g, rr);
+              const LevelBox b = unpack_box(bw);
+              // it must live on this level and cover this cell, and must not
+              // have been taken from an earlier cell of this tile
+              keep = b.level == lev && box_holds(b, ux, uy, uz);
+              for (int jj = 0; jj < j && keep; ++jj) {
+                const unsigned long long ci = s_cell[wib][jj];
+                keep = !box_holds(b, (uint32_t)(ci & kCoordMax), (uint32_t)((ci >> 20) & kCoordMax),
+                                  (uint32_t)((ci >> 40) & kCoordMax));
               }
+              if (keep) {
+                // sphere test: distance from mu to the tile box vs k * max s
+                const float ex = fmaxf(fmaxf(bx0 - rr[0], rr[0] - bx1), 0.0f);
+                const float ey = fmaxf(fmaxf(by0 - rr[1], rr[1] - by1), 0.0f);
+                const float ez = fmaxf(fmaxf(bz0 - rr[2], rr[2] - bz1), 0.0f);
+                keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= rr[3] * rr[3];
+              }
+              if (keep)
+                keep = mahalanobis_lower_bound(rr + 4, rr[0], rr[1], rr[2], cx, cy, cz, hx, hy, hz) <=
+                       cut_keep;
             }
             const uint32_t kb = __ballot_sync(kFullMask, keep);
             if (keep) {
-              const float4* src = reinterpret_cast<const float4*>(a.rec + (int64_t)g * RS);
               float4* dst = reinterpret_cast<float4*>(my_rec + __popc(kb & lanemask_lt()) * RS);
 #pragma unroll
-              for (int v = 0; v < RS / 4; ++v) dst[v] = __ldg(src + v);
+              for (int q4 = 0; q4 < RS / 4; ++q4)
+                dst[q4] = make_float4(rr[4 * q4], rr[4 * q4 + 1], rr[4 * q4 + 2], rr[4 * q4 + 3]);
             }
             __syncwarp();
             const int nk = __popc(kb);
@@ -249,24 +263,23 @@ fwd_kernel(FwdArgs a) {
               for (int s = 0; s < nk; ++s)
                 eval_pair<C, PSI, COUNT>(my_rec + s * RS, px, py, pz, a, L, Z, n_eval, n_inc);
             __syncwarp();
+            v = vn;
           }
         }
       } else if (active) {
         // ---- per-lane mode: each lane walks its own cell's list, four
         // entries at a time so that their loads are in flight together
-        const CellHash h = cell_hash(G, lev, lx, ly, lz);
-        const uint2 rg = a.brange[h.bucket];
-        uint32_t prev = rg.x > 0 ? __ldg(a.gval + rg.x - 1) : 0u;
+        const uint32_t tag = cell_hash(G, lev, lx, ly, lz).tag;
+        const uint2 rg = s_range[wib][lev][lane];
+        uint32_t prev = 0xffffffffu;
         for (uint32_t e = rg.x; e < rg.y; e += 4) {
           uint32_t v[4];
           bool ok[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) v[u] = e + u < rg.y ? __ldg(a.gval + e + u) : 0u;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            ok[u] = e + u < rg.y && (v[u] & ~G.id_mask) == h.tag &&
-                    v[u] != (u == 0 ? (e > rg.x ? prev : ~v[0]) : v[u - 1]);
-          }
+          for (int u = 0; u < 4; ++u)
+            ok[u] = e + u < rg.y && (v[u] & ~G.id_mask) == tag && v[u] != (u == 0 ? prev : v[u - 1]);
           prev = v[3];
           uint4 bw[4];
 #pragma unroll

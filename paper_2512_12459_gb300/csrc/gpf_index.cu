@@ -11,12 +11,11 @@
 // query-level cell of their mean, the order the backward walks them in.
 //
 // Kernels, in stream order:
-//   preprocess (records, level boxes, level mask, mean keys)
-//   query_keys (hit point keys, occupancy bits of the used levels)
-//   sort hit points, per-cell starts
-//   count entries (Gaussians without any leave the backward's order)
-//   sort Gaussians by mean cell
-//   scan -> emit (bucket, Gaussian) entries -> sort -> bucket starts
+//   query_keys (hit point keys and per-cell counts, occupancy bits of every level)
+//   preprocess (records, level boxes, entry counts, order keys, level mask)
+//   sort hit points, per-cell starts (scan of the counts)
+//   sort Gaussians into the backward's order
+//   scan of entry counts -> emit (bucket, Gaussian) entries -> sort -> bucket ranges
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -32,13 +31,22 @@ constexpr int kThreads = 256;
 constexpr int64_t kMaxBoxCells = int64_t(1) << 16;
 constexpr uint32_t kNoBox = 0xffffffffu;
 
+__device__ __forceinline__ bool occupied(const uint32_t* occ, uint32_t b) {
+  return (occ[b >> 5] >> (b & 31u)) & 1u;
+}
+
+// Per Gaussian: record, level box, the number of cells of that box holding a
+// hit point (its list entries) and its key in the backward's order.
 __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brute,
                                   float* __restrict__ rec, int rs, uint4* __restrict__ box,
+                                  const uint32_t* __restrict__ occ,
+                                  uint32_t* __restrict__ gcount,
                                   uint32_t* __restrict__ okey, uint32_t* __restrict__ oval,
                                   DeviceHeader* header) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = f.n;
   uint32_t level_bit = 0;
+  bool live = false, small = false;
   if (g < n) {
     const float mu[3] = {f.mean[g], f.mean[n + g], f.mean[2 * n + g]};
     const Frame fr = gaussian_frame(f.quat, f.logscale, n, g);
@@ -56,20 +64,22 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
     for (int c = 0; c < f.channels; ++c) r[13 + c] = f.spectrum[(int64_t)c * n + g];
     for (int c = 13 + f.channels; c < rs; ++c) r[c] = 0.0f;
     // the order the backward walks Gaussians in: class (0 = bounds within
-    // 2 x 2 x 2 query-level cells, 1 = larger; dead ones get 2 later), then
-    // the query-level cell of the mean
-    const int K = grid.qlevel;
-    const uint32_t mkey = qkey_of(grid, coord0(mu[0], grid.ox, grid.inv_cell0, grid.max0x) >> K,
-                                  coord0(mu[1], grid.oy, grid.inv_cell0, grid.max0y) >> K,
-                                  coord0(mu[2], grid.oz, grid.inv_cell0, grid.max0z) >> K);
-    okey[g] = mkey | (1u << grid.key_bits);
+    // 2 x 2 x 2 query-level cells, 1 = larger, 2 = no hit point in reach),
+    // then the cell of the mean on a coarse level
+    const int K = grid.qlevel, os = grid.oshift;
+    const uint32_t mkey =
+        ((coord0(mu[2], grid.oz, grid.inv_cell0, grid.max0z) >> os) * grid.ody +
+         (coord0(mu[1], grid.oy, grid.inv_cell0, grid.max0y) >> os)) * grid.odx +
+        (coord0(mu[0], grid.ox, grid.inv_cell0, grid.max0x) >> os);
+    const int cls_shift = grid.obits - 2;
+    uint32_t cls = 1;
     oval[g] = (uint32_t)g;
     if (!brute) {
       uint32_t lo[3], hi[3];
       gaussian_cells0(grid, fr, mu, cutoff, lo, hi);
       if ((hi[0] >> K) - (lo[0] >> K) <= 1 && (hi[1] >> K) - (lo[1] >> K) <= 1 &&
           (hi[2] >> K) - (lo[2] >> K) <= 1)
-        okey[g] = mkey;
+        cls = 0;
       int L = 0;
       for (; L < grid.levels - 1; ++L) {
         const uint32_t sx = (hi[0] >> L) - (lo[0] >> L), sy = (hi[1] >> L) - (lo[1] >> L),
@@ -79,17 +89,31 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
       const uint32_t lx = lo[0] >> L, ly = lo[1] >> L, lz = lo[2] >> L;
       const uint32_t sx = (hi[0] >> L) - lx, sy = (hi[1] >> L) - ly, sz = (hi[2] >> L) - lz;
       const int64_t vol = (int64_t)(sx + 1) * (sy + 1) * (sz + 1);
+      uint32_t cnt = 0;
       if (sx > 255 || sy > 255 || sz > 255 || vol > kMaxBoxCells) {
         box[g] = make_uint4(kNoBox, kNoBox, kNoBox, 0);
         atomicExch(&header->overflow, 1u);
       } else {
         box[g] = make_uint4(lx | ((uint32_t)L << 20), ly, lz, sx | (sy << 8) | (sz << 16));
         level_bit = 1u << L;
+        for (uint32_t iz = lz; iz <= lz + sz; ++iz)
+          for (uint32_t iy = ly; iy <= ly + sy; ++iy)
+            for (uint32_t ix = lx; ix <= lx + sx; ++ix)
+              cnt += occupied(occ, bucket_of(grid, L, ix, iy, iz)) ? 1u : 0u;
       }
+      gcount[g] = cnt;
+      live = cnt > 0;
+      if (!live) cls = 2;
+      small = live && cls == 0;
     }
+    okey[g] = mkey | (cls << cls_shift);
   }
   const uint32_t m = __reduce_or_sync(kFullMask, level_bit);
   if ((threadIdx.x & 31) == 0 && m) atomicOr(&header->level_mask, m);
+  const uint32_t blive = __ballot_sync(kFullMask, live);
+  const uint32_t bsmall = __ballot_sync(kFullMask, small);
+  if ((threadIdx.x & 31) == 0 && blive) atomicAdd(&header->n_live, __popc(blive));
+  if ((threadIdx.x & 31) == 0 && bsmall) atomicAdd(&header->n_small, __popc(bsmall));
 }
 
 __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
@@ -116,9 +140,7 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
       k = qkey_of(grid, cx >> K, cy >> K, cz >> K);
       atomicAdd(&qcount[k], 1u);
       if (mark) {
-        const uint32_t lm = header->level_mask;
         for (int L = 0; L < grid.levels; ++L) {
-          if (!((lm >> L) & 1u)) continue;
           const uint32_t b = bucket_of(grid, L, cx >> L, cy >> L, cz >> L);
           const uint32_t bit = 1u << (b & 31u);
           if (!(occ[b >> 5] & bit)) atomicOr(&occ[b >> 5], bit);
@@ -132,47 +154,16 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
   if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(&header->n_active, __popc(ballot));
 }
 
-__device__ __forceinline__ bool occupied(const uint32_t* occ, uint32_t b) {
-  return (occ[b >> 5] >> (b & 31u)) & 1u;
-}
-
-// EMIT = false: count the occupied cells of every Gaussian's level box;
-// EMIT = true: write one (bucket, Gaussian) entry per occupied cell, in the
-// box's cell order (a Gaussian whose cells share a bucket appears there on
-// consecutive entries; the pair loops take only the first).
-// Counting also retires the Gaussians without entries from the backward's
-// order (their mean key becomes the inactive key) and counts the others.
-template <bool EMIT>
-__global__ void entries_kernel(Grid grid, int64_t n, int64_t p_max, const uint4* __restrict__ box,
-                               const uint32_t* __restrict__ occ, uint32_t* __restrict__ gcount,
-                               const uint32_t* __restrict__ goffset, uint32_t* __restrict__ gkey,
-                               uint32_t* __restrict__ gval, uint32_t* __restrict__ okey,
-                               DeviceHeader* header) {
+// One (bucket, Gaussian) entry per occupied cell of every Gaussian's level
+// box, in the box's cell order, at the Gaussian's offset (the exclusive scan
+// of the counts). A Gaussian whose cells share a bucket appears there on
+// consecutive entries; the pair loops take only the first.
+__global__ void emit_kernel(Grid grid, int64_t n, int64_t p_max, const uint4* __restrict__ box,
+                            const uint32_t* __restrict__ occ, const uint32_t* __restrict__ goffset,
+                            uint32_t* __restrict__ gkey, uint32_t* __restrict__ gval,
+                            DeviceHeader* header) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (EMIT && g == 0 && (int64_t)header->n_pairs > p_max) atomicExch(&header->overflow, 1u);
-  if (!EMIT) {
-    bool live = false, small = false;
-    if (g < n) {
-      const uint4 bw = box[g];
-      uint32_t cnt = 0;
-      if (bw.x != kNoBox) {
-        const LevelBox b = unpack_box(bw);
-        for (uint32_t iz = b.lz; iz <= b.hz; ++iz)
-          for (uint32_t iy = b.ly; iy <= b.hy; ++iy)
-            for (uint32_t ix = b.lx; ix <= b.hx; ++ix)
-              cnt += occupied(occ, bucket_of(grid, b.level, ix, iy, iz)) ? 1u : 0u;
-      }
-      gcount[g] = cnt;
-      live = cnt > 0;
-      if (!live) okey[g] = 2u << grid.key_bits;
-      small = live && (okey[g] >> grid.key_bits) == 0;
-    }
-    const uint32_t ballot = __ballot_sync(kFullMask, live);
-    const uint32_t bsmall = __ballot_sync(kFullMask, small);
-    if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(&header->n_live, __popc(ballot));
-    if ((threadIdx.x & 31) == 0 && bsmall) atomicAdd(&header->n_small, __popc(bsmall));
-    return;
-  }
+  if (g == 0 && (int64_t)header->n_pairs > p_max) atomicExch(&header->overflow, 1u);
   if (g >= n) return;
   const uint4 bw = box[g];
   if (bw.x == kNoBox) return;
@@ -222,46 +213,37 @@ cudaError_t launch_build(const IndexDims& d, const IndexBuffers& b, const gpf_fi
   // hit points per query-level cell, counted by the key pass
   e = cudaMemsetAsync(b.qstart, 0, sizeof(uint32_t) * ((size_t)grid.n_keys + 2), stream);
   if (e != cudaSuccess) return e;
-  // 1. Gaussian records, level boxes, level mask
-  if (f.n > 0) {
-    preprocess_kernel<<<blocks_for(f.n), kThreads, 0, stream>>>(
-        f, grid, d.cutoff, d.brute ? 1 : 0, b.rec, rec_stride(d.channels), b.box, b.okey[0],
-        b.oval[0], b.header);
-    note_launches(1);
-  }
-  // 2. hit point keys and occupancy of the used levels
+  // 1. hit point keys and occupancy bits of every level
   if (q.m > 0) {
     query_keys_kernel<<<blocks_for(q.m), kThreads, 0, stream>>>(
         grid, q.x, q.normal, q.wo, q.valid, q.m, b.qkey[0], b.qval[0], b.occ, d.brute ? 0 : 1,
         b.qstart, b.header);
     note_launches(1);
   }
+  // 2. Gaussian records, level boxes, entry counts, order keys, level mask
+  if (f.n > 0) {
+    preprocess_kernel<<<blocks_for(f.n), kThreads, 0, stream>>>(
+        f, grid, d.cutoff, d.brute ? 1 : 0, b.rec, rec_stride(d.channels), b.box, b.occ,
+        b.gcount, b.okey[0], b.oval[0], b.header);
+    note_launches(1);
+  }
   // 3. hit points sorted by query-level cell (inactive ones last), cell starts
   e = radix_sort_pairs(b.qkey[0], b.qval[0], b.qkey[1], b.qval[1], q.m, nullptr, grid.key_bits,
                        b.qsort_ws, stream);
   if (e != cudaSuccess) return e;
-  // cell starts: exclusive scan of the counts (inactive points come last)
   e = exclusive_scan_u32(b.qstart, b.qstart, (int64_t)grid.n_keys + 2, nullptr, b.scan_ws,
                          stream);
   if (e != cudaSuccess) return e;
-  // 4. entry counts (Gaussians without any retire from the backward's order),
-  //    then Gaussians sorted by the query-level cell of their mean
-  if (!d.brute && f.n > 0) {
-    entries_kernel<false><<<blocks_for(f.n), kThreads, 0, stream>>>(
-        grid, f.n, d.p_max, b.box, b.occ, b.gcount, nullptr, nullptr, nullptr, b.okey[0],
-        b.header);
-    note_launches(1);
-  }
-  e = radix_sort_pairs(b.okey[0], b.oval[0], b.okey[1], b.oval[1], f.n, nullptr,
-                       grid.key_bits + 2, b.osort_ws, stream);
+  // 4. Gaussians in the backward's order
+  e = radix_sort_pairs(b.okey[0], b.oval[0], b.okey[1], b.oval[1], f.n, nullptr, grid.obits,
+                       b.osort_ws, stream);
   if (e != cudaSuccess) return e;
   if (d.brute || f.n == 0) return cudaGetLastError();
   // 5. (bucket, Gaussian) entries: scan, emit, sort, bucket starts
   e = exclusive_scan_u32(b.gcount, b.goffset, f.n, &b.header->n_pairs, b.scan_ws, stream);
   if (e != cudaSuccess) return e;
-  entries_kernel<true><<<blocks_for(f.n), kThreads, 0, stream>>>(
-      grid, f.n, d.p_max, b.box, b.occ, b.gcount, b.goffset, b.gkey[0], b.gval[0], nullptr,
-      b.header);
+  emit_kernel<<<blocks_for(f.n), kThreads, 0, stream>>>(grid, f.n, d.p_max, b.box, b.occ,
+                                                        b.goffset, b.gkey[0], b.gval[0], b.header);
   note_launches(1);
   e = radix_sort_pairs(b.gkey[0], b.gval[0], b.gkey[1], b.gval[1], d.p_max, &b.header->n_pairs,
                        grid.hash_bits, b.gsort_ws, stream);
