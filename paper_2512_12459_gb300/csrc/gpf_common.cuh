@@ -33,9 +33,22 @@ static_assert(sizeof(DeviceHeader) == 256, "header is one 256-byte block");
 
 // Per-Gaussian record read by the pair loops, float32, stride rec_stride(C):
 //   [0..2]  mu
-//   [3]     bounding-sphere radius of the k-sigma ellipsoid (k * max s_j)
+//   [3]     bounding-sphere radius of the k-sigma ellipsoid (k * max s_j),
+//           rounded up to carry the Gaussian's grid level in its low
+//           kLevelBits mantissa bits (rec_radius_with_level, rec_level)
 //   [4..12] M = S^-1 R^T, row-major: M[j][k] = R[k][j] / s_j
 //   [13..]  Phi[0..C-1], then zero padding to a multiple of 4 floats
+constexpr int kLevelBits = 4;  // levels < 2^kLevelBits = kMaxLevels
+constexpr uint32_t kLevelMask = (1u << kLevelBits) - 1u;
+static_assert(kMaxLevels <= (1 << kLevelBits), "a level must fit in kLevelBits");
+
+// A radius no smaller than r (finite, >= 0) whose low mantissa bits hold level.
+__device__ __forceinline__ float rec_radius_with_level(float r, uint32_t level) {
+  const uint32_t u = __float_as_uint(fminf(r, 1e30f));
+  return __uint_as_float(((u + kLevelMask) & ~kLevelMask) | level);
+}
+__device__ __forceinline__ uint32_t rec_level(float r) { return __float_as_uint(r) & kLevelMask; }
+
 __host__ __device__ constexpr int rec_stride(int channels) {
   return channels <= 3 ? 16 : 4 * ((13 + channels + 3) / 4);
 }

@@ -12,7 +12,9 @@
 //     Mahalanobis distance rules out the tile's box of hit points). Survivors
 //     are staged in shared memory and every lane evaluates all of them.
 //   * many distinct cells (the Gaussians are small next to the spacing of the
-//     hit points): per-lane mode. Each lane walks its own cell's list.
+//     hit points): pooled mode. The lanes' own cell lists are concatenated and
+//     taken 32 (hit point, entry) items at a time, one per lane; a segmented
+//     sum over the lanes returns each hit point's share to its lane.
 // Every lane applies the exact predicate Q <= k^2, so the result equals the
 // brute-force sum over {i : Q_i <= k^2}. With no cell lists (k = +INF or
 // brute force) the candidates are all Gaussians, in index order.
@@ -26,7 +28,7 @@ namespace gpf {
 
 namespace {
 
-constexpr int kFwdWarps = 8;
+constexpr int kFwdWarps = 4;
 constexpr int kFwdThreads = kFwdWarps * kWarp;
 // A tile whose hit points fall in at most this many cells of a level walks
 // that level cooperatively.
@@ -65,11 +67,12 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-// Accumulate one Gaussian record r into this lane's sums (or count it).
-template <int C, bool PSI, bool COUNT>
-__device__ __forceinline__ void eval_pair(const float* __restrict__ r, float px, float py, float pz,
-                                          const FwdArgs& a, float (&L)[C], float& Z,
-                                          uint32_t& n_eval, uint32_t& n_inc) {
+// Weight of one pair: w = exp(-Q/2) psi(|d|) when Q <= k^2 (hit = true).
+// In count mode only the evaluated and included pairs are counted.
+template <bool PSI, bool COUNT>
+__device__ __forceinline__ float pair_weight(const float* __restrict__ r, float px, float py,
+                                             float pz, const FwdArgs& a, bool& hit,
+                                             uint32_t& n_eval, uint32_t& n_inc) {
   const float dx = px - r[0], dy = py - r[1], dz = pz - r[2];
   const float u0 = fmaf(r[4], dx, fmaf(r[5], dy, r[6] * dz));
   const float u1 = fmaf(r[7], dx, fmaf(r[8], dy, r[9] * dz));
@@ -78,24 +81,71 @@ __device__ __forceinline__ void eval_pair(const float* __restrict__ r, float px,
   if (COUNT) {
     ++n_eval;
     n_inc += Q <= a.cut2 ? 1u : 0u;
-    return;
+    hit = false;
+    return 0.0f;
   }
-  if (Q <= a.cut2) {
-    float e = -0.5f * Q;
-    if (PSI) {
-      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      if (d2 > a.r2) {
-        // correctly rounded: the exponent's sensitivity to |d| is 6 t (t + 1) / |d|
-        const float dist = sqrtf(d2);
-        const float t = (dist - a.r) * a.inv_rr;
-        e = fmaf(-3.0f * t, t, e);
-      }
+  hit = Q <= a.cut2;
+  if (!hit) return 0.0f;
+  float e = -0.5f * Q;
+  if (PSI) {
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (d2 > a.r2) {
+      // correctly rounded: the exponent's sensitivity to |d| is 6 t (t + 1) / |d|
+      const float dist = sqrtf(d2);
+      const float t = (dist - a.r) * a.inv_rr;
+      e = fmaf(-3.0f * t, t, e);
     }
-    const float w = ex2_approx(e * kLog2e);
+  }
+  return ex2_approx(e * kLog2e);
+}
+
+// Accumulate one Gaussian record r into this lane's sums (or count it).
+template <int C, bool PSI, bool COUNT>
+__device__ __forceinline__ void eval_pair(const float* __restrict__ r, float px, float py, float pz,
+                                          const FwdArgs& a, float (&L)[C], float& Z,
+                                          uint32_t& n_eval, uint32_t& n_inc) {
+  bool hit;
+  const float w = pair_weight<PSI, COUNT>(r, px, py, pz, a, hit, n_eval, n_inc);
+  if (hit) {
 #pragma unroll
     for (int c = 0; c < C; ++c) L[c] = fmaf(w, r[13 + c], L[c]);
     Z += w;
   }
+}
+
+// Hands the per-lane partial sums pc of the lanes with f set to their owner
+// key (owner lane) in acc[c][key]. The flushing lanes of one key are
+// contiguous, so a segmented inclusive sum over the lanes leaves each key's
+// total in its last lane, which adds it to acc. Lanes that flush restart
+// from zero.
+template <int C>
+__device__ __forceinline__ void pooled_flush(float (*acc)[kWarp], int lane, int key_in, bool f,
+                                             float (&pc)[C + 1]) {
+  const int key = f ? key_in : 2 * kWarp + lane;
+  float t[C + 1];
+#pragma unroll
+  for (int c = 0; c <= C; ++c) t[c] = f ? pc[c] : 0.0f;
+#pragma unroll
+  for (int d = 1; d < kWarp; d <<= 1) {
+    const int kd = __shfl_up_sync(kFullMask, key, d);
+    float u[C + 1];
+#pragma unroll
+    for (int c = 0; c <= C; ++c) u[c] = __shfl_up_sync(kFullMask, t[c], d);
+    if (lane >= d && kd == key) {
+#pragma unroll
+      for (int c = 0; c <= C; ++c) t[c] += u[c];
+    }
+  }
+  const int kn = __shfl_down_sync(kFullMask, key, 1);
+  if (f && (lane == kWarp - 1 || kn != key)) {
+#pragma unroll
+    for (int c = 0; c <= C; ++c) acc[c][key] += t[c];
+  }
+  if (f) {
+#pragma unroll
+    for (int c = 0; c <= C; ++c) pc[c] = 0.0f;
+  }
+  __syncwarp();
 }
 
 template <int RS>
@@ -117,6 +167,7 @@ fwd_kernel(FwdArgs a) {
   __shared__ unsigned long long s_cell[kFwdWarps][kUnionMax];
   __shared__ int s_leader[kFwdWarps][kUnionMax];
   __shared__ uint2 s_range[kFwdWarps][kMaxLevels][kWarp];
+  __shared__ float s_acc[kFwdWarps][C + 1][kWarp];  // pooled-mode sums per hit point
 
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t tile = (int64_t)blockIdx.x * kFwdWarps + wib;
@@ -147,6 +198,9 @@ fwd_kernel(FwdArgs a) {
   float Z = 0.0f;
   uint32_t n_eval = 0, n_inc = 0;
   float* my_rec = s_rec[wib];
+#pragma unroll
+  for (int c = 0; c <= C; ++c) s_acc[wib][c][lane] = 0.0f;
+  __syncwarp();
 
   if (BRUTE) {
     for (int64_t g0 = 0; g0 < a.n; g0 += kWarp) {
@@ -266,35 +320,77 @@ fwd_kernel(FwdArgs a) {
             v = vn;
           }
         }
-      } else if (active) {
-        // ---- per-lane mode: each lane walks its own cell's list, four
-        // entries at a time so that their loads are in flight together
+      } else {
+        // ---- pooled mode: the lanes' lists are laid end to end and the warp
+        // takes them 32 (hit point, entry) items at a time, one item per lane.
+        // A lane sums what it evaluates for one owner at a time and hands the
+        // sum over (pooled_flush) when the owner of its item slot changes, so
+        // no lane waits for the longest list and every sum has a fixed order.
+        // The cell-box test is not needed here: an entry that reached this
+        // bucket from another cell on the same level has a box that misses
+        // this hit point, so Q > k^2 rejects it; the level test and the
+        // duplicate test keep any Gaussian from being counted twice.
         const uint32_t tag = cell_hash(G, lev, lx, ly, lz).tag;
-        const uint2 rg = s_range[wib][lev][lane];
-        uint32_t prev = 0xffffffffu;
-        for (uint32_t e = rg.x; e < rg.y; e += 4) {
-          uint32_t v[4];
-          bool ok[4];
+        const uint2 rg = s_range[wib][lev][lane];  // (0, 0) for inactive lanes
+        const uint32_t len = rg.y - rg.x;
+        uint32_t incl = len;  // inclusive prefix sum of the list lengths
 #pragma unroll
-          for (int u = 0; u < 4; ++u) v[u] = e + u < rg.y ? __ldg(a.gval + e + u) : 0u;
+        for (int o = 1; o < kWarp; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(kFullMask, incl, o);
+          if (lane >= o) incl += t;
+        }
+        const uint32_t total = __shfl_sync(kFullMask, incl, kWarp - 1);
+        int cur = -1;  // owner of this lane's item slot in the previous chunk
+        float pc[C + 1];
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-            ok[u] = e + u < rg.y && (v[u] & ~G.id_mask) == tag && v[u] != (u == 0 ? prev : v[u - 1]);
-          prev = v[3];
-          uint4 bw[4];
+        for (int c = 0; c <= C; ++c) pc[c] = 0.0f;
+        uint32_t o_first = 0, o_start = 0, o_tag = 0;
+        float qx = 0.0f, qy = 0.0f, qz = 0.0f;
+        uint32_t carry = 0xffffffffu;
+        for (uint32_t b = 0; b < total; b += kWarp) {
+          const uint32_t i = b + lane;
+          const bool live = i < total;
+          // owner: the first lane whose inclusive end exceeds i (kWarp: none)
+          int own = 0;
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (ok[u]) bw[u] = __ldg(a.box + (v[u] & G.id_mask));
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (!ok[u]) continue;
-            const LevelBox b = unpack_box(bw[u]);
-            if (b.level != lev || !box_holds(b, lx, ly, lz)) continue;
+          for (int st = 16; st > 0; st >>= 1) {
+            const uint32_t pe = __shfl_sync(kFullMask, incl, own + st - 1);
+            if (pe <= i) own += st;
+          }
+          if (!live) own = kWarp;
+          const bool chg = own != cur;
+          if (__any_sync(kFullMask, chg)) {
+            pooled_flush<C>(s_acc[wib], lane, cur, chg && cur >= 0 && cur < kWarp, pc);
+            const int src = own & (kWarp - 1);
+            o_first = __shfl_sync(kFullMask, incl - len, src);
+            o_start = __shfl_sync(kFullMask, rg.x, src);
+            o_tag = __shfl_sync(kFullMask, tag, src);
+            qx = __shfl_sync(kFullMask, px, src);
+            qy = __shfl_sync(kFullMask, py, src);
+            qz = __shfl_sync(kFullMask, pz, src);
+            cur = own;
+          }
+          const uint32_t kk = i - o_first;  // position in the owner's list
+          const uint32_t v = live ? __ldg(a.gval + o_start + kk) : 0u;
+          // the owner's previous entry is the previous item
+          uint32_t vprev = __shfl_up_sync(kFullMask, v, 1);
+          if (lane == 0) vprev = carry;
+          carry = __shfl_sync(kFullMask, v, kWarp - 1);
+          if (live && (v & ~G.id_mask) == o_tag && !(kk > 0 && v == vprev)) {
             float rr[RS];
-            load_rec<RS>(a.rec, v[u] & G.id_mask, rr);
-            eval_pair<C, PSI, COUNT>(rr, px, py, pz, a, L, Z, n_eval, n_inc);
+            load_rec<RS>(a.rec, v & G.id_mask, rr);
+            if (rec_level(rr[3]) == (uint32_t)lev) {
+              bool hit;
+              const float w = pair_weight<PSI, COUNT>(rr, qx, qy, qz, a, hit, n_eval, n_inc);
+              if (hit) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) pc[c] = fmaf(w, rr[13 + c], pc[c]);
+                pc[C] += w;
+              }
+            }
           }
         }
+        pooled_flush<C>(s_acc[wib], lane, cur, cur >= 0 && cur < kWarp, pc);
       }
     }
   }
@@ -311,6 +407,11 @@ fwd_kernel(FwdArgs a) {
     }
     return;
   }
+  // the pooled-mode sums of this lane's hit point
+  __syncwarp();
+#pragma unroll
+  for (int c = 0; c < C; ++c) L[c] += s_acc[wib][c][lane];
+  Z += s_acc[wib][C][lane];
   if (active) {
     float scale = 1.0f;
     if (a.mode == GPF_NORMALIZED) scale = 1.0f / fmaxf(Z, a.eps);

@@ -95,6 +95,7 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
         atomicExch(&header->overflow, 1u);
       } else {
         box[g] = make_uint4(lx | ((uint32_t)L << 20), ly, lz, sx | (sy << 8) | (sz << 16));
+        r[3] = rec_radius_with_level(r[3], (uint32_t)L);
         level_bit = 1u << L;
         for (uint32_t iz = lz; iz <= lz + sz; ++iz)
           for (uint32_t iy = ly; iy <= ly + sy; ++iy)
