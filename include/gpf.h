@@ -9,18 +9,18 @@
  *
  *   Gaussian i: mean mu_i, rotation q_i (quaternion (w,x,y,z), normalised by
  *   the library), log-scale l_i (scale s_i = exp(l_i)), spectral flux Phi_i
- *   (C channels). Sec. 3.1: Sigma_i = R S S^T R^T, contribution
+ *   (C channels). Sec. 4.1: Sigma_i = R S S^T R^T, contribution
  *   Phi_i exp(-1/2 d^T Sigma_i^-1 d).
  *
  *   Hit point x with normal n, direction to the viewer w_o, albedo rho:
  *     u_i = S_i^-1 R_i^T (x - mu_i),  Q_i = u_i . u_i
  *     psi = 1 if |x - mu_i| <= r else exp(-3 t^2), t = (|x - mu_i| - r)/max(r, 1e-6)
- *     w_i = exp(-Q_i / 2) psi                 (Sec. 3.2, aggregation)
+ *     w_i = exp(-Q_i / 2) psi                 (Sec. 4.2, aggregation)
  *     L = sum_{i : Q_i <= k^2} w_i Phi_i,  Z = sum_{i : Q_i <= k^2} w_i
  *     O = rho * L * [n.w_o > 0]                  (GPF_SUM)
  *     O = rho * L / max(Z, eps) * [n.w_o > 0]    (GPF_NORMALIZED; the soft
  *                                                  normalisation of the
- *                                                  supplementary query listing)
+ *                                                  query listing of Algorithm S3)
  *   k is the truncation in standard deviations (3: the 3-sigma ellipsoid; an
  *   infinite k sums every Gaussian).
  *
@@ -73,7 +73,7 @@ typedef enum gpf_mode { GPF_SUM = 0, GPF_NORMALIZED = 1 } gpf_mode;
 /* Maximum number of grid levels. */
 #define GPF_MAX_LEVELS 16
 
-/* The Gaussian Photon Field (Sec. 3.1). All arrays [rows, n], float32. */
+/* The Gaussian Photon Field (Sec. 4.1). All arrays [rows, n], float32. */
 typedef struct gpf_field {
   int64_t n;             /* number of Gaussians N >= 0                       */
   int32_t channels;      /* C, 1..GPF_MAX_CHANNELS                           */
@@ -84,7 +84,7 @@ typedef struct gpf_field {
   const float *spectrum; /* [C,N] Phi                                        */
 } gpf_field;
 
-/* Camera-ray hit points (first diffuse hits, Sec. 3.2). */
+/* Camera-ray hit points (first diffuse hits, Sec. 4.2). */
 typedef struct gpf_queries {
   int64_t m;             /* number of hit points M >= 0                      */
   const float *x;        /* [3,M] positions                                  */
@@ -151,7 +151,7 @@ typedef struct gpf_field_grad {
   int32_t reserved;
 } gpf_field_grad;
 
-/* Adam hyper-parameters (Sec. S1.2: Adam, learning rate 5e-4). */
+/* Adam hyper-parameters (Sec. A.2: Adam, learning rate 5e-4). */
 typedef struct gpf_adam_hparams {
   float lr[4];           /* learning rate per group: mean, quat, logscale,
                             spectrum                                         */
@@ -200,8 +200,8 @@ gpf_status gpf_index_workspace_size(const gpf_index *index, size_t *bytes);
  * then emits one (cell, Gaussian) entry for every cell that the Gaussian's
  * bounds overlap and that holds at least one active hit point, and
  * radix-sorts the entries by cell into per-cell Gaussian lists. It replaces
- * the paper's periodically rebuilt KD-tree over the centres (Sec. S1.2) and
- * bounds the neighbourhood by the k-sigma ellipsoid (Sec. 3.2, Neighborhood
+ * the paper's periodically rebuilt KD-tree over the centres (Sec. A.2) and
+ * bounds the neighbourhood by the k-sigma ellipsoid (Sec. 4.2, Neighborhood
  * Search, read as {i : Q_i <= k^2}).
  *
  *   index      handle from gpf_index_create.
@@ -229,9 +229,9 @@ gpf_status gpf_index_stats(const gpf_index *index, gpf_index_stats_t *stats,
                            gpf_stream stream);
 
 /*
- * gpf_radiance_fwd - radiance O at every hit point (Sec. 3.2, aggregation
- * equation; the soft falloff and normalisation of the supplementary query
- * listing; the BSDF modulation read as albedo times a hemisphere gate).
+ * gpf_radiance_fwd - radiance O at every hit point (Sec. 4.2, aggregation
+ * equation; the soft falloff and normalisation of the query listing of
+ * Algorithm S3; the BSDF modulation read as albedo times a hemisphere gate).
  *
  *   index, field, queries  as given to the last gpf_build_index.
  *   params  host pointer: mode, r_max (+INF: psi = 1), eps.
@@ -252,7 +252,7 @@ gpf_status gpf_radiance_fwd(const gpf_index *index, const gpf_field *field,
  * gpf_count_pairs - the work of gpf_radiance_fwd for the last build, without
  * computing radiance: counts[0] = (hit point, candidate Gaussian) pairs the
  * pair loop evaluates after culling, counts[1] = pairs with Q <= k^2 (the
- * neighbourhood of Sec. 3.2 read as the k-sigma ellipsoid; the algorithmic
+ * neighbourhood of Sec. 4.2 read as the k-sigma ellipsoid; the algorithmic
  * work of the query).
  *   counts  device array of 2 uint64, 8-byte aligned, overwritten.
  * Errors: as gpf_radiance_fwd.
@@ -269,7 +269,7 @@ uint64_t gpf_launch_count(void);
 
 /*
  * gpf_radiance_bwd - gradient of sum_{c,m} grad_out[c,m] O[c,m] with respect
- * to mu, q (raw), l and Phi (Sec. 3.2, Differentiable Accumulation). The
+ * to mu, q (raw), l and Phi (Sec. 4.2, Differentiable Accumulation). The
  * exponentials are recomputed, not stored. Contributions are reduced per
  * Gaussian inside one warp (no global atomics), so results are bitwise
  * reproducible.
@@ -289,7 +289,7 @@ gpf_status gpf_radiance_bwd(const gpf_index *index, const gpf_field *field,
                             gpf_stream stream);
 
 /*
- * gpf_mse_loss_grad - the MSE loss of Sec. 3.3 and its gradient:
+ * gpf_mse_loss_grad - the MSE loss of Sec. 4.3 and its gradient:
  *   loss = (1/|V|) sum_{m valid} sum_c (out[c,m] - target[c,m])^2
  *   grad[c,m] = 2 (out - target) / |V| on valid points, 0 elsewhere.
  *   out, target  [C,M] float32 device; valid [M] uint8 device or NULL.
@@ -328,7 +328,7 @@ gpf_status gpf_mse_loss_grad_noalloc(int64_t m, int32_t channels, const float *o
                                      float *loss, float *grad, gpf_stream stream);
 
 /*
- * gpf_adam_step - one bias-corrected Adam update (Sec. S1.2) of the four
+ * gpf_adam_step - one bias-corrected Adam update (Sec. A.2) of the four
  * parameter tensors in place:
  *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2
  *   p -= lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps)

@@ -6,16 +6,16 @@ and its Python binding) never imports, links or executes anything here, and
 this package imports nothing from the product.
 
 What it computes (paper arxiv 2512.12459):
-  * forward radiance at hit points: Eq. (G_i) of Sec. 3.1, the aggregation
+  * forward radiance at hit points: Eq. (G_i) of Sec. 4.1, the aggregation
     L_GPF = sum_i w_i Phi_i with w_i = exp(-1/2 d^T Lambda_i d) psi(|d|) of
-    Sec. 3.2 (Radiance Query and Aggregation), the soft falloff psi and the
-    soft normalisation max(sum w, eps) of the supplementary query listing
-    (Sec. S1.2), the BSDF modulation of Sec. 3.2 read as a per-hit albedo and
+    Sec. 4.2 (Radiance Query and Aggregation), the soft falloff psi and the
+    soft normalisation max(sum w, eps) of the query listing of Algorithm S3
+    (Sec. A.2), the BSDF modulation of Sec. 4.2 read as a per-hit albedo and
     a hemisphere gate;
   * the analytic gradient of that output with respect to every Gaussian
-    parameter (Sec. 3.2, Differentiable Accumulation), by the chain rule;
-  * the MSE loss of Sec. 3.3 and its gradient;
-  * the Adam update of Sec. S1.2 (lr 5e-4).
+    parameter (Sec. 4.2, Differentiable Accumulation), by the chain rule;
+  * the MSE loss of Sec. 4.3 and its gradient;
+  * the Adam update of Sec. A.2 (lr 5e-4).
 
 Everything is a brute-force sum over all Gaussians in float64; the inputs are
 the float32 values the GPU path receives, widened exactly.

@@ -7,14 +7,14 @@ spatial index, no fusion, no reordering beyond what the definitions state.
 Notation follows the paper: Gaussian i has mean mu_i, rotation q_i (unit
 quaternion, stored (w, x, y, z) and normalised here), scale s_i = exp(l_i)
 and spectral flux Phi_i in R^C; Sigma_i = R S S^T R^T and the precision is
-Lambda_i = R S^-2 R^T (Sec. 3.1). For a hit point x with normal n, direction
+Lambda_i = R S^-2 R^T (Sec. 4.1). For a hit point x with normal n, direction
 to the viewer w_o and albedo rho:
 
     d   = x - mu_i
     u   = S^-1 R^T d          (local frame, per-axis divided by the scale)
     Q   = u . u = d^T Lambda_i d
     psi = 1 if |d| <= r else exp(-3 t^2), t = (|d| - r) / max(r, 1e-6)
-    w_i = exp(-Q / 2) psi      (Sec. 3.2, aggregation equation)
+    w_i = exp(-Q / 2) psi      (Sec. 4.2, aggregation equation)
     L   = sum_i w_i Phi_i,  Z = sum_i w_i
     O   = rho * L * [n.w_o > 0]                    (mode SUM)
     O   = rho * L / max(Z, eps) * [n.w_o > 0]      (mode NORMALIZED)
@@ -40,7 +40,7 @@ def quat_to_rotmat(qhat: np.ndarray) -> np.ndarray:
     """Rotation matrix of unit quaternions (w, x, y, z), shape [..., 4] -> [..., 3, 3].
 
     Textbook form: column j of R is the j-th local axis expressed in world
-    coordinates (Sec. 3.1: the rotation is a unit quaternion)."""
+    coordinates (Sec. 4.1: the rotation is a unit quaternion)."""
     w, x, y, z = (qhat[..., 0], qhat[..., 1], qhat[..., 2], qhat[..., 3])
     R = np.empty(qhat.shape[:-1] + (3, 3), dtype=_F64)
     R[..., 0, 0] = 1.0 - 2.0 * (y * y + z * z)
@@ -77,8 +77,8 @@ def _rotmat_partials(qhat: np.ndarray) -> np.ndarray:
 
 
 def falloff_psi(dist: np.ndarray, r_max: float) -> np.ndarray:
-    """Soft distance falloff psi(|d|) of Sec. 3.2, in the form the supplementary
-    query listing gives: 1 inside the radius r, exp(-3 t^2) outside with
+    """Soft distance falloff psi(|d|) of Sec. 4.2, in the form the query listing of
+    Algorithm S3 gives: 1 inside the radius r, exp(-3 t^2) outside with
     t = (|d| - r) / max(r, 1e-6). An infinite radius disables it (psi = 1)."""
     dist = np.asarray(dist, dtype=_F64)
     if not math.isfinite(r_max):
@@ -199,7 +199,7 @@ def radiance_bwd(mean, quat, logscale, spectrum, x, n, wo, grad_out, albedo=None
     """Gradient of sum_{c,m} grad_out[c,m] * O[c,m] with respect to the raw
     parameters: mean [3,N], quat [4,N] (raw, through the normalisation),
     logscale [3,N], spectrum [C,N]. Chain rule through each step of the
-    forward (Sec. 3.2, Differentiable Accumulation); the indicator Q <= cutoff^2
+    forward (Sec. 4.2, Differentiable Accumulation); the indicator Q <= cutoff^2
     is piecewise constant and contributes no derivative."""
     P = _Prepared(mean, quat, logscale, spectrum)
     X = np.asarray(x, dtype=_F64).T
@@ -255,7 +255,7 @@ def radiance_bwd(mean, quat, logscale, spectrum, x, n, wo, grad_out, albedo=None
 
 
 def mse_loss(out, target, valid=None) -> float:
-    """Sec. 3.3: (1/|V|) sum_{x in V} |O(x) - O_ref(x)|_2^2 over the valid points."""
+    """Sec. 4.3: (1/|V|) sum_{x in V} |O(x) - O_ref(x)|_2^2 over the valid points."""
     O = np.asarray(out, dtype=_F64)
     T = np.asarray(target, dtype=_F64)
     v = np.ones(O.shape[1], dtype=bool) if valid is None else np.asarray(valid).astype(bool)
@@ -279,7 +279,7 @@ def mse_loss_grad(out, target, valid=None) -> np.ndarray:
 
 def adam_step(param, grad, m, v, step: int, lr: float = 5e-4, beta1: float = 0.9,
               beta2: float = 0.999, eps: float = 1e-8):
-    """One Adam update (Kingma & Ba, bias-corrected; the optimiser of Sec. S1.2
+    """One Adam update (Kingma & Ba, bias-corrected; the optimiser of Sec. A.2
     with its learning rate 5e-4). `step` is the 1-based index of this update.
     Returns (param, m, v) as new float64 arrays."""
     p = np.asarray(param, dtype=_F64)

@@ -22,7 +22,7 @@ __all__ = [
     "gpf_adam_step", "AdamState", "PAPER_R", "PAPER_EPS", "PAPER_LR",
 ]
 
-# Hyper-parameters the paper prints (Sec. S1.2 and the supplementary query listing).
+# Hyper-parameters the paper prints (Sec. A.2 and the query listing of Algorithm S3).
 PAPER_R = 0.02
 PAPER_EPS = 1e-6
 PAPER_LR = 5e-4

@@ -1,5 +1,5 @@
 // gpf_radiance_bwd: gradient of the hit-point radiance with respect to every
-// Gaussian parameter (Sec. 3.2, Differentiable Accumulation).
+// Gaussian parameter (Sec. 4.2, Differentiable Accumulation).
 //
 // Chain rule for a pair (Gaussian i, hit point x) with w = exp(-Q/2) psi:
 //   d loss / d w   = beta = zeta (sum_c gamma_c Phi_c - kappa)

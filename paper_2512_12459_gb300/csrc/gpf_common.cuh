@@ -156,7 +156,7 @@ __device__ __forceinline__ bool box_holds(const LevelBox& b, uint32_t x, uint32_
 }
 
 // Rotation and scale of a Gaussian from its raw parameters: R(q/|q|) with
-// column j = local axis j in world coordinates (Sec. 3.1), s = exp(l).
+// column j = local axis j in world coordinates (Sec. 4.1), s = exp(l).
 struct Frame {
   float R[3][3];
   float s[3];

@@ -1,5 +1,5 @@
-// gpf_radiance_fwd: radiance at hit points (Sec. 3.2, aggregation equation;
-// the soft falloff and soft normalisation of the supplementary query listing).
+// gpf_radiance_fwd: radiance at hit points (Sec. 4.2, aggregation equation;
+// the soft falloff and soft normalisation of the query listing of Algorithm S3).
 //
 // One warp per tile of 32 consecutive hit points in cell-sorted order. For
 // every grid level that holds Gaussians, the lanes find their cell on that

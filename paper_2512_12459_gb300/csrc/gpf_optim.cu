@@ -1,4 +1,4 @@
-// MSE loss and its gradient (Sec. 3.3) and the Adam update (Sec. S1.2).
+// MSE loss and its gradient (Sec. 4.3) and the Adam update (Sec. A.2).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>

@@ -4,12 +4,12 @@ Every generator takes an integer seed and draws from numpy's PCG64, so a
 (seed, size) pair always yields the same bytes. Arrays are structure-of-arrays
 float32 (one row per component), which is the layout the C library takes.
 
-The analytic scene stands in for the paper's Mitsuba scenes (Sec. 4.1), which
+The analytic scene stands in for the paper's Mitsuba scenes (Sec. 5.1), which
 are not available: a floor z = 0 on [-4, 4]^2 and a unit sphere centred at
 (0, 0, 1). Photons are deposited 70 % in a mixture of eight anisotropic 2D
 Gaussians on the floor (a caustic-like pattern) and 30 % uniformly by area over
 floor and sphere. One Gaussian per photon follows the paper's initialisation
-(Sec. 3.1: mean at the photon, flux from the photon, random rotation), with the
+(Sec. 4.1: mean at the photon, flux from the photon, random rotation), with the
 isotropic scale taken from the distance to the 8th nearest photon.
 """
 

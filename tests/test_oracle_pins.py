@@ -153,7 +153,7 @@ def test_plane_integral_depends_on_orientation():
 
 def _kde2d(points, weights, h, xq):
     """Weighted 2D Gaussian-kernel density estimate with bandwidth h (a kernel
-    density estimate as in the photon-density background of Sec. 2.2, with a
+    density estimate as in the photon density estimate of Sec. 3.2, with a
     smooth kernel in place of the disk): sum_i W_i N(x; p_i, h^2 I)."""
     out = np.zeros(xq.shape[0])
     for p, wgt in zip(points, weights):
