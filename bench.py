@@ -135,6 +135,40 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+# DRAM bytes (read + write) per launch of the pair-loop kernels on this
+# workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
+# second warm-up step of `python bench.py --steps 3 --warmup 3
+# --no-cpu-baseline`), with the SHA-256 of the sources the kernel was built
+# from; reported only while those sources are unchanged.
+PROFILED_TRAFFIC = {
+    "fwd_kernel": {"bytes": 432348672 + 11620352, "sources": {
+        "paper_2512_12459_gb300/csrc/gpf_fwd.cu":
+            "e4c41578d5b68051aa52e9f10cf1d448251403cd9bc04d416ac704d1ad3cf07f",
+        "paper_2512_12459_gb300/csrc/gpf_common.cuh":
+            "3ee18429921eb65442208a104407f4d68a54b6b6d21ff58ea35d3e204a0e3593"}},
+    "bwd_grid_kernel": {"bytes": 175708928 + 52078848, "sources": {
+        "paper_2512_12459_gb300/csrc/gpf_bwd.cu":
+            "e1fb6e0a9d81d03f900c23325e663f7076bf84d93600dfdb0756aee71164ed0f",
+        "paper_2512_12459_gb300/csrc/gpf_common.cuh":
+            "3ee18429921eb65442208a104407f4d68a54b6b6d21ff58ea35d3e204a0e3593"}},
+}
+
+
+def _sha256(path: str) -> str:
+    import hashlib
+    with open(os.path.join(ROOT, path), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()
+
+
+def profiled_traffic(kernel: str):
+    rec = PROFILED_TRAFFIC.get(kernel)
+    if rec is None:
+        return None
+    if any(_sha256(p) != h for p, h in rec["sources"].items()):
+        return None
+    return rec["bytes"]
+
+
 def fp32_peak_tflops(sm_mhz_max: float, sms: int = 152) -> float:
     """FP32 lane peak: SMs x 128 FP32 lanes x 2 flops (FMA) x max SM clock."""
     return sms * 128 * 2 * sm_mhz_max * 1e6 / 1e12
@@ -257,8 +291,11 @@ def main():
     ev = {k: [] for k in ("step", "build", "fwd", "loss", "bwd", "adam")}
 
     def step(timed: bool):
-        marks = [torch.cuda.Event(enable_timing=True) for _ in range(6)] if timed else None
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(10)] if timed else None
         if timed:
+            # the library records marks[6:8] / marks[8:10] around the forward
+            # and backward pair-loop kernels themselves
+            idx.set_timing_events(fwd=(marks[6], marks[7]), bwd=(marks[8], marks[9]))
             marks[0].record(stream)
         idx.build(field, queries)
         if timed:
@@ -281,6 +318,7 @@ def main():
             marks[5].record(stream)
         return marks
 
+    idx.set_timing_events()
     for _ in range(args.warmup):
         step(False)
     torch.cuda.synchronize()
@@ -302,6 +340,7 @@ def main():
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
+    idx.set_timing_events()
     launches = gpf.gpf_launch_count() - launches0
 
     per = {k: [] for k in ("build", "fwd", "loss", "bwd", "adam", "step")}
@@ -311,6 +350,8 @@ def main():
             per[nm].append(mk[i].elapsed_time(mk[i + 1]))
         per["step"].append(mk[0].elapsed_time(mk[5]))
     ms = {k: float(np.mean(v)) for k, v in per.items()}
+    kernel_ms = {"fwd_kernel": float(np.mean([mk[6].elapsed_time(mk[7]) for mk in all_marks])),
+                 "bwd_grid_kernel": float(np.mean([mk[8].elapsed_time(mk[9]) for mk in all_marks]))}
     step_ms = ms["step"]
     if world > 1:
         t = torch.tensor([step_ms], device="cuda")
@@ -366,13 +407,15 @@ def main():
         inc = pairs["included"]
         fwd_flops = inc * (25 + 2 * C)       # per included pair, FMA = 2 flops
         bwd_flops = inc * (55 + 4 * C)
-        fwd_ach = fwd_flops / (ms["fwd"] / 1e3) / 1e12
-        bwd_ach = bwd_flops / (ms["bwd"] / 1e3) / 1e12
-        dom = "bwd" if ms["bwd"] >= ms["fwd"] else "fwd"
-        ach = bwd_ach if dom == "bwd" else fwd_ach
-        roof = {"bound": "alu", "kernel": "radiance_" + dom, "achieved": ach, "peak": fp32_peak,
-                "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {smax:.0f} MHz ({peaks_src} max clock)"}
+        fwd_ach = fwd_flops / (kernel_ms["fwd_kernel"] / 1e3) / 1e12
+        bwd_ach = bwd_flops / (kernel_ms["bwd_grid_kernel"] / 1e3) / 1e12
+        dom = "bwd_grid_kernel" if kernel_ms["bwd_grid_kernel"] >= kernel_ms["fwd_kernel"] \
+            else "fwd_kernel"
+        ach = bwd_ach if dom == "bwd_grid_kernel" else fwd_ach
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": profiled_traffic(dom),
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {smax:.0f} MHz ({peaks_src} max clock)",
+                "duration_ms": kernel_ms[dom]}
         extra = {"included_pairs": inc, "candidate_pairs": pairs["candidates"],
                  "fwd_alu_frac": fwd_ach / fp32_peak, "bwd_alu_frac": bwd_ach / fp32_peak}
 
@@ -399,6 +442,7 @@ def main():
             "fwd_queries_per_s": n_active / (ms["fwd"] / 1e3),
             "fwd_bwd_queries_per_s": n_active / ((ms["fwd"] + ms["bwd"] + ms["loss"]) / 1e3),
             "ms_breakdown": {k: v for k, v in ms.items() if k != "step"},
+            "kernel_ms": kernel_ms,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": total_q / (e2e_ms / 1e3), "unit": "queries/s",

@@ -262,6 +262,24 @@ gpf_status gpf_count_pairs(const gpf_index *index, const gpf_field *field,
                            gpf_stream stream);
 
 /*
+ * gpf_index_set_timing_events - have later calls on this index record
+ * caller-created CUDA events around their pair-loop kernels, for per-kernel
+ * timing with cudaEventElapsedTime: fwd_start / fwd_stop around the kernel of
+ * gpf_radiance_fwd, bwd_start / bwd_stop around the pair-loop kernel of
+ * gpf_radiance_bwd (not its packing and gradient-epilogue kernels).
+ *   each event  a cudaEvent_t passed as void*, created and owned by the
+ *               caller, or NULL (not recorded). The handles are kept until
+ *               the next call of this function and recorded on the stream of
+ *               every later gpf_radiance_fwd / gpf_radiance_bwd call; the
+ *               caller keeps them alive for as long as they are set.
+ * The paper has no counterpart: it is an instrumentation hook.
+ * Errors: GPF_ERR_INVALID_ARG (index NULL); a failed event record surfaces
+ * as GPF_ERR_CUDA from the call that records it.
+ */
+gpf_status gpf_index_set_timing_events(gpf_index *index, void *fwd_start, void *fwd_stop,
+                                       void *bwd_start, void *bwd_stop);
+
+/*
  * gpf_launch_count - number of CUDA kernels this library has launched in the
  * process so far (host-side counter; memsets and copies are not counted).
  */

@@ -78,6 +78,7 @@ SIGNATURES = {
     "gpf_count_pairs": (c_i32, [c_vp, ctypes.POINTER(gpf_field), ctypes.POINTER(gpf_queries),
                                 c_vp, c_vp]),
     "gpf_launch_count": (ctypes.c_uint64, []),
+    "gpf_index_set_timing_events": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "gpf_radiance_bwd": (c_i32, [c_vp, ctypes.POINTER(gpf_field), ctypes.POINTER(gpf_queries),
                                  ctypes.POINTER(gpf_query_params), c_vp, c_vp, c_vp,
                                  ctypes.POINTER(gpf_field_grad), c_vp]),

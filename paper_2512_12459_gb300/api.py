@@ -209,6 +209,18 @@ class Index:
                                         _stream(stream)), "gpf_build_index")
         self._field, self._queries = field, queries
 
+    def set_timing_events(self, fwd=None, bwd=None) -> None:
+        """gpf_index_set_timing_events: `fwd` and `bwd` are (start, stop)
+        pairs of torch.cuda.Event (enable_timing=True) or None; later
+        gpf_radiance_fwd / gpf_radiance_bwd calls record them around their
+        pair-loop kernels."""
+        hs = []
+        for pair in (fwd, bwd):
+            for ev in (pair if pair is not None else (None, None)):
+                hs.append(_event_handle(ev))
+        self._timing = (fwd, bwd)   # keep the events alive while they are set
+        check(self._lib.gpf_index_set_timing_events(self._h, *hs), "gpf_index_set_timing_events")
+
     def stats(self, stream=None) -> dict:
         """gpf_index_stats (synchronises the stream)."""
         st = _abi.gpf_index_stats_t()
@@ -217,6 +229,17 @@ class Index:
         if status not in (_abi.GPF_OK, _abi.GPF_ERR_CAPACITY):
             check(status, "gpf_index_stats")
         return out
+
+
+def _event_handle(ev):
+    """The cudaEvent_t of a torch.cuda.Event (created on first use), or None."""
+    if ev is None:
+        return None
+    h = int(ev.cuda_event or 0)
+    if h == 0:
+        ev.record()          # torch creates the CUDA event lazily
+        h = int(ev.cuda_event)
+    return h
 
 
 def _params(mode, r_max, eps) -> _abi.gpf_query_params:

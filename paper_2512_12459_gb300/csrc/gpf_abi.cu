@@ -56,6 +56,8 @@ struct gpf_index {
   // identity of the last build
   gpf_field field;
   gpf_queries queries;
+  // gpf_index_set_timing_events
+  KernelEvents fwd_ev, bwd_ev;
 };
 
 namespace {
@@ -341,7 +343,7 @@ gpf_status gpf_radiance_fwd(const gpf_index* index, const gpf_field* field,
     if (z_out && !aligned(z_out, 4)) return fail(GPF_ERR_INVALID_ARG, "z_out is not aligned");
   }
   cudaError_t e = launch_forward(index->dims, index->buf, *queries, *params, field->n, out, z_out,
-                                 nullptr, reinterpret_cast<cudaStream_t>(stream));
+                                 nullptr, index->fwd_ev, reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "gpf_radiance_fwd");
   return GPF_OK;
 }
@@ -357,9 +359,19 @@ gpf_status gpf_count_pairs(const gpf_index* index, const gpf_field* field,
     return fail(GPF_ERR_INVALID_ARG, "counts is NULL or not 8-byte aligned");
   gpf_query_params p{GPF_SUM, INFINITY, 1e-6f, 0};
   cudaError_t e = launch_forward(index->dims, index->buf, *queries, p, field->n, nullptr, nullptr,
-                                 reinterpret_cast<unsigned long long*>(counts),
+                                 reinterpret_cast<unsigned long long*>(counts), KernelEvents{},
                                  reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "gpf_count_pairs");
+  return GPF_OK;
+}
+
+gpf_status gpf_index_set_timing_events(gpf_index* index, void* fwd_start, void* fwd_stop,
+                                       void* bwd_start, void* bwd_stop) {
+  if (!index) return fail(GPF_ERR_INVALID_ARG, "index is NULL");
+  index->fwd_ev.start = static_cast<cudaEvent_t>(fwd_start);
+  index->fwd_ev.stop = static_cast<cudaEvent_t>(fwd_stop);
+  index->bwd_ev.start = static_cast<cudaEvent_t>(bwd_start);
+  index->bwd_ev.stop = static_cast<cudaEvent_t>(bwd_stop);
   return GPF_OK;
 }
 
@@ -391,7 +403,7 @@ gpf_status gpf_radiance_bwd(const gpf_index* index, const gpf_field* field,
     }
   }
   cudaError_t e = launch_backward(index->dims, index->buf, *field, *queries, *params, grad_out, out,
-                                  z, *grads, reinterpret_cast<cudaStream_t>(stream));
+                                  z, *grads, index->bwd_ev, reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "gpf_radiance_bwd");
   return GPF_OK;
 }

@@ -456,7 +456,8 @@ __global__ void bwd_epilogue_kernel(BwdArgs a, int brute) {
 }
 
 template <int C>
-cudaError_t launch_c(const BwdArgs& a, const IndexDims& d, bool psi, cudaStream_t stream) {
+cudaError_t launch_c(const BwdArgs& a, const IndexDims& d, bool psi, const KernelEvents& ev,
+                     cudaStream_t stream) {
   const unsigned pblocks = (unsigned)((a.m + 255) / 256);
   pack_qrec_kernel<C><<<pblocks, 256, 0, stream>>>(a);
   note_launches(1);
@@ -464,6 +465,8 @@ cudaError_t launch_c(const BwdArgs& a, const IndexDims& d, bool psi, cudaStream_
   // brute force: a warp per Gaussian; grid: up to n / 32 lane warps + n warps
   const int64_t warps = d.brute ? a.n : a.n + (a.n + kWarp - 1) / kWarp;
   const unsigned blocks = (unsigned)((warps + kBwdWarps - 1) / kBwdWarps);
+  cudaError_t e;
+  if (ev.start && (e = cudaEventRecord(ev.start, stream)) != cudaSuccess) return e;
   if (d.brute) {
     if (psi) bwd_brute_kernel<C, true><<<blocks, kBwdThreads, 0, stream>>>(a);
     else bwd_brute_kernel<C, false><<<blocks, kBwdThreads, 0, stream>>>(a);
@@ -471,6 +474,7 @@ cudaError_t launch_c(const BwdArgs& a, const IndexDims& d, bool psi, cudaStream_
     if (psi) bwd_grid_kernel<C, true><<<blocks, kBwdThreads, 0, stream>>>(a);
     else bwd_grid_kernel<C, false><<<blocks, kBwdThreads, 0, stream>>>(a);
   }
+  if (ev.stop && (e = cudaEventRecord(ev.stop, stream)) != cudaSuccess) return e;
   bwd_epilogue_kernel<C><<<(unsigned)((a.n + 255) / 256), 256, 0, stream>>>(a, d.brute ? 1 : 0);
   note_launches(2);
   return cudaGetLastError();
@@ -481,7 +485,8 @@ cudaError_t launch_c(const BwdArgs& a, const IndexDims& d, bool psi, cudaStream_
 cudaError_t launch_backward(const IndexDims& d, const IndexBuffers& b, const gpf_field& f,
                             const gpf_queries& q, const gpf_query_params& p,
                             const float* grad_out, const float* out, const float* z,
-                            const gpf_field_grad& g, cudaStream_t stream) {
+                            const gpf_field_grad& g, const KernelEvents& ev,
+                            cudaStream_t stream) {
   const int64_t n = f.n;
   if (!g.accumulate && n > 0) {
     cudaError_t e;
@@ -521,14 +526,14 @@ cudaError_t launch_backward(const IndexDims& d, const IndexBuffers& b, const gpf
   a.cut2 = isinf(d.cutoff) ? INFINITY : d.cutoff * d.cutoff;
   a.g = g;
   switch (d.channels) {
-    case 1: return launch_c<1>(a, d, psi, stream);
-    case 2: return launch_c<2>(a, d, psi, stream);
-    case 3: return launch_c<3>(a, d, psi, stream);
-    case 4: return launch_c<4>(a, d, psi, stream);
-    case 5: return launch_c<5>(a, d, psi, stream);
-    case 6: return launch_c<6>(a, d, psi, stream);
-    case 7: return launch_c<7>(a, d, psi, stream);
-    case 8: return launch_c<8>(a, d, psi, stream);
+    case 1: return launch_c<1>(a, d, psi, ev, stream);
+    case 2: return launch_c<2>(a, d, psi, ev, stream);
+    case 3: return launch_c<3>(a, d, psi, ev, stream);
+    case 4: return launch_c<4>(a, d, psi, ev, stream);
+    case 5: return launch_c<5>(a, d, psi, ev, stream);
+    case 6: return launch_c<6>(a, d, psi, ev, stream);
+    case 7: return launch_c<7>(a, d, psi, ev, stream);
+    case 8: return launch_c<8>(a, d, psi, ev, stream);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -428,7 +428,8 @@ fwd_kernel(FwdArgs a) {
 
 cudaError_t launch_forward(const IndexDims& d, const IndexBuffers& b, const gpf_queries& q,
                            const gpf_query_params& p, int64_t n, float* out, float* z,
-                           unsigned long long* counts, cudaStream_t stream) {
+                           unsigned long long* counts, const KernelEvents& ev,
+                           cudaStream_t stream) {
   if (counts) {
     cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return e;
@@ -477,6 +478,10 @@ cudaError_t launch_forward(const IndexDims& d, const IndexBuffers& b, const gpf_
     }                                                                      \
     note_launches(1);                                                      \
     break;
+  if (ev.start) {
+    const cudaError_t e = cudaEventRecord(ev.start, stream);
+    if (e != cudaSuccess) return e;
+  }
   switch (d.channels) {
     GPF_FWD_CASE(1)
     GPF_FWD_CASE(2)
@@ -492,7 +497,9 @@ cudaError_t launch_forward(const IndexDims& d, const IndexBuffers& b, const gpf_
 #undef GPF_FWD_CASE
 #undef GPF_FWD_MODES
 #undef GPF_FWD_LAUNCH
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return ev.stop ? cudaEventRecord(ev.stop, stream) : cudaSuccess;
 }
 
 }  // namespace gpf

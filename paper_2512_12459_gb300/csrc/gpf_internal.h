@@ -67,14 +67,21 @@ cudaError_t launch_build(const IndexDims& dims, const IndexBuffers& b, const gpf
                          const gpf_queries& q, cudaStream_t stream);
 
 // ---- pair loops (gpf_fwd.cu, gpf_bwd.cu)
+// Events recorded around a pair-loop kernel (either may be null).
+struct KernelEvents {
+  cudaEvent_t start = nullptr;
+  cudaEvent_t stop = nullptr;
+};
 // With counts != null nothing is written but the pair counts (see gpf_count_pairs).
 cudaError_t launch_forward(const IndexDims& dims, const IndexBuffers& b, const gpf_queries& q,
                            const gpf_query_params& p, int64_t n, float* out, float* z,
-                           unsigned long long* counts, cudaStream_t stream);
+                           unsigned long long* counts, const KernelEvents& ev,
+                           cudaStream_t stream);
 cudaError_t launch_backward(const IndexDims& dims, const IndexBuffers& b, const gpf_field& f,
                             const gpf_queries& q, const gpf_query_params& p,
                             const float* grad_out, const float* out, const float* z,
-                            const gpf_field_grad& g, cudaStream_t stream);
+                            const gpf_field_grad& g, const KernelEvents& ev,
+                            cudaStream_t stream);
 
 // ---- loss and optimiser (gpf_optim.cu)
 size_t mse_workspace_bytes(int64_t m);

@@ -126,6 +126,9 @@ def test_host_validation_before_any_launch(lib):
                                     None, None) == 1
     stats = _abi.gpf_index_stats_t()
     assert lib.gpf_index_stats(h, ctypes.byref(stats), None) == 5
+    # timing events: any handles (or none) on a live index, never on NULL
+    assert lib.gpf_index_set_timing_events(None, None, None, None, None) == 1
+    assert lib.gpf_index_set_timing_events(h, None, None, None, None) == 0
     lib.gpf_index_destroy(h)
 
 

@@ -185,6 +185,26 @@ def test_forward_is_bitwise_reproducible(gpf):
     assert np.array_equal(a, b) and np.array_equal(za, zb)
 
 
+def test_timing_events_bracket_the_pair_loops(gpf):
+    """gpf_index_set_timing_events: the events are recorded around the pair
+    loops of both calls and measure a positive time; clearing them stops it."""
+    import torch
+    fnp, qnp = _caustic(30000, seed=23, w=128, h=128)
+    out, z, idx, (field, queries, out_t, z_t) = gpu_fwd(gpf, fnp, qnp, oracle.GPF_SUM, 0.02, 3.0,
+                                                         cell=0.05)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    idx.set_timing_events(fwd=(ev[0], ev[1]), bwd=(ev[2], ev[3]))
+    gpf.gpf_radiance_fwd(idx, field, queries, gpf.GPF_SUM, r_max=0.02, out=out_t, z=z_t)
+    gpf.gpf_radiance_bwd(idx, field, queries, torch.ones_like(out_t), out_t, z_t, gpf.GPF_SUM,
+                         r_max=0.02)
+    torch.cuda.synchronize()
+    assert ev[0].elapsed_time(ev[1]) > 0 and ev[2].elapsed_time(ev[3]) > 0
+    idx.set_timing_events()
+    gpf.gpf_radiance_fwd(idx, field, queries, gpf.GPF_SUM, r_max=0.02, out=out_t, z=z_t)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out_t.cpu().numpy(), out.astype(np.float32))
+
+
 def test_overflow_is_reported_and_outputs_untouched(gpf):
     import torch
     from paper_2512_12459_gb300.setup_index import make_index
