@@ -262,6 +262,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     import paper_2512_12459_gb300 as gpf
+    from paper_2512_12459_gb300 import sharding
     from paper_2512_12459_gb300.setup_index import make_index
 
     fnp, tgt_np, qnp = make_inputs(rank)
@@ -269,6 +270,9 @@ def main():
     queries = gpf.Queries.from_numpy(qnp)
     tgt_field = gpf.Field.from_numpy(tgt_np)
     n_active = int(qnp.valid.sum())
+    # every rank's MSE is normalised by its own valid points; the gradients
+    # are combined with weights n_active / n_total (the MSE over all views)
+    n_total = sharding.global_count(n_active, device="cuda") if world > 1 else n_active
 
     # target radiance: the perturbed field rendered through the same path (outside timing)
     tidx = make_index(tgt_field, queries, query_cell=CELL, cutoff_sigma=CUTOFF)
@@ -309,8 +313,7 @@ def main():
         gpf.gpf_radiance_bwd(idx, field, queries, gout, out, z, gpf.GPF_SUM, r_max=R_MAX,
                              grads=grads)
         if world > 1:
-            for t in grads.tensors():
-                dist.all_reduce(t)
+            sharding.allreduce_gradients(grads.tensors(), n_active, n_total)
         if timed:
             marks[4].record(stream)
         gpf.gpf_adam_step(field, grads, state, lr=LR)
@@ -352,16 +355,8 @@ def main():
     ms = {k: float(np.mean(v)) for k, v in per.items()}
     kernel_ms = {"fwd_kernel": float(np.mean([mk[6].elapsed_time(mk[7]) for mk in all_marks])),
                  "bwd_grid_kernel": float(np.mean([mk[8].elapsed_time(mk[9]) for mk in all_marks]))}
-    step_ms = ms["step"]
-    if world > 1:
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
-        nact = torch.tensor([n_active], device="cuda", dtype=torch.float64)
-        dist.all_reduce(nact)
-        total_q = float(nact.item())
-    else:
-        total_q = float(n_active)
+    step_ms = sharding.max_over_ranks(ms["step"], device="cuda")
+    total_q = float(n_total)
     value = total_q / (step_ms / 1000.0)
 
     # pair counts for the roofline (outside timing)
@@ -391,11 +386,7 @@ def main():
         e1.record(stream)
         e1.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
-    e2e_ms = float(np.mean(e2e_times))
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = sharding.max_over_ranks(float(np.mean(e2e_times)), device="cuda")
 
     peaks, peaks_src = measured_peaks()
     smax = float(peaks.get("sm_max_mhz", 2070.0))
