@@ -241,6 +241,9 @@ gpf_status gpf_index_stats(const gpf_index *index, gpf_index_stats_t *stats,
  *           elsewhere. Keep it for gpf_radiance_bwd in GPF_NORMALIZED mode.
  * Sums run in float32 in a fixed order: results are bitwise reproducible
  * for a given build.
+ * The pair loop is a persistent kernel whose warps take tiles of hit points
+ * from a work counter in the index: calls on one index must be ordered (one
+ * stream, or events between streams).
  * Errors: GPF_ERR_INVALID_ARG, GPF_ERR_NOT_BUILT, GPF_ERR_MISMATCH, GPF_ERR_CUDA.
  */
 gpf_status gpf_radiance_fwd(const gpf_index *index, const gpf_field *field,

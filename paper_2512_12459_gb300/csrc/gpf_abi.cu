@@ -171,6 +171,21 @@ gpf_status check_same(const gpf_index* ix, const gpf_field* f, const gpf_queries
 
 }  // namespace
 
+namespace gpf {
+int64_t persistent_blocks(const void* kernel, int threads, int64_t max_blocks) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
+      sms <= 0 || per_sm <= 0) {
+    cudaGetLastError();  // clear; fall back to one block per work unit
+    return max_blocks > 0 ? max_blocks : 1;
+  }
+  const int64_t resident = (int64_t)sms * per_sm;
+  return std::max<int64_t>(1, std::min<int64_t>(resident, max_blocks));
+}
+}  // namespace gpf
+
 extern "C" {
 
 const char* gpf_version(void) { return "gpf 0.1 (sm_103a)"; }

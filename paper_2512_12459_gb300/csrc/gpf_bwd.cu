@@ -53,6 +53,7 @@ struct BwdArgs {
   int mode;
   float r, r2, inv_rr, eps, cut, cut2;
   gpf_field_grad g;
+  unsigned long long* next_work;  // work counter, zero at launch
 };
 
 template <int C>
@@ -332,17 +333,24 @@ __global__ void __launch_bounds__(kBwdThreads)
 bwd_grid_kernel(BwdArgs a) {
   constexpr int QS = qrec_stride(C);
   const int lane = threadIdx.x & 31;
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (a.header->overflow) return;
   const int64_t n_small = a.header->n_small, n_live = a.header->n_live;
   const int64_t small_warps = (n_small + kWarp - 1) / kWarp;
+  const int64_t units = small_warps + (n_live - n_small);
+  // persistent: every warp takes the next work unit (32 small Gaussians, or
+  // one large one) until none is left
+  for (;;) {
+  unsigned long long w_u = 0;
+  if (lane == 0) w_u = atomicAdd(a.next_work, 1ull);
+  const int64_t w = (int64_t)__shfl_sync(kFullMask, w_u, 0);
+  if (w >= units) break;
   if (w < small_warps) {
     const int64_t idx = w * kWarp + lane;
     if (idx < n_small) bwd_lane_gaussian<C, PSI>(a, idx, a.order[idx]);
-    return;
+    __syncwarp();
+    continue;
   }
   const int64_t j = n_small + (w - small_warps);
-  if (j >= n_live) return;
   const Grid& Gd = a.grid;
   const int64_t gi = a.order[j];
   GaussianRegs G;
@@ -415,6 +423,7 @@ bwd_grid_kernel(BwdArgs a) {
   const float sum = reduce_scatter<Acc<C>::NS>(v, lane, &slot);
   if (Acc<C>::NS == 32 || (lane & 1) == 0) a.gacc[j * Acc<C>::NS + slot] = sum;
   (void)fr;
+  }  // work loop
 }
 
 // Brute-force path (no cell lists): one warp per Gaussian over all active hit points.
@@ -466,13 +475,20 @@ cudaError_t launch_c(const BwdArgs& a, const IndexDims& d, bool psi, const Kerne
   const int64_t warps = d.brute ? a.n : a.n + (a.n + kWarp - 1) / kWarp;
   const unsigned blocks = (unsigned)((warps + kBwdWarps - 1) / kBwdWarps);
   cudaError_t e;
+  if (!d.brute &&
+      (e = cudaMemsetAsync(a.next_work, 0, sizeof(unsigned long long), stream)) != cudaSuccess)
+    return e;
   if (ev.start && (e = cudaEventRecord(ev.start, stream)) != cudaSuccess) return e;
   if (d.brute) {
     if (psi) bwd_brute_kernel<C, true><<<blocks, kBwdThreads, 0, stream>>>(a);
     else bwd_brute_kernel<C, false><<<blocks, kBwdThreads, 0, stream>>>(a);
   } else {
-    if (psi) bwd_grid_kernel<C, true><<<blocks, kBwdThreads, 0, stream>>>(a);
-    else bwd_grid_kernel<C, false><<<blocks, kBwdThreads, 0, stream>>>(a);
+    // persistent: as many blocks as can be resident at once
+    const void* kfn = psi ? reinterpret_cast<const void*>(&bwd_grid_kernel<C, true>)
+                          : reinterpret_cast<const void*>(&bwd_grid_kernel<C, false>);
+    const unsigned pblocks = (unsigned)persistent_blocks(kfn, kBwdThreads, blocks);
+    if (psi) bwd_grid_kernel<C, true><<<pblocks, kBwdThreads, 0, stream>>>(a);
+    else bwd_grid_kernel<C, false><<<pblocks, kBwdThreads, 0, stream>>>(a);
   }
   if (ev.stop && (e = cudaEventRecord(ev.stop, stream)) != cudaSuccess) return e;
   bwd_epilogue_kernel<C><<<(unsigned)((a.n + 255) / 256), 256, 0, stream>>>(a, d.brute ? 1 : 0);
@@ -525,6 +541,7 @@ cudaError_t launch_backward(const IndexDims& d, const IndexBuffers& b, const gpf
   a.cut = d.cutoff;
   a.cut2 = isinf(d.cutoff) ? INFINITY : d.cutoff * d.cutoff;
   a.g = g;
+  a.next_work = &b.header->next_work;
   switch (d.channels) {
     case 1: return launch_c<1>(a, d, psi, ev, stream);
     case 2: return launch_c<2>(a, d, psi, ev, stream);

@@ -27,7 +27,10 @@ struct DeviceHeader {
   uint32_t level_mask;   // bit L set when some Gaussian lives on level L
   uint32_t n_live;       // Gaussians whose level box holds a hit point
   uint32_t n_small;      // live Gaussians spanning <= 2 query-level cells per axis
-  uint32_t pad[58];
+  // work counters of the persistent pair loops (reset before each launch)
+  unsigned long long next_tile;       // forward: next tile of 32 hit points
+  unsigned long long next_work;       // backward: next work item
+  uint32_t pad[54];
 };
 static_assert(sizeof(DeviceHeader) == 256, "header is one 256-byte block");
 

@@ -54,6 +54,7 @@ struct FwdArgs {
   float* out;              // [C,M]
   float* z;                // [M] or null
   unsigned long long* counts;  // count mode: [candidates, included]
+  unsigned long long* next_tile;  // work counter, zero at launch
 };
 
 __device__ __forceinline__ float warp_min(float v) {
@@ -170,11 +171,19 @@ fwd_kernel(FwdArgs a) {
   __shared__ float s_acc[kFwdWarps][C + 1][kWarp];  // pooled-mode sums per hit point
 
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t tile = (int64_t)blockIdx.x * kFwdWarps + wib;
-  const int64_t base = tile * kWarp;
-  if (base >= a.m) return;
   if (a.header->overflow) return;
   const int64_t n_act = a.header->n_active;
+  const int64_t n_tiles = (a.m + kWarp - 1) / kWarp;
+  uint32_t n_eval = 0, n_inc = 0;
+  // persistent: every warp takes the next tile until none is left, so a
+  // warp that drew a light tile goes on with another one
+  for (;;) {
+  __syncwarp();
+  unsigned long long tile_u = 0;
+  if (lane == 0) tile_u = atomicAdd(a.next_tile, 1ull);
+  const int64_t tile = (int64_t)__shfl_sync(kFullMask, tile_u, 0);
+  if (tile >= n_tiles) break;
+  const int64_t base = tile * kWarp;
   const int64_t k = base + lane;
   const bool in_range = k < a.m;
   const bool active = k < n_act;
@@ -184,7 +193,7 @@ fwd_kernel(FwdArgs a) {
     for (int c = 0; c < C; ++c) a.out[(int64_t)c * a.m + q] = 0.0f;
     if (a.z) a.z[q] = 0.0f;
   }
-  if (base >= n_act) return;  // warp-uniform
+  if (base >= n_act) continue;  // warp-uniform
 
   float px = 0.f, py = 0.f, pz = 0.f;
   if (active) {
@@ -196,7 +205,6 @@ fwd_kernel(FwdArgs a) {
 #pragma unroll
   for (int c = 0; c < C; ++c) L[c] = 0.0f;
   float Z = 0.0f;
-  uint32_t n_eval = 0, n_inc = 0;
   float* my_rec = s_rec[wib];
 #pragma unroll
   for (int c = 0; c <= C; ++c) s_acc[wib][c][lane] = 0.0f;
@@ -395,6 +403,25 @@ fwd_kernel(FwdArgs a) {
     }
   }
 
+  if (!COUNT) {
+    // the pooled-mode sums of this lane's hit point
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < C; ++c) L[c] += s_acc[wib][c][lane];
+    Z += s_acc[wib][C][lane];
+    if (active) {
+      float scale = 1.0f;
+      if (a.mode == GPF_NORMALIZED) scale = 1.0f / fmaxf(Z, a.eps);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const float rho = a.albedo ? a.albedo[(int64_t)c * a.m + q] : 1.0f;
+        a.out[(int64_t)c * a.m + q] = rho * (L[c] * scale);
+      }
+      if (a.z) a.z[q] = Z;
+    }
+  }
+  }  // tile loop
+
   if (COUNT) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -405,22 +432,6 @@ fwd_kernel(FwdArgs a) {
       atomicAdd(&a.counts[0], (unsigned long long)n_eval);
       atomicAdd(&a.counts[1], (unsigned long long)n_inc);
     }
-    return;
-  }
-  // the pooled-mode sums of this lane's hit point
-  __syncwarp();
-#pragma unroll
-  for (int c = 0; c < C; ++c) L[c] += s_acc[wib][c][lane];
-  Z += s_acc[wib][C][lane];
-  if (active) {
-    float scale = 1.0f;
-    if (a.mode == GPF_NORMALIZED) scale = 1.0f / fmaxf(Z, a.eps);
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      const float rho = a.albedo ? a.albedo[(int64_t)c * a.m + q] : 1.0f;
-      a.out[(int64_t)c * a.m + q] = rho * (L[c] * scale);
-    }
-    if (a.z) a.z[q] = Z;
   }
 }
 
@@ -459,9 +470,19 @@ cudaError_t launch_forward(const IndexDims& d, const IndexBuffers& b, const gpf_
   a.out = out;
   a.z = z;
   a.counts = counts;
+  a.next_tile = &b.header->next_tile;
+  {
+    const cudaError_t e = cudaMemsetAsync(a.next_tile, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return e;
+  }
   const int64_t tiles = (q.m + kWarp - 1) / kWarp;
-  const unsigned blocks = (unsigned)((tiles + kFwdWarps - 1) / kFwdWarps);
-#define GPF_FWD_LAUNCH(CC, BR, PS, CN) fwd_kernel<CC, BR, PS, CN><<<blocks, kFwdThreads, 0, stream>>>(a)
+  const int64_t want = (tiles + kFwdWarps - 1) / kFwdWarps;
+#define GPF_FWD_LAUNCH(CC, BR, PS, CN)                                                    \
+  do {                                                                                    \
+    const unsigned blocks = (unsigned)persistent_blocks(                                  \
+        reinterpret_cast<const void*>(&fwd_kernel<CC, BR, PS, CN>), kFwdThreads, want);   \
+    fwd_kernel<CC, BR, PS, CN><<<blocks, kFwdThreads, 0, stream>>>(a);                    \
+  } while (0)
 #define GPF_FWD_MODES(CC, BR, PS)                   \
   do {                                              \
     if (counts) GPF_FWD_LAUNCH(CC, BR, false, true); \

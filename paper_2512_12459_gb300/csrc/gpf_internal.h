@@ -14,6 +14,11 @@ inline size_t align_up(size_t b, size_t a = 256) { return (b + a - 1) / a * a; }
 // Host-side count of the kernels this library has launched (gpf_launch_count).
 void note_launches(uint64_t k);
 
+// Blocks of a persistent launch of `kernel` (static shared memory only):
+// the blocks that can be resident on all SMs of the current device at once,
+// at most max_blocks and at least 1.
+int64_t persistent_blocks(const void* kernel, int threads, int64_t max_blocks);
+
 // ---- scan / sort (gpf_sort.cu)
 int64_t scan_partials_count(int64_t n);
 size_t scan_workspace_bytes(int64_t n_max);
