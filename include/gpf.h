@@ -110,6 +110,8 @@ typedef struct gpf_query_params {
  * query_level, a dims[0] x dims[1] x dims[2] grid. Points outside the grid
  * are clamped into its border cells, which keeps the result exact (only
  * slower). */
+#define GPF_MAX_COOP_CELLS 8
+
 typedef struct gpf_grid_config {
   float origin[3];       /* lower corner shared by all levels                */
   float cell_size;       /* c0: cell edge on the finest level, > 0           */
@@ -123,6 +125,11 @@ typedef struct gpf_grid_config {
                             truncation (every Gaussian, no cell lists)       */
   int32_t brute_force;   /* 1: no cell lists; every Gaussian is tested with
                             Q <= k^2 (used to check the culled path)         */
+  int32_t coop_cells;    /* forward tile shape: a tile of 32 hit points walks
+                            a level's lists together when its points fall in
+                            at most this many cells of that level, else each
+                            point's own list is pooled; 1..GPF_MAX_COOP_CELLS,
+                            0 = 4                                            */
   int64_t max_gaussians; /* capacity N_max                                   */
   int64_t max_queries;   /* capacity M_max                                   */
   int64_t max_pairs;     /* capacity of (cell, Gaussian) entries             */
@@ -156,7 +163,12 @@ typedef struct gpf_adam_hparams {
   float lr[4];           /* learning rate per group: mean, quat, logscale,
                             spectrum                                         */
   float beta1, beta2, eps;
-  int32_t step;          /* 1-based index of the update being applied        */
+  int32_t step;          /* 1-based index of the update being applied, or 0
+                            when step_counter is given                        */
+  int64_t *step_counter; /* NULL, or a device int64 holding the number of
+                            updates applied so far: the update uses
+                            t = *step_counter + 1 and then increments it, so
+                            a captured CUDA graph replays correct steps       */
 } gpf_adam_hparams;
 
 /* ------------------------------------------------------------------------ */
@@ -358,7 +370,11 @@ gpf_status gpf_mse_loss_grad_noalloc(int64_t m, int32_t channels, const float *o
  *   grads   gradients from gpf_radiance_bwd.
  *   m, v    first and second moments, same layout as params (a gpf_field_grad
  *           each; zero them before step 1).
- *   hp      host struct; hp->step >= 1.
+ *   hp      host struct; either hp->step >= 1 and hp->step_counter NULL, or
+ *           hp->step == 0 and hp->step_counter a device int64 (8-byte
+ *           aligned) that this call reads and increments on the stream.
+ * One launch over all four tensors (plus one single-thread launch that
+ * increments step_counter when it is given).
  */
 gpf_status gpf_adam_step(const gpf_field *params, const gpf_field_grad *grads,
                          const gpf_field_grad *m, const gpf_field_grad *v,

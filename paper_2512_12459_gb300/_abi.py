@@ -44,7 +44,7 @@ class gpf_grid_config(ctypes.Structure):
     _fields_ = [("origin", c_f32 * 3), ("cell_size", c_f32), ("levels", c_i32),
                 ("max_span", c_i32), ("query_level", c_i32), ("dims", c_i32 * 3),
                 ("hash_bits", c_i32), ("channels", c_i32), ("cutoff_sigma", c_f32), ("brute_force", c_i32),
-                ("max_gaussians", c_i64), ("max_queries", c_i64), ("max_pairs", c_i64)]
+                ("coop_cells", c_i32), ("max_gaussians", c_i64), ("max_queries", c_i64), ("max_pairs", c_i64)]
 
 
 class gpf_index_stats_t(ctypes.Structure):
@@ -59,7 +59,7 @@ class gpf_field_grad(ctypes.Structure):
 
 class gpf_adam_hparams(ctypes.Structure):
     _fields_ = [("lr", c_f32 * 4), ("beta1", c_f32), ("beta2", c_f32), ("eps", c_f32),
-                ("step", c_i32)]
+                ("step", c_i32), ("step_counter", c_vp)]
 
 
 # name -> (restype, argtypes); every symbol include/gpf.h declares

@@ -145,6 +145,7 @@ class GridConfig:
     max_queries: int = 0
     max_pairs: int = 0
     brute_force: bool = False
+    coop_cells: int = 0        # forward tile shape (0 = library default, 4)
 
     def c_struct(self) -> _abi.gpf_grid_config:
         return _abi.gpf_grid_config((ctypes.c_float * 3)(*self.origin), float(self.cell_size),
@@ -152,7 +153,8 @@ class GridConfig:
                                     (ctypes.c_int32 * 3)(*[int(d) for d in self.dims]),
                                     int(self.hash_bits), int(self.channels),
                                     float(self.cutoff_sigma), 1 if self.brute_force else 0,
-                                    int(self.max_gaussians), int(self.max_queries),
+                                    int(self.coop_cells), int(self.max_gaussians),
+                                    int(self.max_queries),
                                     int(self.max_pairs))
 
 
@@ -349,13 +351,23 @@ def gpf_mse_loss_grad(out: torch.Tensor, target: torch.Tensor,
 
 @dataclasses.dataclass
 class AdamState:
+    """First and second moments and the update count. With `step_counter`
+    (a device int64 tensor, see `with_device_counter`) the count lives on the
+    device: each update reads and increments it, which is what a captured
+    CUDA graph of the training step needs; `step` is then not advanced."""
     m: Field
     v: Field
     step: int = 0
+    step_counter: Optional[torch.Tensor] = None
 
     @staticmethod
-    def zeros_like(f: Field) -> "AdamState":
-        return AdamState(Field.zeros_like(f), Field.zeros_like(f), 0)
+    def zeros_like(f: Field, device_counter: bool = False) -> "AdamState":
+        ctr = torch.zeros(1, dtype=torch.int64, device=f.mean.device) if device_counter else None
+        return AdamState(Field.zeros_like(f), Field.zeros_like(f), 0, ctr)
+
+    def updates(self) -> int:
+        """Updates applied so far (reads the device counter when there is one)."""
+        return int(self.step_counter.item()) if self.step_counter is not None else self.step
 
 
 def _grad_struct(f: Field) -> _abi.gpf_field_grad:
@@ -368,9 +380,14 @@ def gpf_adam_step(params: Field, grads: Field, state: AdamState, lr=PAPER_LR, be
     lrs = list(lr) if isinstance(lr, (list, tuple)) else [float(lr)] * 4
     for g, p in zip(grads.tensors() + state.m.tensors() + state.v.tensors(), params.tensors() * 3):
         _need(g, "adam tensor", p.shape[0], p.shape[1])
-    state.step += 1
     fs = params.c_struct()
-    hp = _abi.gpf_adam_hparams((ctypes.c_float * 4)(*lrs), beta1, beta2, eps, state.step)
+    if state.step_counter is not None:
+        hp = _abi.gpf_adam_hparams((ctypes.c_float * 4)(*lrs), beta1, beta2, eps, 0,
+                                   state.step_counter.data_ptr())
+    else:
+        state.step += 1
+        hp = _abi.gpf_adam_hparams((ctypes.c_float * 4)(*lrs), beta1, beta2, eps, state.step,
+                                   None)
     g, m, v = _grad_struct(grads), _grad_struct(state.m), _grad_struct(state.v)
     check(load().gpf_adam_step(ctypes.byref(fs), ctypes.byref(g), ctypes.byref(m),
                                ctypes.byref(v), ctypes.byref(hp), _stream(stream)),

@@ -234,6 +234,9 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
     return fail(GPF_ERR_INVALID_ARG, "cutoff_sigma must be > 0 (or +INF)");
   if (cfg->brute_force != 0 && cfg->brute_force != 1)
     return fail(GPF_ERR_INVALID_ARG, "brute_force must be 0 or 1");
+  if (cfg->coop_cells < 0 || cfg->coop_cells > GPF_MAX_COOP_CELLS)
+    return fail(GPF_ERR_INVALID_ARG, "coop_cells = %d outside 0..%d", cfg->coop_cells,
+                GPF_MAX_COOP_CELLS);
   if (cfg->max_gaussians < 0 || cfg->max_queries < 0 || cfg->max_pairs < 0)
     return fail(GPF_ERR_INVALID_ARG, "capacities must be >= 0");
   if (cfg->max_gaussians >= (int64_t)kIdMask || cfg->max_queries >= (int64_t)0xffffffffLL ||
@@ -254,6 +257,7 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
   d.grid.inv_cell0 = 1.0f / cfg->cell_size;
   d.grid.levels = cfg->levels;
   d.grid.max_span = cfg->max_span;
+  d.grid.coop = cfg->coop_cells ? cfg->coop_cells : 4;
   d.grid.qlevel = cfg->query_level;
   d.grid.hash_bits = cfg->hash_bits;
   d.grid.n_buckets = 1u << cfg->hash_bits;
@@ -482,7 +486,13 @@ gpf_status gpf_adam_step(const gpf_field* params, const gpf_field_grad* grads,
   if (params->n < 0) return fail(GPF_ERR_INVALID_ARG, "params.n < 0");
   if (params->channels < 1 || params->channels > GPF_MAX_CHANNELS)
     return fail(GPF_ERR_INVALID_ARG, "params.channels outside 1..%d", GPF_MAX_CHANNELS);
-  if (hp->step < 1) return fail(GPF_ERR_INVALID_ARG, "hp.step = %d < 1", hp->step);
+  if (hp->step_counter) {
+    if (hp->step != 0) return fail(GPF_ERR_INVALID_ARG, "hp.step must be 0 with a step_counter");
+    if (!aligned(hp->step_counter, 8))
+      return fail(GPF_ERR_INVALID_ARG, "hp.step_counter is not 8-byte aligned");
+  } else if (hp->step < 1) {
+    return fail(GPF_ERR_INVALID_ARG, "hp.step = %d < 1", hp->step);
+  }
   if (!(hp->beta1 >= 0.0f && hp->beta1 < 1.0f) || !(hp->beta2 >= 0.0f && hp->beta2 < 1.0f))
     return fail(GPF_ERR_INVALID_ARG, "betas must lie in [0, 1)");
   if (!(hp->eps >= 0.0f)) return fail(GPF_ERR_INVALID_ARG, "eps must be >= 0");

@@ -93,6 +93,7 @@ struct Grid {
   int oshift;              // level whose cells order the backward's Gaussians
   uint32_t odx, ody;       // cells per axis on that level
   int obits;               // bits of an order key (cell key and 2 class bits)
+  int coop;                // forward: cooperative mode up to this many cells
 };
 
 // Level-0 cell coordinate of v along one axis: floor((v - o) / c0) in float32,

@@ -30,9 +30,9 @@ namespace {
 
 constexpr int kFwdWarps = 4;
 constexpr int kFwdThreads = kFwdWarps * kWarp;
-// A tile whose hit points fall in at most this many cells of a level walks
-// that level cooperatively.
-constexpr int kUnionMax = 4;
+// A tile whose hit points fall in at most Grid::coop cells of a level walks
+// that level cooperatively; kUnionMax bounds that threshold.
+constexpr int kUnionMax = GPF_MAX_COOP_CELLS;
 
 struct FwdArgs {
   Grid grid;
@@ -261,7 +261,7 @@ fwd_kernel(FwdArgs a) {
       const bool leader = active && (peers & lanemask_lt()) == 0;
       const uint32_t uniq = __ballot_sync(kFullMask, leader);
       const int nu = __popc(uniq);
-      if (nu <= kUnionMax) {
+      if (nu <= G.coop) {
         // ---- warp-cooperative mode over the tile's distinct cells
         if (leader) {
           const int slot = __popc(uniq & lanemask_lt());

@@ -77,31 +77,70 @@ __global__ void mse_grad_kernel(int64_t m, int channels, const float* __restrict
   }
 }
 
-struct AdamGroup {
-  float* p;
-  const float* g;
-  float* m;
-  float* v;
-  int64_t count;
-  float step_size;   // lr / (1 - b1^t)
+// The four parameter tensors as one index space: element i belongs to tensor
+// k with end[k-1] <= i < end[k] (in units of 4 floats when vectorised).
+struct AdamArgs {
+  float* p[4];
+  const float* g[4];
+  float* m[4];
+  float* v[4];
+  int64_t end[4];
+  float lr[4];
+  float b1, b2, eps;
+  int64_t t_host;            // update index when counter is null
+  const int64_t* counter;    // device count of updates applied, or null
 };
 
 // torch.optim.Adam's update order: m += (1-b1)(g-m); v = b2 v + (1-b2) g^2;
 // p -= step_size * m / (sqrt(v)/sqrt(1-b2^t) + eps)
-__global__ void adam_kernel(AdamGroup grp, float b1, float b2, float eps, float inv_bc2_sqrt) {
+__device__ __forceinline__ float adam_one(float g, float& m, float& v, float p, float b1, float b2,
+                                          float eps, float step_size, float inv_bc2_sqrt) {
+  m = fmaf(1.0f - b1, g - m, m);
+  v = fmaf(1.0f - b2, g * g, b2 * v);
+  const float denom = sqrtf(v) * inv_bc2_sqrt + eps;
+  return p - step_size * (m / denom);
+}
+
+template <bool VEC>
+__global__ void adam_kernel(AdamArgs a) {
+  __shared__ float s_step[4];
+  __shared__ float s_inv_bc2_sqrt;
+  if (threadIdx.x == 0) {
+    const int64_t t = a.counter ? *a.counter + 1 : a.t_host;
+    const double bc1 = 1.0 - pow((double)a.b1, (double)t);
+    const double bc2 = 1.0 - pow((double)a.b2, (double)t);
+    for (int k = 0; k < 4; ++k) s_step[k] = (float)((double)a.lr[k] / bc1);
+    s_inv_bc2_sqrt = (float)(1.0 / sqrt(bc2));
+  }
+  __syncthreads();
+  const float ib = s_inv_bc2_sqrt;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < grp.count; i += stride) {
-    const float g = grp.g[i];
-    float m = grp.m[i];
-    float v = grp.v[i];
-    m = fmaf(1.0f - b1, g - m, m);
-    v = fmaf(1.0f - b2, g * g, b2 * v);
-    const float denom = sqrtf(v) * inv_bc2_sqrt + eps;
-    grp.p[i] = grp.p[i] - grp.step_size * (m / denom);
-    grp.m[i] = m;
-    grp.v[i] = v;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.end[3]; i += stride) {
+    const int k = (i >= a.end[0]) + (i >= a.end[1]) + (i >= a.end[2]);
+    const int64_t j = i - (k ? a.end[k - 1] : 0);
+    const float ss = s_step[k];
+    if (VEC) {
+      const float4 g = reinterpret_cast<const float4*>(a.g[k])[j];
+      float4 m = reinterpret_cast<float4*>(a.m[k])[j];
+      float4 v = reinterpret_cast<float4*>(a.v[k])[j];
+      float4 p = reinterpret_cast<float4*>(a.p[k])[j];
+      p.x = adam_one(g.x, m.x, v.x, p.x, a.b1, a.b2, a.eps, ss, ib);
+      p.y = adam_one(g.y, m.y, v.y, p.y, a.b1, a.b2, a.eps, ss, ib);
+      p.z = adam_one(g.z, m.z, v.z, p.z, a.b1, a.b2, a.eps, ss, ib);
+      p.w = adam_one(g.w, m.w, v.w, p.w, a.b1, a.b2, a.eps, ss, ib);
+      reinterpret_cast<float4*>(a.p[k])[j] = p;
+      reinterpret_cast<float4*>(a.m[k])[j] = m;
+      reinterpret_cast<float4*>(a.v[k])[j] = v;
+    } else {
+      float m = a.m[k][j], v = a.v[k][j];
+      a.p[k][j] = adam_one(a.g[k][j], m, v, a.p[k][j], a.b1, a.b2, a.eps, ss, ib);
+      a.m[k][j] = m;
+      a.v[k][j] = v;
+    }
   }
 }
+
+__global__ void adam_count_kernel(int64_t* counter) { *counter += 1; }
 
 }  // namespace
 
@@ -139,20 +178,39 @@ cudaError_t launch_adam(const gpf_field& params, const gpf_field_grad& g, const 
                         const gpf_field_grad& v, const gpf_adam_hparams& hp, cudaStream_t stream) {
   const int64_t n = params.n;
   if (n == 0) return cudaSuccess;
-  const double bc1 = 1.0 - pow((double)hp.beta1, (double)hp.step);
-  const double bc2 = 1.0 - pow((double)hp.beta2, (double)hp.step);
-  const float inv_bc2_sqrt = (float)(1.0 / sqrt(bc2));
+  AdamArgs a;
   float* P[4] = {const_cast<float*>(params.mean), const_cast<float*>(params.quat),
                  const_cast<float*>(params.logscale), const_cast<float*>(params.spectrum)};
   const float* G[4] = {g.mean, g.quat, g.logscale, g.spectrum};
   float* Mm[4] = {m.mean, m.quat, m.logscale, m.spectrum};
   float* Vv[4] = {v.mean, v.quat, v.logscale, v.spectrum};
   const int64_t rows[4] = {3, 4, 3, params.channels};
+  // float4 when every tensor holds a multiple of 4 floats on 16-byte boundaries
+  bool vec = n % 4 == 0;
+  for (int k = 0; k < 4; ++k)
+    vec = vec && ((uintptr_t)P[k] | (uintptr_t)G[k] | (uintptr_t)Mm[k] | (uintptr_t)Vv[k]) % 16 == 0;
+  const int64_t unit = vec ? 4 : 1;
+  int64_t acc = 0;
   for (int k = 0; k < 4; ++k) {
-    AdamGroup grp{P[k], G[k], Mm[k], Vv[k], rows[k] * n, (float)(hp.lr[k] / bc1)};
-    const int64_t blocks = std::min<int64_t>((grp.count + 255) / 256, 152 * 16);
-    adam_kernel<<<(unsigned)blocks, 256, 0, stream>>>(grp, hp.beta1, hp.beta2, hp.eps,
-                                                      inv_bc2_sqrt);
+    a.p[k] = P[k];
+    a.g[k] = G[k];
+    a.m[k] = Mm[k];
+    a.v[k] = Vv[k];
+    a.lr[k] = hp.lr[k];
+    acc += rows[k] * n / unit;
+    a.end[k] = acc;
+  }
+  a.b1 = hp.beta1;
+  a.b2 = hp.beta2;
+  a.eps = hp.eps;
+  a.t_host = hp.step;
+  a.counter = hp.step_counter;
+  const int64_t blocks = std::min<int64_t>((acc + 255) / 256, 152 * 8);
+  if (vec) adam_kernel<true><<<(unsigned)blocks, 256, 0, stream>>>(a);
+  else adam_kernel<false><<<(unsigned)blocks, 256, 0, stream>>>(a);
+  note_launches(1);
+  if (hp.step_counter) {
+    adam_count_kernel<<<1, 1, 0, stream>>>(hp.step_counter);
     note_launches(1);
   }
   return cudaGetLastError();

@@ -11,6 +11,7 @@ computation runs in libgpf."""
 
 from __future__ import annotations
 
+import dataclasses
 import math
 from typing import Optional, Sequence
 
@@ -93,13 +94,16 @@ def make_index(field: Field, queries: Queries, cutoff_sigma: float = 3.0,
                bounds: Optional[Sequence] = None, max_gaussians: Optional[int] = None,
                max_queries: Optional[int] = None, headroom: float = 1.1, max_span: int = 4,
                query_cell: Optional[float] = None, hash_bits: Optional[int] = None,
-               grid: Optional[GridConfig] = None) -> Index:
+               grid: Optional[GridConfig] = None, coop_cells: int = 0) -> Index:
     """An index planned for (field, queries). With max_pairs=None the pair
     capacity comes from a trial build (gpf_index_stats) times `headroom`
     (room for the pairs to grow while the parameters are optimised)."""
     if grid is None:
         grid = plan_grid(field, queries, cutoff_sigma, max_span, query_cell, hash_bits, bounds,
                          brute_force=brute_force)
+        grid.coop_cells = coop_cells
+    else:
+        grid = dataclasses.replace(grid)     # capacities below are this index's own
     grid.max_gaussians = max_gaussians if max_gaussians is not None else max(field.n, 1)
     grid.max_queries = max_queries if max_queries is not None else max(queries.m, 1)
     brute = brute_force or math.isinf(cutoff_sigma)
@@ -116,3 +120,67 @@ def make_index(field: Field, queries: Queries, cutoff_sigma: float = 3.0,
         grid.max_pairs = want
         idx = Index(grid, device=field.mean.device)
     return idx
+
+
+def time_step(index: Index, field: Field, queries: Queries, mode: int = 0, r_max: float = 0.02,
+              repeats: int = 3) -> float:
+    """Median milliseconds of build + forward + backward with `index`."""
+    from . import api
+    out = torch.empty((field.channels, queries.m), device=field.mean.device)
+    z = torch.empty((queries.m,), device=field.mean.device)
+    gout = torch.ones_like(out)
+    grads = Field.zeros_like(field)
+    times = []
+    for i in range(repeats + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        index.build(field, queries)
+        api.gpf_radiance_fwd(index, field, queries, mode, r_max=r_max, out=out, z=z)
+        api.gpf_radiance_bwd(index, field, queries, gout, out, z, mode, r_max=r_max, grads=grads)
+        e1.record()
+        e1.synchronize()
+        if i:                       # the first run pays one-off costs
+            times.append(e0.elapsed_time(e1))
+    return float(sorted(times)[len(times) // 2])
+
+
+def autotune(field: Field, queries: Queries, cutoff_sigma: float = 3.0, mode: int = 0,
+             r_max: float = 0.02, query_cells: Optional[Sequence[float]] = None,
+             max_spans: Sequence[int] = (3, 4, 6), coop_options: Sequence[int] = (2, 4, 8),
+             repeats: int = 3, headroom: float = 1.25):
+    """Chooses the grid geometry and the forward tile shape for this field
+    and batch of hit points by timing build + forward + backward, one knob at
+    a time: the query cell size (the hit-point grid), then the largest span of
+    a Gaussian's box in cells of its level (the cell size of every level),
+    then the cooperative-mode threshold of the forward's 32-point tiles.
+    Returns (best GridConfig, report), report = [(knobs, ms), ...] in the
+    order tried. Results are independent of the choice; only speed differs."""
+    if query_cells is None:
+        query_cells = (0.01, 0.02, 0.04, 0.08)
+    best = {"query_cell": 0.02, "max_span": 4, "coop_cells": 4}
+    report = []
+    cache = {}
+
+    def trial(knobs):
+        key = tuple(sorted(knobs.items()))
+        if key not in cache:
+            idx = make_index(field, queries, cutoff_sigma=cutoff_sigma, headroom=headroom,
+                             query_cell=knobs["query_cell"], max_span=knobs["max_span"],
+                             coop_cells=knobs["coop_cells"])
+            ms = time_step(idx, field, queries, mode, r_max, repeats)
+            cache[key] = (ms, idx.grid)
+            report.append((dict(knobs), ms))
+            del idx
+            torch.cuda.empty_cache()
+        return cache[key][0]
+
+    for name, options in (("query_cell", query_cells), ("max_span", max_spans),
+                          ("coop_cells", coop_options)):
+        scores = {}
+        for v in options:
+            knobs = dict(best, **{name: v})
+            scores[v] = trial(knobs)
+        best[name] = min(scores, key=lambda v: (scores[v], v))
+    grid = cache[tuple(sorted(best.items()))][1]
+    return grid, report

@@ -49,7 +49,7 @@ def test_version_and_status_strings(lib):
 def _cfg(**kw):
     from paper_2512_12459_gb300 import _abi
     c = _abi.gpf_grid_config((ctypes.c_float * 3)(0, 0, 0), 0.1, 4, 4, 0,
-                             (ctypes.c_int32 * 3)(10, 10, 10), 16, 3, 3.0, 0, 100, 200, 1000)
+                             (ctypes.c_int32 * 3)(10, 10, 10), 16, 3, 3.0, 0, 0, 100, 200, 1000)
     for k, v in kw.items():
         if k == "dims":
             c.dims = (ctypes.c_int32 * 3)(*v)
@@ -64,7 +64,8 @@ def _cfg(**kw):
                                  dict(brute_force=2), dict(max_pairs=-5),
                                  dict(dims=(1024, 1024, 1024)), dict(levels=0), dict(levels=17),
                                  dict(max_span=0), dict(hash_bits=7), dict(hash_bits=29),
-                                 dict(query_level=16), dict(query_level=11, dims=(1024, 4, 4))])
+                                 dict(query_level=16), dict(query_level=11, dims=(1024, 4, 4)),
+                                 dict(coop_cells=-1), dict(coop_cells=9)])
 def test_index_create_rejects_bad_configs(lib, bad):
     h = ctypes.c_void_p()
     cfg = _cfg(**bad)
@@ -148,6 +149,14 @@ def test_loss_and_adam_validation(lib):
     hp.step, hp.beta1 = 1, 1.0
     assert lib.gpf_adam_step(ctypes.byref(f), ctypes.byref(g), ctypes.byref(g), ctypes.byref(g),
                              ctypes.byref(hp), None) == 1
+    # a device step counter: step must be 0 and the counter 8-byte aligned
+    hp.beta1, hp.step, hp.step_counter = 0.9, 1, fake
+    assert lib.gpf_adam_step(ctypes.byref(f), ctypes.byref(g), ctypes.byref(g), ctypes.byref(g),
+                             ctypes.byref(hp), None) == 1
+    hp.step, hp.step_counter = 0, fake + 4
+    assert lib.gpf_adam_step(ctypes.byref(f), ctypes.byref(g), ctypes.byref(g), ctypes.byref(g),
+                             ctypes.byref(hp), None) == 1
+    assert b"step_counter" in lib.gpf_last_error()
 
 
 def test_package_defaults_are_the_papers(lib):

@@ -136,6 +136,27 @@ def test_adam_matches_oracle(gpf):
         np.testing.assert_allclose(t.cpu().numpy(), r, rtol=0, atol=5e-6)
 
 
+@pytest.mark.parametrize("n", [1000, 1001])
+def test_adam_device_counter_equals_host_steps(gpf, n):
+    """The device step counter (for graph replay) gives the host-step updates
+    bitwise, on the vectorised (n % 4 == 0) and the scalar path."""
+    import torch
+    rng = np.random.default_rng(37)
+    fnp, _ = synth.config1_random(seed=37, n=n, m=10)
+    pa, pb = gpf.Field.from_numpy(fnp), gpf.Field.from_numpy(fnp)
+    sa = gpf.AdamState.zeros_like(pa)
+    sb = gpf.AdamState.zeros_like(pb, device_counter=True)
+    for _ in range(7):
+        gr = gpf.Field(*(torch.as_tensor(rng.standard_normal(t.shape).astype(np.float32),
+                                         device="cuda") for t in pa.tensors()))
+        gpf.gpf_adam_step(pa, gr, sa, lr=[5e-4, 1e-3, 2e-3, 5e-4])
+        gpf.gpf_adam_step(pb, gr, sb, lr=[5e-4, 1e-3, 2e-3, 5e-4])
+    assert sa.updates() == 7 and sb.updates() == 7
+    for x, y in zip(pa.tensors() + sa.m.tensors() + sa.v.tensors(),
+                    pb.tensors() + sb.m.tensors() + sb.v.tensors()):
+        assert torch.equal(x, y)
+
+
 def test_autograd_function_matches_direct_calls(gpf):
     import torch
     from paper_2512_12459_gb300.setup_index import make_index
