@@ -228,6 +228,113 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """Many views of uneven resolution in one batch: the autotuned index, the
+    whole step (build, forward, MSE, backward, Adam) captured once as a CUDA
+    graph and replayed, against the same step as one launch sequence per view.
+    One GPU; inputs (several GB) are larger than L2."""
+    import torch
+    import synth
+    import paper_2512_12459_gb300 as gpf
+    from paper_2512_12459_gb300.setup_index import autotune, make_index
+    from paper_2512_12459_gb300.train import TrainStep, per_view_step
+
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    pos, flux = synth.caustic_photons(args.batched_photons, seed=0)
+    fnp = synth.field_from_photons(pos, flux, seed=0)
+    tgt_np = synth.perturbed_copy(fnp, seed=1)
+    qnp = synth.uneven_views(args.batched_views, seed=0)
+    gen_s = time.time() - t0
+    field = gpf.Field.from_numpy(fnp)
+    queries = gpf.Queries.from_numpy(qnp)
+    offs = qnp.view_offsets
+    n_active = int(qnp.valid.sum())
+
+    tf = gpf.Field.from_numpy(tgt_np)
+    tidx = make_index(tf, queries, query_cell=CELL)
+    tidx.build(tf, queries)
+    target, _ = gpf.gpf_radiance_fwd(tidx, tf, queries, gpf.GPF_SUM, r_max=R_MAX)
+    target = target.clone()
+    del tidx, tf
+    torch.cuda.empty_cache()
+
+    t0 = time.time()
+    grid, report = autotune(field, queries, r_max=R_MAX, repeats=2)
+    tune_s = time.time() - t0
+    idx = make_index(field, queries, grid=grid, headroom=1.25)
+    step = TrainStep(field, queries, target, idx, r_max=R_MAX, lr=LR)
+    step.capture(warmup=args.warmup)
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    launches0 = gpf.gpf_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    e1.synchronize()
+    graph_ms = e0.elapsed_time(e1) / args.steps
+    graph_launches = gpf.gpf_launch_count() - launches0   # replays launch nothing from the host
+    st = idx.stats()
+    if st["overflow"]:
+        raise RuntimeError(f"pair buffer overflow: {st}")
+
+    # the per-view baseline: one index (capacity of the largest view), one
+    # launch sequence per view, the same field and Adam
+    views = [gpf.Queries.from_numpy(synth.subset_queries(qnp, np.arange(offs[v], offs[v + 1])))
+             for v in range(len(offs) - 1)]
+    vt = [target[:, offs[v]:offs[v + 1]].contiguous() for v in range(len(offs) - 1)]
+    big = int(np.argmax(np.diff(offs)))
+    # a view occupies a subset of the batch's cells: its entries fit the batch's count
+    pidx = make_index(field, views[big], grid=grid, max_queries=int(np.diff(offs).max()),
+                      max_pairs=int(st["n_pairs"] * 1.25) + 1024)
+    pf = gpf.Field(*(t.clone() for t in field.tensors()))
+    pstate = gpf.AdamState.zeros_like(pf, device_counter=True)
+    pgrads = gpf.Field.zeros_like(pf)
+    outs = [torch.empty_like(t) for t in vt]
+    zs = [torch.empty((v.m,), device="cuda") for v in views]
+    gouts = [torch.empty_like(t) for t in vt]
+    pidxs = [pidx] * len(views)
+    for _ in range(args.warmup):
+        per_view_step(pf, views, vt, pidxs, pstate, pgrads, outs, zs, gouts, r_max=R_MAX, lr=LR)
+    torch.cuda.synchronize()
+    launches0 = gpf.gpf_launch_count()
+    e0.record()
+    for _ in range(args.steps):
+        per_view_step(pf, views, vt, pidxs, pstate, pgrads, outs, zs, gouts, r_max=R_MAX, lr=LR)
+    e1.record()
+    e1.synchronize()
+    view_ms = e0.elapsed_time(e1) / args.steps
+    view_launches = (gpf.gpf_launch_count() - launches0) / args.steps
+    if pidx.stats()["overflow"]:
+        raise RuntimeError("per-view pair buffer overflow")
+
+    line = {
+        "metric": METRIC, "value": n_active / (graph_ms / 1e3), "unit": "queries/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": graph_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{len(offs) - 1} uneven views (sides 256..1024), "
+                               f"{fnp.n:,} Gaussians, one batch, CUDA graph",
+                   "hit_points": int(qnp.m), "active_hit_points": n_active,
+                   "gaussians": fnp.n, "l2": "inputs larger than L2"},
+        "per_view": {"value": n_active / (view_ms / 1e3), "ms_per_step": view_ms,
+                     "launches_per_step": view_launches},
+        "graph_vs_per_view": view_ms / graph_ms,
+        "graph_host_launches_per_step": graph_launches / args.steps,
+        "autotuned": {"query_cell": grid.cell_size * (1 << grid.query_level),
+                      "query_level": grid.query_level, "max_span": grid.max_span,
+                      "coop_cells": grid.coop_cells, "levels": grid.levels,
+                      "hash_bits": grid.hash_bits},
+        "autotune_trials": [[k, round(ms, 3)] for k, ms in report],
+        "setup_s": {"generate": round(gen_s, 1), "autotune": round(tune_s, 1)},
+        "index": {"n_pairs": st["n_pairs"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global N_PHOTONS, VIEW, WORKLOAD
     ap = argparse.ArgumentParser()
@@ -241,6 +348,11 @@ def main():
     ap.add_argument("--photons", type=int, default=N_PHOTONS,
                     help="Gaussians (smaller cases are for profiling only)")
     ap.add_argument("--view", type=int, default=VIEW, help="view side in pixels")
+    ap.add_argument("--workload", default="single", choices=["single", "batched"],
+                    help="single: the 1M-Gaussian 1024x1024 step (default line); batched: "
+                         "64 uneven views over 2M Gaussians, graph replay vs per-view launches")
+    ap.add_argument("--batched-views", type=int, default=64)
+    ap.add_argument("--batched-photons", type=int, default=2_000_000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if (args.photons, args.view) != (N_PHOTONS, VIEW):
@@ -254,6 +366,9 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    if args.workload == "batched":
+        run_batched(args)
+        return
 
     import torch
     import torch.distributed as dist
@@ -263,7 +378,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     import paper_2512_12459_gb300 as gpf
     from paper_2512_12459_gb300 import sharding
-    from paper_2512_12459_gb300.setup_index import make_index
+    from paper_2512_12459_gb300.setup_index import autotune, make_index
 
     fnp, tgt_np, qnp = make_inputs(rank)
     field = gpf.Field.from_numpy(fnp)
@@ -281,8 +396,11 @@ def main():
     target = target.clone()
     del tidx
 
-    # headroom for the pairs to grow as Adam moves the Gaussians
-    idx = make_index(field, queries, query_cell=CELL, cutoff_sigma=CUTOFF, headroom=1.25)
+    # grid geometry and forward tile shape chosen by timing candidates on this
+    # scene (outside the timed region); headroom for the pairs to grow as
+    # Adam moves the Gaussians
+    tuned, _ = autotune(field, queries, cutoff_sigma=CUTOFF, r_max=R_MAX, repeats=2)
+    idx = make_index(field, queries, grid=tuned, headroom=1.25)
     state = gpf.AdamState.zeros_like(field)
     grads = gpf.Field(*(torch.empty_like(t) for t in field.tensors()))
     out = torch.empty((3, queries.m), device="cuda")
@@ -429,7 +547,11 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "global_batch": int(total_q), "seq_len": None,
                        "parallelism": f"dp{world}", "hit_points_per_gpu": n_active,
-                       "gaussians": fnp.n, "query_cell": CELL, "levels": idx.grid.levels, "finest_cell": idx.grid.cell_size, "l2": "flushed between steps"},
+                       "gaussians": fnp.n, "l2": "flushed between steps",
+                       "grid": {"query_cell": idx.grid.cell_size * (1 << idx.grid.query_level),
+                                "levels": idx.grid.levels, "finest_cell": idx.grid.cell_size,
+                                "max_span": idx.grid.max_span,
+                                "coop_cells": idx.grid.coop_cells, "autotuned": True}},
             "fwd_queries_per_s": n_active / (ms["fwd"] / 1e3),
             "fwd_bwd_queries_per_s": n_active / ((ms["fwd"] + ms["bwd"] + ms["loss"]) / 1e3),
             "ms_breakdown": {k: v for k, v in ms.items() if k != "step"},
