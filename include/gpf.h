@@ -73,15 +73,45 @@ typedef enum gpf_mode { GPF_SUM = 0, GPF_NORMALIZED = 1 } gpf_mode;
 /* Maximum number of grid levels. */
 #define GPF_MAX_LEVELS 16
 
-/* The Gaussian Photon Field (Sec. 4.1). All arrays [rows, n], float32. */
+/* Storage of a field's parameter arrays (gpf_field.storage). */
+#define GPF_F32 0
+#define GPF_BF16 1
+#define GPF_BF16_MEAN32 2
+/* Gaussians per anchor group of the GPF_BF16 storage. */
+#define GPF_BF16_GROUP 16
+
+/* The Gaussian Photon Field (Sec. 4.1). Arrays [rows, n].
+ *
+ * storage GPF_F32: float32 arrays as named; anchor NULL.
+ * storage GPF_BF16 (16-bit storage, float32 arithmetic): the four arrays hold
+ *   bfloat16 values (uint16, the upper half of a float32), and anchor holds
+ *   float32 [ceil(N/16), 4], 16-byte aligned: for each group j of
+ *   GPF_BF16_GROUP consecutive Gaussians (16j .. 16j+15) four consecutive
+ *   floats, an origin (x, y, z) and a log-scale reference l_ref.
+ *   The decoded float32 parameters are
+ *     mu_k = origin_k + f32(mean_k)          (means as offsets from the origin)
+ *     l_k  = l_ref + f32(logscale_k)         (log-scales as offsets)
+ *     q, Phi = f32(quat), f32(spectrum)
+ *   (float32 additions). gpf_build_index decodes them once per build; every
+ *   later step computes in float32 on the decoded values, and gradients are
+ *   with respect to the decoded values. A group should be compact in space
+ *   (order the Gaussians spatially, e.g. by the Morton code of the means):
+ *   the offsets then carry bfloat16's 8 significant bits on a small range.
+ *   gpf_field_quantize writes this form from a float32 field.
+ * storage GPF_BF16_MEAN32: as GPF_BF16, except that mean holds the float32
+ *   means themselves (anchors still carry the log-scale references; their
+ *   origins are unused). Eight significant bits cannot place a mean to the
+ *   few 1e-4 of its own scale that a 1e-3 radiance error needs; this form
+ *   keeps that precision and stores the rest in 16 bits. */
 typedef struct gpf_field {
   int64_t n;             /* number of Gaussians N >= 0                       */
   int32_t channels;      /* C, 1..GPF_MAX_CHANNELS                           */
-  int32_t reserved;      /* must be 0                                        */
-  const float *mean;     /* [3,N] mu                                         */
-  const float *quat;     /* [4,N] (w,x,y,z), any non-zero norm               */
-  const float *logscale; /* [3,N] l, scale s = exp(l)                        */
-  const float *spectrum; /* [C,N] Phi                                        */
+  int32_t storage;       /* GPF_F32, GPF_BF16 or GPF_BF16_MEAN32             */
+  const void *mean;      /* [3,N] mu                                         */
+  const void *quat;      /* [4,N] (w,x,y,z), any non-zero norm               */
+  const void *logscale;  /* [3,N] l, scale s = exp(l)                        */
+  const void *spectrum;  /* [C,N] Phi                                        */
+  const float *anchor;   /* GPF_BF16: [ceil(N/16), 4]; GPF_F32: NULL         */
 } gpf_field;
 
 /* Camera-ray hit points (first diffuse hits, Sec. 4.2). */
@@ -130,6 +160,9 @@ typedef struct gpf_grid_config {
                             at most this many cells of that level, else each
                             point's own list is pooled; 1..GPF_MAX_COOP_CELLS,
                             0 = 4                                            */
+  int32_t field_storage; /* storage of the fields built from: GPF_F32,
+                            GPF_BF16 or GPF_BF16_MEAN32 (the 16-bit forms
+                            reserve float32 decode arrays)                   */
   int64_t max_gaussians; /* capacity N_max                                   */
   int64_t max_queries;   /* capacity M_max                                   */
   int64_t max_pairs;     /* capacity of (cell, Gaussian) entries             */
@@ -379,6 +412,23 @@ gpf_status gpf_mse_loss_grad_noalloc(int64_t m, int32_t channels, const float *o
 gpf_status gpf_adam_step(const gpf_field *params, const gpf_field_grad *grads,
                          const gpf_field_grad *m, const gpf_field_grad *v,
                          const gpf_adam_hparams *hp, gpf_stream stream);
+
+/*
+ * gpf_field_quantize - the GPF_BF16 form of a float32 field (a facility of
+ * the 16-bit storage; the paper keeps float32 parameters). Used after each
+ * Adam update of a float32 master copy.
+ *   src  GPF_F32 field of N Gaussians (device arrays, read).
+ *   dst  GPF_BF16 or GPF_BF16_MEAN32 field with the same n and channels;
+ *        its arrays (uint16, or float32 means for GPF_BF16_MEAN32) and its
+ *        anchor array are written.
+ * For every group of GPF_BF16_GROUP consecutive Gaussians: origin = midpoint
+ * of the group's smallest and largest mean per axis, l_ref = midpoint of the
+ * smallest and largest of its 3 x 16 log-scales (float32 (lo + hi) * 0.5);
+ * offsets are float32 differences; every stored value is the float32 value
+ * rounded to the nearest bfloat16, ties to even. One launch.
+ * Errors: GPF_ERR_INVALID_ARG, GPF_ERR_CUDA.
+ */
+gpf_status gpf_field_quantize(const gpf_field *src, const gpf_field *dst, gpf_stream stream);
 
 #ifdef __cplusplus
 }

@@ -22,13 +22,18 @@ GPF_NORMALIZED = 1
 GPF_MAX_CHANNELS = 8
 GPF_MAX_DIM = 1024
 GPF_MAX_LEVELS = 16
+GPF_MAX_COOP_CELLS = 8
+GPF_F32 = 0
+GPF_BF16 = 1
+GPF_BF16_MEAN32 = 2
+GPF_BF16_GROUP = 16
 
 c_i32, c_i64, c_f32, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p
 
 
 class gpf_field(ctypes.Structure):
-    _fields_ = [("n", c_i64), ("channels", c_i32), ("reserved", c_i32), ("mean", c_vp),
-                ("quat", c_vp), ("logscale", c_vp), ("spectrum", c_vp)]
+    _fields_ = [("n", c_i64), ("channels", c_i32), ("storage", c_i32), ("mean", c_vp),
+                ("quat", c_vp), ("logscale", c_vp), ("spectrum", c_vp), ("anchor", c_vp)]
 
 
 class gpf_queries(ctypes.Structure):
@@ -44,7 +49,7 @@ class gpf_grid_config(ctypes.Structure):
     _fields_ = [("origin", c_f32 * 3), ("cell_size", c_f32), ("levels", c_i32),
                 ("max_span", c_i32), ("query_level", c_i32), ("dims", c_i32 * 3),
                 ("hash_bits", c_i32), ("channels", c_i32), ("cutoff_sigma", c_f32), ("brute_force", c_i32),
-                ("coop_cells", c_i32), ("max_gaussians", c_i64), ("max_queries", c_i64), ("max_pairs", c_i64)]
+                ("coop_cells", c_i32), ("field_storage", c_i32), ("max_gaussians", c_i64), ("max_queries", c_i64), ("max_pairs", c_i64)]
 
 
 class gpf_index_stats_t(ctypes.Structure):
@@ -78,6 +83,7 @@ SIGNATURES = {
     "gpf_count_pairs": (c_i32, [c_vp, ctypes.POINTER(gpf_field), ctypes.POINTER(gpf_queries),
                                 c_vp, c_vp]),
     "gpf_launch_count": (ctypes.c_uint64, []),
+    "gpf_field_quantize": (c_i32, [ctypes.POINTER(gpf_field), ctypes.POINTER(gpf_field), c_vp]),
     "gpf_index_set_timing_events": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "gpf_radiance_bwd": (c_i32, [c_vp, ctypes.POINTER(gpf_field), ctypes.POINTER(gpf_queries),
                                  ctypes.POINTER(gpf_query_params), c_vp, c_vp, c_vp,

@@ -54,13 +54,17 @@ def _need(t: torch.Tensor, name: str, rows: int, count: int, dtype=torch.float32
 
 @dataclasses.dataclass
 class Field:
-    """N Gaussians as float32 CUDA tensors: mean [3,N], quat [4,N] (w,x,y,z),
-    logscale [3,N], spectrum [C,N]."""
+    """N Gaussians as CUDA tensors [rows, N]: mean [3,N], quat [4,N] (w,x,y,z),
+    logscale [3,N], spectrum [C,N]. float32 (GPF_F32 storage), or bfloat16
+    with `anchor` float32 [ceil(N/16), 4] (GPF_BF16 storage: means and
+    log-scales as offsets from each group's anchor; GPF_BF16_MEAN32: the
+    same with float32 means; see include/gpf.h)."""
 
     mean: torch.Tensor
     quat: torch.Tensor
     logscale: torch.Tensor
     spectrum: torch.Tensor
+    anchor: Optional[torch.Tensor] = None
 
     @property
     def n(self) -> int:
@@ -70,14 +74,24 @@ class Field:
     def channels(self) -> int:
         return int(self.spectrum.shape[0])
 
+    @property
+    def storage(self) -> int:
+        if self.quat.dtype != torch.bfloat16:
+            return _abi.GPF_F32
+        return _abi.GPF_BF16 if self.mean.dtype == torch.bfloat16 else _abi.GPF_BF16_MEAN32
+
     def c_struct(self) -> _abi.gpf_field:
         n, c = self.n, self.channels
-        _need(self.mean, "mean", 3, n)
-        _need(self.quat, "quat", 4, n)
-        _need(self.logscale, "logscale", 3, n)
-        _need(self.spectrum, "spectrum", c, n)
-        return _abi.gpf_field(n, c, 0, _ptr(self.mean), _ptr(self.quat), _ptr(self.logscale),
-                              _ptr(self.spectrum))
+        st = self.storage
+        dt = torch.float32 if st == _abi.GPF_F32 else torch.bfloat16
+        _need(self.mean, "mean", 3, n, torch.bfloat16 if st == _abi.GPF_BF16 else torch.float32)
+        _need(self.quat, "quat", 4, n, dt)
+        _need(self.logscale, "logscale", 3, n, dt)
+        _need(self.spectrum, "spectrum", c, n, dt)
+        if st != _abi.GPF_F32 and n > 0:
+            _need(self.anchor, "anchor", (n + _abi.GPF_BF16_GROUP - 1) // _abi.GPF_BF16_GROUP, 4)
+        return _abi.gpf_field(n, c, self.storage, _ptr(self.mean), _ptr(self.quat),
+                              _ptr(self.logscale), _ptr(self.spectrum), _ptr(self.anchor))
 
     def tensors(self):
         return [self.mean, self.quat, self.logscale, self.spectrum]
@@ -90,6 +104,38 @@ class Field:
     def from_numpy(f, device="cuda") -> "Field":
         return Field(*(torch.as_tensor(a, dtype=torch.float32, device=device).contiguous()
                        for a in (f.mean, f.quat, f.logscale, f.spectrum)))
+
+    @staticmethod
+    def empty_bf16(n: int, channels: int, device="cuda", mean32: bool = False) -> "Field":
+        """Uninitialised GPF_BF16 (or GPF_BF16_MEAN32) arrays for n Gaussians."""
+        g = (n + _abi.GPF_BF16_GROUP - 1) // _abi.GPF_BF16_GROUP
+        e = lambda r, dt=torch.bfloat16: torch.empty((r, n), dtype=dt, device=device)  # noqa
+        return Field(e(3, torch.float32 if mean32 else torch.bfloat16), e(4), e(3), e(channels),
+                     torch.empty((g, 4), dtype=torch.float32, device=device))
+
+    def quantize_into(self, dst: "Field", stream=None) -> "Field":
+        """gpf_field_quantize: write the GPF_BF16 form of this float32 field into dst."""
+        fs, ds = self.c_struct(), dst.c_struct()
+        check(load().gpf_field_quantize(ctypes.byref(fs), ctypes.byref(ds), _stream(stream)),
+              "gpf_field_quantize")
+        return dst
+
+    def quantized(self, mean32: bool = False, stream=None) -> "Field":
+        """A new GPF_BF16 (mean32: GPF_BF16_MEAN32) field holding this float32
+        field's quantised form."""
+        return self.quantize_into(
+            Field.empty_bf16(self.n, self.channels, self.mean.device, mean32), stream)
+
+    def decoded(self) -> "Field":
+        """float32 values of a GPF_BF16 field (host-side set-up and checks
+        only; the library decodes on the GPU inside gpf_build_index)."""
+        if self.storage == _abi.GPF_F32:
+            return self
+        grp = torch.arange(self.n, device=self.mean.device) // _abi.GPF_BF16_GROUP
+        a = self.anchor[grp].T                         # [4, N]
+        mean = self.mean if self.storage == _abi.GPF_BF16_MEAN32 else a[:3] + self.mean.float()
+        return Field(mean.contiguous(), self.quat.float(),
+                     (a[3:4] + self.logscale.float()).contiguous(), self.spectrum.float())
 
 
 @dataclasses.dataclass
@@ -146,6 +192,7 @@ class GridConfig:
     max_pairs: int = 0
     brute_force: bool = False
     coop_cells: int = 0        # forward tile shape (0 = library default, 4)
+    field_storage: int = 0     # GPF_F32 or GPF_BF16 fields
 
     def c_struct(self) -> _abi.gpf_grid_config:
         return _abi.gpf_grid_config((ctypes.c_float * 3)(*self.origin), float(self.cell_size),
@@ -153,7 +200,8 @@ class GridConfig:
                                     (ctypes.c_int32 * 3)(*[int(d) for d in self.dims]),
                                     int(self.hash_bits), int(self.channels),
                                     float(self.cutoff_sigma), 1 if self.brute_force else 0,
-                                    int(self.coop_cells), int(self.max_gaussians),
+                                    int(self.coop_cells), int(self.field_storage),
+                                    int(self.max_gaussians),
                                     int(self.max_queries),
                                     int(self.max_pairs))
 
@@ -294,9 +342,10 @@ def gpf_radiance_bwd(index: Index, field: Field, queries: Queries, grad_out: tor
     logscale and spectrum."""
     m, c = queries.m, field.channels
     _need(grad_out, "grad_out", c, m)
-    if grads is None:
-        grads = Field.zeros_like(field) if accumulate else Field(
-            *(torch.empty_like(t) for t in field.tensors()))
+    if grads is None:       # float32 gradients for either storage
+        mk = torch.zeros if accumulate else torch.empty
+        grads = Field(*(mk(tuple(t.shape), dtype=torch.float32, device=t.device)
+                        for t in field.tensors()))
     for name, g, t in zip(("grad_mean", "grad_quat", "grad_logscale", "grad_spectrum"),
                           grads.tensors(), field.tensors()):
         _need(g, name, t.shape[0], t.shape[1])

@@ -37,10 +37,23 @@ gpf_status cuda_fail(cudaError_t e, const char* where) {
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-#define GPF_CHECK_PTR(p, what)                                                              \
+#define GPF_CHECK_PTR_AL(p, al, what)                                                       \
   do {                                                                                      \
     if ((p) == nullptr) return fail(GPF_ERR_INVALID_ARG, "%s is NULL", what);               \
-    if (!aligned((p), 4)) return fail(GPF_ERR_INVALID_ARG, "%s is not 4-byte aligned", what); \
+    if (!aligned((p), (al)))                                                                \
+      return fail(GPF_ERR_INVALID_ARG, "%s is not %d-byte aligned", what, (int)(al));       \
+  } while (0)
+#define GPF_CHECK_PTR(p, what) GPF_CHECK_PTR_AL(p, 4, what)
+
+// The four arrays (and the anchors) of a field in its storage.
+#define GPF_CHECK_FIELD_ARRAYS(f, name)                                                    \
+  do {                                                                                      \
+    const int al_ = (f)->storage == GPF_F32 ? 4 : 2;                                        \
+    GPF_CHECK_PTR_AL((f)->mean, (f)->storage == GPF_BF16 ? 2 : 4, name ".mean");            \
+    GPF_CHECK_PTR_AL((f)->quat, al_, name ".quat");                                         \
+    GPF_CHECK_PTR_AL((f)->logscale, al_, name ".logscale");                                 \
+    GPF_CHECK_PTR_AL((f)->spectrum, al_, name ".spectrum");                                 \
+    if ((f)->storage != GPF_F32) GPF_CHECK_PTR_AL((f)->anchor, 16, name ".anchor");         \
   } while (0)
 
 }  // namespace
@@ -97,6 +110,7 @@ size_t layout(const gpf_index* ix, char* base, IndexBuffers* b) {
   }
   t.occ = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * ((nb + 31) / 32)));
   t.brange = reinterpret_cast<uint2*>(take(sizeof(uint2) * nb));
+  t.dec = d.bf16 ? reinterpret_cast<float*>(take(sizeof(float) * (10 + d.channels) * N)) : nullptr;
   t.scan_ws = take(scan_workspace_bytes(std::max<int64_t>(std::max<int64_t>(N, 1), ncp)));
   t.qsort_ws = take(radix_sort_workspace_bytes(M > 0 ? M : 1));
   t.gsort_ws = take(radix_sort_workspace_bytes(P > 0 ? P : 1));
@@ -118,13 +132,12 @@ gpf_status check_field(const gpf_index* ix, const gpf_field* f) {
   if (f->channels != ix->dims.channels)
     return fail(GPF_ERR_INVALID_ARG, "field.channels = %d but the index holds %d channels",
                 f->channels, ix->dims.channels);
-  if (f->reserved != 0) return fail(GPF_ERR_INVALID_ARG, "field.reserved must be 0");
-  if (f->n > 0) {
-    GPF_CHECK_PTR(f->mean, "field.mean");
-    GPF_CHECK_PTR(f->quat, "field.quat");
-    GPF_CHECK_PTR(f->logscale, "field.logscale");
-    GPF_CHECK_PTR(f->spectrum, "field.spectrum");
-  }
+  if (f->storage != GPF_F32 && f->storage != GPF_BF16 && f->storage != GPF_BF16_MEAN32)
+    return fail(GPF_ERR_INVALID_ARG, "field.storage = %d is not a storage form", f->storage);
+  if (f->storage != ix->dims.storage)
+    return fail(GPF_ERR_INVALID_ARG, "field.storage = %d but the index was created for %d",
+                f->storage, ix->dims.storage);
+  if (f->n > 0) GPF_CHECK_FIELD_ARRAYS(f, "field");
   return GPF_OK;
 }
 
@@ -234,6 +247,10 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
     return fail(GPF_ERR_INVALID_ARG, "cutoff_sigma must be > 0 (or +INF)");
   if (cfg->brute_force != 0 && cfg->brute_force != 1)
     return fail(GPF_ERR_INVALID_ARG, "brute_force must be 0 or 1");
+  if (cfg->field_storage != GPF_F32 && cfg->field_storage != GPF_BF16 &&
+      cfg->field_storage != GPF_BF16_MEAN32)
+    return fail(GPF_ERR_INVALID_ARG, "field_storage = %d is not a storage form",
+                cfg->field_storage);
   if (cfg->coop_cells < 0 || cfg->coop_cells > GPF_MAX_COOP_CELLS)
     return fail(GPF_ERR_INVALID_ARG, "coop_cells = %d outside 0..%d", cfg->coop_cells,
                 GPF_MAX_COOP_CELLS);
@@ -291,6 +308,8 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
   d.channels = cfg->channels;
   d.cutoff = cfg->cutoff_sigma;
   d.brute = isinf(cfg->cutoff_sigma) || cfg->brute_force == 1;
+  d.storage = cfg->field_storage;
+  d.bf16 = cfg->field_storage != GPF_F32;
   d.n_max = cfg->max_gaussians;
   d.m_max = cfg->max_queries;
   d.p_max = d.brute ? 0 : cfg->max_pairs;
@@ -421,7 +440,9 @@ gpf_status gpf_radiance_bwd(const gpf_index* index, const gpf_field* field,
       GPF_CHECK_PTR(z, "z");
     }
   }
-  cudaError_t e = launch_backward(index->dims, index->buf, *field, *queries, *params, grad_out, out,
+  cudaError_t e = launch_backward(index->dims, index->buf,
+                                  float32_view(index->dims, index->buf, *field), *queries, *params,
+                                  grad_out, out,
                                   z, *grads, index->bwd_ev, reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "gpf_radiance_bwd");
   return GPF_OK;
@@ -484,6 +505,8 @@ gpf_status gpf_adam_step(const gpf_field* params, const gpf_field_grad* grads,
   if (!params || !grads || !m || !v || !hp)
     return fail(GPF_ERR_INVALID_ARG, "a pointer argument is NULL");
   if (params->n < 0) return fail(GPF_ERR_INVALID_ARG, "params.n < 0");
+  if (params->storage != GPF_F32)
+    return fail(GPF_ERR_INVALID_ARG, "Adam updates a GPF_F32 (master) field");
   if (params->channels < 1 || params->channels > GPF_MAX_CHANNELS)
     return fail(GPF_ERR_INVALID_ARG, "params.channels outside 1..%d", GPF_MAX_CHANNELS);
   if (hp->step_counter) {
@@ -513,6 +536,24 @@ gpf_status gpf_adam_step(const gpf_field* params, const gpf_field_grad* grads,
   }
   cudaError_t e = launch_adam(*params, *grads, *m, *v, *hp, reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "gpf_adam_step");
+  return GPF_OK;
+}
+
+gpf_status gpf_field_quantize(const gpf_field* src, const gpf_field* dst, gpf_stream stream) {
+  if (!src || !dst) return fail(GPF_ERR_INVALID_ARG, "src or dst is NULL");
+  if (src->storage != GPF_F32) return fail(GPF_ERR_INVALID_ARG, "src must be GPF_F32");
+  if (dst->storage != GPF_BF16 && dst->storage != GPF_BF16_MEAN32)
+    return fail(GPF_ERR_INVALID_ARG, "dst must be GPF_BF16 or GPF_BF16_MEAN32");
+  if (src->n < 0 || src->n != dst->n || src->channels != dst->channels)
+    return fail(GPF_ERR_INVALID_ARG, "src and dst differ in n or channels");
+  if (src->channels < 1 || src->channels > GPF_MAX_CHANNELS)
+    return fail(GPF_ERR_INVALID_ARG, "channels outside 1..%d", GPF_MAX_CHANNELS);
+  if (src->n > 0) {
+    GPF_CHECK_FIELD_ARRAYS(src, "src");
+    GPF_CHECK_FIELD_ARRAYS(dst, "dst");
+  }
+  const cudaError_t e = launch_quantize(*src, *dst, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "gpf_field_quantize");
   return GPF_OK;
 }
 

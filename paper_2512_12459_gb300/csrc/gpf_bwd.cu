@@ -530,8 +530,8 @@ cudaError_t launch_backward(const IndexDims& d, const IndexBuffers& b, const gpf
   a.box = b.box;
   a.order = b.oval[b.osorted];
   a.n = n;
-  a.quat = f.quat;
-  a.logscale = f.logscale;
+  a.quat = static_cast<const float*>(f.quat);
+  a.logscale = static_cast<const float*>(f.logscale);
   a.mode = p.mode;
   const bool psi = isfinite(p.r_max);
   a.r = psi ? p.r_max : 0.0f;

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "../../include/gpf.h"
 
@@ -41,6 +42,25 @@ static_assert(sizeof(DeviceHeader) == 256, "header is one 256-byte block");
 //           kLevelBits mantissa bits (rec_radius_with_level, rec_level)
 //   [4..12] M = S^-1 R^T, row-major: M[j][k] = R[k][j] / s_j
 //   [13..]  Phi[0..C-1], then zero padding to a multiple of 4 floats
+// bfloat16 as the upper 16 bits of a float32: exact widening, and rounding
+// to nearest with ties to even (the carry of the low half into the upper
+// half, plus the upper half's last bit for ties); finite values.
+__host__ __device__ __forceinline__ float bf16_to_f32(uint16_t h) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float((uint32_t)h << 16);
+#else
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+#endif
+}
+__device__ __forceinline__ uint16_t f32_to_bf16(float x) {
+  uint32_t u = __float_as_uint(x);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
 constexpr int kLevelBits = 4;  // levels < 2^kLevelBits = kMaxLevels
 constexpr uint32_t kLevelMask = (1u << kLevelBits) - 1u;
 static_assert(kMaxLevels <= (1 << kLevelBits), "a level must fit in kLevelBits");

@@ -35,6 +35,92 @@ __device__ __forceinline__ bool occupied(const uint32_t* occ, uint32_t b) {
   return (occ[b >> 5] >> (b & 31u)) & 1u;
 }
 
+// GPF_BF16 / GPF_BF16_MEAN32 field -> float32 [(10 + C), n] rows: mean, quat, logscale,
+// spectrum (the decoding stated at gpf_field).
+__global__ void decode_bf16_kernel(gpf_field f, float* __restrict__ dec) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = f.n;
+  if (g >= n) return;
+  const float* anc = f.anchor + 4 * (g / GPF_BF16_GROUP);
+  const uint16_t* quat = static_cast<const uint16_t*>(f.quat);
+  const uint16_t* lsc = static_cast<const uint16_t*>(f.logscale);
+  const uint16_t* spec = static_cast<const uint16_t*>(f.spectrum);
+  const float4 a = *reinterpret_cast<const float4*>(anc);
+  if (f.storage == GPF_BF16) {
+    const uint16_t* mean = static_cast<const uint16_t*>(f.mean);
+    dec[g] = __fadd_rn(a.x, bf16_to_f32(mean[g]));
+    dec[n + g] = __fadd_rn(a.y, bf16_to_f32(mean[n + g]));
+    dec[2 * n + g] = __fadd_rn(a.z, bf16_to_f32(mean[2 * n + g]));
+  } else {
+    const float* mean = static_cast<const float*>(f.mean);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dec[k * n + g] = mean[k * n + g];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) dec[(3 + k) * n + g] = bf16_to_f32(quat[k * n + g]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dec[(7 + k) * n + g] = __fadd_rn(a.w, bf16_to_f32(lsc[k * n + g]));
+  for (int c = 0; c < f.channels; ++c) dec[(10 + c) * n + g] = bf16_to_f32(spec[c * n + g]);
+}
+
+// gpf_field_quantize: one half-warp per group of 16 Gaussians, one lane per
+// Gaussian; min / max over the group by xor shuffles within the half-warp.
+__global__ void quantize_bf16_kernel(gpf_field src, gpf_field dst) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = src.n;
+  const bool live = g < n;
+  const float* mean = static_cast<const float*>(src.mean);
+  const float* quat = static_cast<const float*>(src.quat);
+  const float* lsc = static_cast<const float*>(src.logscale);
+  const float* spec = static_cast<const float*>(src.spectrum);
+  float mu[3], l[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    mu[k] = live ? mean[k * n + g] : 0.0f;
+    l[k] = live ? lsc[k * n + g] : 0.0f;
+  }
+  float lo[4], hi[4];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) lo[k] = hi[k] = mu[k];
+  lo[3] = fminf(l[0], fminf(l[1], l[2]));
+  hi[3] = fmaxf(l[0], fmaxf(l[1], l[2]));
+  if (!live) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { lo[k] = INFINITY; hi[k] = -INFINITY; }
+  }
+#pragma unroll
+  for (int o = GPF_BF16_GROUP / 2; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(kFullMask, lo[k], o, GPF_BF16_GROUP));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(kFullMask, hi[k], o, GPF_BF16_GROUP));
+    }
+  }
+  float ref[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) ref[k] = __fmul_rn(__fadd_rn(lo[k], hi[k]), 0.5f);
+  if (!live) return;
+  if (g % GPF_BF16_GROUP == 0)
+    *reinterpret_cast<float4*>(const_cast<float*>(dst.anchor) + 4 * (g / GPF_BF16_GROUP)) =
+        make_float4(ref[0], ref[1], ref[2], ref[3]);
+  const bool mean32 = dst.storage == GPF_BF16_MEAN32;
+  uint16_t* dquat = static_cast<uint16_t*>(const_cast<void*>(dst.quat));
+  uint16_t* dlsc = static_cast<uint16_t*>(const_cast<void*>(dst.logscale));
+  uint16_t* dspec = static_cast<uint16_t*>(const_cast<void*>(dst.spectrum));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (mean32)
+      static_cast<float*>(const_cast<void*>(dst.mean))[k * n + g] = mu[k];
+    else
+      static_cast<uint16_t*>(const_cast<void*>(dst.mean))[k * n + g] =
+          f32_to_bf16(__fsub_rn(mu[k], ref[k]));
+    dlsc[k * n + g] = f32_to_bf16(__fsub_rn(l[k], ref[3]));
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) dquat[k * n + g] = f32_to_bf16(quat[k * n + g]);
+  for (int c = 0; c < src.channels; ++c) dspec[c * n + g] = f32_to_bf16(spec[c * n + g]);
+}
+
 // Per Gaussian: record, level box, the number of cells of that box holding a
 // hit point (its list entries) and its key in the backward's order.
 __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brute,
@@ -48,8 +134,11 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
   uint32_t level_bit = 0;
   bool live = false, small = false;
   if (g < n) {
-    const float mu[3] = {f.mean[g], f.mean[n + g], f.mean[2 * n + g]};
-    const Frame fr = gaussian_frame(f.quat, f.logscale, n, g);
+    const float* mean = static_cast<const float*>(f.mean);
+    const float* spec = static_cast<const float*>(f.spectrum);
+    const float mu[3] = {mean[g], mean[n + g], mean[2 * n + g]};
+    const Frame fr = gaussian_frame(static_cast<const float*>(f.quat),
+                                    static_cast<const float*>(f.logscale), n, g);
     float* r = rec + g * rs;
     const float smax = fmaxf(fr.s[0], fmaxf(fr.s[1], fr.s[2]));
     r[0] = mu[0]; r[1] = mu[1]; r[2] = mu[2];
@@ -61,7 +150,7 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
 #pragma unroll
       for (int k = 0; k < 3; ++k) r[4 + 3 * j + k] = fr.R[k][j] * inv;
     }
-    for (int c = 0; c < f.channels; ++c) r[13 + c] = f.spectrum[(int64_t)c * n + g];
+    for (int c = 0; c < f.channels; ++c) r[13 + c] = spec[(int64_t)c * n + g];
     for (int c = 13 + f.channels; c < rs; ++c) r[c] = 0.0f;
     // the order the backward walks Gaussians in: class (0 = bounds within
     // 2 x 2 x 2 query-level cells, 1 = larger, 2 = no hit point in reach),
@@ -202,11 +291,31 @@ inline unsigned blocks_for(int64_t n, int t = kThreads) {
 
 }  // namespace
 
-cudaError_t launch_build(const IndexDims& d, const IndexBuffers& b, const gpf_field& f,
+gpf_field float32_view(const IndexDims& d, const IndexBuffers& b, const gpf_field& f) {
+  if (f.storage == GPF_F32) return f;
+  // rows of the field's own length n, packed at the start of the buffer
+  const int64_t n = f.n;
+  gpf_field v = f;
+  v.storage = GPF_F32;
+  v.mean = b.dec;
+  v.quat = b.dec + 3 * n;
+  v.logscale = b.dec + 7 * n;
+  v.spectrum = b.dec + 10 * n;
+  v.anchor = nullptr;
+  return v;
+}
+
+cudaError_t launch_build(const IndexDims& d, const IndexBuffers& b, const gpf_field& f_in,
                          const gpf_queries& q, cudaStream_t stream) {
   const Grid& grid = d.grid;
   cudaError_t e = cudaMemsetAsync(b.header, 0, sizeof(DeviceHeader), stream);
   if (e != cudaSuccess) return e;
+  // 0. 16-bit storage: decode every parameter to float32 once
+  if (f_in.storage != GPF_F32 && f_in.n > 0) {
+    decode_bf16_kernel<<<blocks_for(f_in.n), kThreads, 0, stream>>>(f_in, b.dec);
+    note_launches(1);
+  }
+  const gpf_field f = float32_view(d, b, f_in);
   if (!d.brute) {
     e = cudaMemsetAsync(b.occ, 0, sizeof(uint32_t) * ((grid.n_buckets + 31) / 32), stream);
     if (e != cudaSuccess) return e;
@@ -257,6 +366,14 @@ cudaError_t launch_build(const IndexDims& d, const IndexBuffers& b, const gpf_fi
         b.gkey[b.gsorted], &b.header->n_pairs, d.p_max, b.brange);
     note_launches(1);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quantize(const gpf_field& src, const gpf_field& dst, cudaStream_t stream) {
+  if (src.n == 0) return cudaSuccess;
+  // whole groups per block: kThreads is a multiple of GPF_BF16_GROUP
+  quantize_bf16_kernel<<<blocks_for(src.n), kThreads, 0, stream>>>(src, dst);
+  note_launches(1);
   return cudaGetLastError();
 }
 

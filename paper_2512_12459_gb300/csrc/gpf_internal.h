@@ -53,6 +53,8 @@ struct IndexBuffers {
   uint32_t* gkey[2];    // [P_max] (bucket, Gaussian) entries, sort ping-pong
   uint32_t* gval[2];
   uint2* brange;        // [n_buckets] [start, end) of every bucket's list
+  float* dec;           // GPF_BF16 fields: decoded float32 [(10 + C), n] (rows
+                        // mean 3, quat 4, logscale 3, spectrum C; N_max room)
   void* scan_ws;
   void* qsort_ws;
   void* gsort_ws;
@@ -65,11 +67,19 @@ struct IndexDims {
   int channels;
   float cutoff;         // k (may be +INF)
   bool brute;           // no cell lists: every Gaussian against every hit point
+  int storage;          // storage form of the fields (gpf_field.storage)
+  bool bf16;            // a 16-bit form (decoded at build)
   int64_t n_max, m_max, p_max;
 };
 
+// GPF_BF16 fields are decoded into b.dec first and the build reads that.
 cudaError_t launch_build(const IndexDims& dims, const IndexBuffers& b, const gpf_field& f,
                          const gpf_queries& q, cudaStream_t stream);
+// The float32 field the pair loops read: f itself, or the decoded arrays of
+// the last build when f is in GPF_BF16 storage.
+gpf_field float32_view(const IndexDims& dims, const IndexBuffers& b, const gpf_field& f);
+// gpf_field_quantize (gpf_index.cu).
+cudaError_t launch_quantize(const gpf_field& src, const gpf_field& dst, cudaStream_t stream);
 
 // ---- pair loops (gpf_fwd.cu, gpf_bwd.cu)
 // Events recorded around a pair-loop kernel (either may be null).

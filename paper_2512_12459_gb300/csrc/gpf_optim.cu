@@ -179,8 +179,10 @@ cudaError_t launch_adam(const gpf_field& params, const gpf_field_grad& g, const 
   const int64_t n = params.n;
   if (n == 0) return cudaSuccess;
   AdamArgs a;
-  float* P[4] = {const_cast<float*>(params.mean), const_cast<float*>(params.quat),
-                 const_cast<float*>(params.logscale), const_cast<float*>(params.spectrum)};
+  float* P[4] = {static_cast<float*>(const_cast<void*>(params.mean)),
+                 static_cast<float*>(const_cast<void*>(params.quat)),
+                 static_cast<float*>(const_cast<void*>(params.logscale)),
+                 static_cast<float*>(const_cast<void*>(params.spectrum))};
   const float* G[4] = {g.mean, g.quat, g.logscale, g.spectrum};
   float* Mm[4] = {m.mean, m.quat, m.logscale, m.spectrum};
   float* Vv[4] = {v.mean, v.quat, v.logscale, v.spectrum};

@@ -99,11 +99,13 @@ def make_index(field: Field, queries: Queries, cutoff_sigma: float = 3.0,
     capacity comes from a trial build (gpf_index_stats) times `headroom`
     (room for the pairs to grow while the parameters are optimised)."""
     if grid is None:
-        grid = plan_grid(field, queries, cutoff_sigma, max_span, query_cell, hash_bits, bounds,
-                         brute_force=brute_force)
+        # plan on the float32 values (a GPF_BF16 field is decoded for this)
+        grid = plan_grid(field.decoded(), queries, cutoff_sigma, max_span, query_cell, hash_bits,
+                         bounds, brute_force=brute_force)
         grid.coop_cells = coop_cells
     else:
         grid = dataclasses.replace(grid)     # capacities below are this index's own
+    grid.field_storage = field.storage
     grid.max_gaussians = max_gaussians if max_gaussians is not None else max(field.n, 1)
     grid.max_queries = max_queries if max_queries is not None else max(queries.m, 1)
     brute = brute_force or math.isinf(cutoff_sigma)

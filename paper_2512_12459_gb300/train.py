@@ -24,21 +24,27 @@ class TrainStep:
     """build index -> radiance forward -> MSE gradient -> radiance backward
     -> Adam, over preallocated buffers.
 
-    field    parameters (updated in place by every step)
+    field    float32 parameters (updated in place by every step)
     queries  the batch of hit points (all views concatenated)
     target   [C, M] radiance to fit
-    index    an Index with capacity for field and queries (setup_index)
+    index    an Index with capacity for the field and queries (setup_index),
+             created for the storage the step reads (see `store`)
+    store    None: the pair loops read `field` itself. A GPF_BF16 Field
+             (Field.quantized()): the pair loops read this 16-bit copy, the
+             gradients (with respect to its decoded values) update the
+             float32 master `field`, which is then re-quantised into it.
     """
 
     def __init__(self, field: Field, queries: Queries, target: torch.Tensor, index: Index,
                  mode: int = GPF_SUM, r_max: float = PAPER_R, eps: float = PAPER_EPS,
-                 lr=PAPER_LR, grad_hook=None):
+                 lr=PAPER_LR, grad_hook=None, store: Optional[Field] = None):
         self.field, self.queries, self.target, self.index = field, queries, target, index
+        self.store = store
         self.mode, self.r_max, self.eps, self.lr = mode, r_max, eps, lr
         c, m = field.channels, queries.m
         dev = field.mean.device
         self.state = AdamState.zeros_like(field, device_counter=True)
-        self.grads = Field.zeros_like(field)
+        self.grads = Field.zeros_like(field)            # float32, like the master
         self.out = torch.empty((c, m), dtype=torch.float32, device=dev)
         self.z = torch.empty((m,), dtype=torch.float32, device=dev)
         self.gout = torch.empty((c, m), dtype=torch.float32, device=dev)
@@ -48,7 +54,8 @@ class TrainStep:
 
     def run_eager(self) -> None:
         """One step, launched now on the current stream."""
-        f, q = self.field, self.queries
+        q = self.queries
+        f = self.store if self.store is not None else self.field
         self.index.build(f, q)
         api.gpf_radiance_fwd(self.index, f, q, self.mode, r_max=self.r_max, eps=self.eps,
                              out=self.out, z=self.z)
@@ -57,7 +64,9 @@ class TrainStep:
                              r_max=self.r_max, eps=self.eps, grads=self.grads)
         if self.grad_hook is not None:
             self.grad_hook(self.grads)
-        api.gpf_adam_step(f, self.grads, self.state, lr=self.lr)
+        api.gpf_adam_step(self.field, self.grads, self.state, lr=self.lr)
+        if self.store is not None:
+            self.field.quantize_into(self.store)
 
     def capture(self, warmup: int = 1) -> None:
         """Run `warmup` real steps on a side stream (first-use set-up outside

@@ -23,3 +23,4 @@ from .scenes import (  # noqa: F401
     knn_distance,
     random_quaternions,
 )
+from . import storage  # noqa: F401,E402

@@ -8,13 +8,17 @@ import numpy as np
 import oracle
 
 FWD_TOL = 1e-5      # relative radiance error (scale: rho * sum_i w_i |Phi_i|)
-# float32 evaluates w = exp(E) from an exponent E rounded to float32 (and from
-# a float32 distance, whose error the falloff amplifies), so w carries a
-# relative error of a few u |E|, u = 2^-24. At hit points where every weight
-# is tiny (largest E below about -33) that bound exceeds FWD_TOL; there the
-# tolerance is EXP_COND * u * |E_max|.
+# float32 evaluates w = exp(E), E = -Q/2 - 3 t^2, so w carries the absolute
+# error of E as a relative error. The Mahalanobis part contributes a few
+# u |Q/2| (u = 2^-24). The falloff part depends on the float32 distance d
+# (relative error <= 2u after the sum of squares and the square root), with
+# t = (d - r)/r: |d(3 t^2)| = 6 t (d/r) 2u = 12 u t (t + 1), which is at most
+# 8 u * 3 t^2 for t >= 1 (and below 24 u, under FWD_TOL, for t < 1). So the
+# error of E is at most 8 u |E|, and where the largest E at a hit point is
+# far below zero that exceeds FWD_TOL: the tolerance there is
+# EXP_COND * u * |E_max|.
 U32 = 2.0 ** -24
-EXP_COND = 5.0
+EXP_COND = 8.0
 GRAD_TOL = 1e-4     # normwise relative error per gradient tensor
 DENOM_FLOOR = 1e-20
 
