@@ -335,6 +335,90 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_bf16(args):
+    """16-bit parameter storage: 4M Gaussians with an 8-bin spectrum in
+    Morton order, 16 views of 1920x1080; the captured training step with
+    float32 parameters, with GPF_BF16_MEAN32 and with GPF_BF16 storage (the
+    16-bit forms update a float32 master and re-quantise it), and the
+    relative difference of each 16-bit form's radiance from the float32
+    form's on 4,096 random valid pixels (GPU outputs only)."""
+    import torch
+    import synth
+    from synth import storage
+    import paper_2512_12459_gb300 as gpf
+    from paper_2512_12459_gb300.setup_index import make_index
+    from paper_2512_12459_gb300.train import TrainStep
+
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    pos, flux = synth.caustic_photons(args.bf16_photons, seed=0, channels=8)
+    fnp = synth.field_from_photons(pos, flux, seed=0)
+    fnp = storage.permuted(fnp, storage.morton_order(fnp))
+    tgt_np = synth.perturbed_copy(fnp, seed=1)
+    qnp = synth.orbit_views(args.bf16_views, 1920, 1080)
+    gen_s = time.time() - t0
+    queries = gpf.Queries.from_numpy(qnp)
+    n_active = int(qnp.valid.sum())
+    tf = gpf.Field.from_numpy(tgt_np)
+    tidx = make_index(tf, queries, query_cell=CELL)
+    tidx.build(tf, queries)
+    target, _ = gpf.gpf_radiance_fwd(tidx, tf, queries, gpf.GPF_SUM, r_max=R_MAX)
+    target = target.clone()
+    del tidx, tf
+    torch.cuda.empty_cache()
+
+    rng = np.random.default_rng(7)
+    sel = torch.as_tensor(rng.choice(np.flatnonzero(qnp.valid.astype(bool)), 4096, replace=False),
+                          device="cuda")
+    results, first = {}, {}
+    for name in ("f32", "bf16_mean32", "bf16"):
+        master = gpf.Field.from_numpy(fnp)
+        store = None if name == "f32" else master.quantized(mean32=(name == "bf16_mean32"))
+        read = master if store is None else store
+        idx = make_index(read, queries, query_cell=CELL, max_span=3, coop_cells=8, headroom=1.25)
+        idx.build(read, queries)
+        o, _ = gpf.gpf_radiance_fwd(idx, read, queries, gpf.GPF_SUM, r_max=R_MAX)
+        first[name] = o[:, sel].double().cpu().numpy()
+        del o
+        step = TrainStep(master, queries, target, idx, r_max=R_MAX, lr=LR, store=store)
+        step.capture(warmup=args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        pbytes = sum(t.numel() * t.element_size() for t in read.tensors())
+        if store is not None:
+            pbytes += store.anchor.numel() * 4
+        results[name] = {"ms_per_step": ms, "queries_per_s": n_active / (ms / 1e3),
+                         "param_bytes": pbytes}
+        del step, idx, master, store, read
+        torch.cuda.empty_cache()
+    ref = first["f32"]
+    for name in ("bf16_mean32", "bf16"):
+        rel = np.abs(first[name] - ref) / np.maximum(np.abs(ref), 1e-30)
+        pp = rel.max(axis=0)
+        results[name]["rel_diff_vs_f32"] = {"median": float(np.median(pp)),
+                                            "p99": float(np.percentile(pp, 99)),
+                                            "max": float(pp.max())}
+    line = {
+        "metric": METRIC, "value": results["bf16_mean32"]["queries_per_s"], "unit": "queries/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": results["bf16_mean32"]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 storage, f32 compute",
+        "data": "synthetic",
+        "config": {"workload": f"{fnp.n:,} Gaussians (8-bin spectrum, Morton order), "
+                               f"{args.bf16_views} views of 1920x1080, CUDA graph",
+                   "hit_points": int(qnp.m), "active_hit_points": n_active,
+                   "l2": "inputs larger than L2"},
+        "forms": results, "setup_s": {"generate": round(gen_s, 1)},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global N_PHOTONS, VIEW, WORKLOAD
     ap = argparse.ArgumentParser()
@@ -348,11 +432,13 @@ def main():
     ap.add_argument("--photons", type=int, default=N_PHOTONS,
                     help="Gaussians (smaller cases are for profiling only)")
     ap.add_argument("--view", type=int, default=VIEW, help="view side in pixels")
-    ap.add_argument("--workload", default="single", choices=["single", "batched"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "bf16"],
                     help="single: the 1M-Gaussian 1024x1024 step (default line); batched: "
                          "64 uneven views over 2M Gaussians, graph replay vs per-view launches")
     ap.add_argument("--batched-views", type=int, default=64)
     ap.add_argument("--batched-photons", type=int, default=2_000_000)
+    ap.add_argument("--bf16-photons", type=int, default=4_000_000)
+    ap.add_argument("--bf16-views", type=int, default=16)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if (args.photons, args.view) != (N_PHOTONS, VIEW):
@@ -368,6 +454,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "bf16":
+        run_bf16(args)
         return
 
     import torch
