@@ -419,6 +419,61 @@ def run_bf16(args):
     print(json.dumps(line), flush=True)
 
 
+def run_kde(args):
+    """The per-view photon density estimate (GPF_DISK_KDE) on the bench
+    scene: the same 1M photons gathered within r = 0.02 at the 1024x1024
+    view's hit points; index build + gather per step, L2 flushed between
+    steps."""
+    import torch
+    import synth
+    import paper_2512_12459_gb300 as gpf
+    from paper_2512_12459_gb300.setup_index import make_index
+
+    torch.cuda.set_device(0)
+    pos, flux = synth.caustic_photons(N_PHOTONS, seed=0)
+    qnp = synth.pinhole_hitpoints(EYE0, LOOK_AT, VIEW, VIEW)
+    n_active = int(qnp.valid.sum())
+    photons = gpf.photon_field(torch.as_tensor(pos.T.copy(), dtype=torch.float32, device="cuda"),
+                               torch.as_tensor(flux.T.copy(), dtype=torch.float32, device="cuda"),
+                               R_MAX)
+    queries = gpf.Queries.from_numpy(qnp)
+    idx = make_index(photons, queries, query_cell=CELL, max_span=3, coop_cells=8)
+    out = torch.empty((3, queries.m), device="cuda")
+    z = torch.empty((queries.m,), device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        idx.build(photons, queries)
+        gpf.gpf_radiance_fwd(idx, photons, queries, gpf.GPF_DISK_KDE, r_max=R_MAX, out=out, z=z)
+    torch.cuda.synchronize()
+    marks = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        idx.build(photons, queries)
+        ev[1].record()
+        gpf.gpf_radiance_fwd(idx, photons, queries, gpf.GPF_DISK_KDE, r_max=R_MAX, out=out, z=z)
+        ev[2].record()
+        marks.append(ev)
+    torch.cuda.synchronize()
+    build_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in marks]))
+    gather_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in marks]))
+    gathered = float(z.sum().item())
+    line = {
+        "metric": "hit-point photon density estimates/sec (disk kernel, build + gather)",
+        "value": n_active / ((build_ms + gather_ms) / 1e3), "unit": "queries/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": build_ms + gather_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{N_PHOTONS:,} caustic photons, {VIEW}x{VIEW} view, r={R_MAX}",
+                   "active_hit_points": n_active, "l2": "flushed between steps"},
+        "gather_queries_per_s": n_active / (gather_ms / 1e3),
+        "ms_breakdown": {"build": build_ms, "gather": gather_ms},
+        "photons_gathered": gathered, "photons_per_hit_point": gathered / max(n_active, 1),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global N_PHOTONS, VIEW, WORKLOAD
     ap = argparse.ArgumentParser()
@@ -432,7 +487,8 @@ def main():
     ap.add_argument("--photons", type=int, default=N_PHOTONS,
                     help="Gaussians (smaller cases are for profiling only)")
     ap.add_argument("--view", type=int, default=VIEW, help="view side in pixels")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "bf16"],
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "batched", "bf16", "kde"],
                     help="single: the 1M-Gaussian 1024x1024 step (default line); batched: "
                          "64 uneven views over 2M Gaussians, graph replay vs per-view launches")
     ap.add_argument("--batched-views", type=int, default=64)
@@ -457,6 +513,9 @@ def main():
         return
     if args.workload == "bf16":
         run_bf16(args)
+        return
+    if args.workload == "kde":
+        run_kde(args)
         return
 
     import torch

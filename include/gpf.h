@@ -24,6 +24,14 @@
  *   k is the truncation in standard deviations (3: the 3-sigma ellipsoid; an
  *   infinite k sums every Gaussian).
  *
+ *   GPF_DISK_KDE is the per-view photon density estimate the field replaces
+ *   (Sec. 3.2, Eq. kde; the gather of Algorithm S1), on the same index: the
+ *   field holds photons (mean = position, spectrum = flux) and
+ *     O = rho * (1 / (pi r^2)) * sum_{i : |x - mu_i| <= r} Phi_i * [n.w_o > 0]
+ *   with r = r_max. The index finds photon i through its k-sigma box, so
+ *   every photon must have k * max scale >= r (e.g. isotropic log-scale
+ *   log(r / k)); rotations do not matter.
+ *
  * Conventions for every call:
  *   - Arrays are float32 structure-of-arrays, row-major [rows, count], one row
  *     per component (mean [3,N] = all x, then all y, then all z).
@@ -64,7 +72,7 @@ typedef enum gpf_status {
   GPF_ERR_MISMATCH = 6            /* field/queries differ from those indexed   */
 } gpf_status;
 
-typedef enum gpf_mode { GPF_SUM = 0, GPF_NORMALIZED = 1 } gpf_mode;
+typedef enum gpf_mode { GPF_SUM = 0, GPF_NORMALIZED = 1, GPF_DISK_KDE = 2 } gpf_mode;
 
 /* Maximum number of spectral channels C. */
 #define GPF_MAX_CHANNELS 8
@@ -127,7 +135,8 @@ typedef struct gpf_queries {
 /* Query parameters. */
 typedef struct gpf_query_params {
   int32_t mode;          /* gpf_mode                                         */
-  float r_max;           /* falloff radius r (paper: 0.02); +INF disables psi */
+  float r_max;           /* falloff radius r (paper: 0.02); +INF disables psi;
+                            GPF_DISK_KDE: the gather radius (finite, > 0)    */
   float eps;             /* normalisation floor (paper: 1e-6)                */
   int32_t reserved;      /* must be 0                                        */
 } gpf_query_params;
@@ -283,7 +292,8 @@ gpf_status gpf_index_stats(const gpf_index *index, gpf_index_stats_t *stats,
  *   out     [C,M] float32 device, written for every hit point (0 where the
  *           point is invalid or n.w_o <= 0).
  *   z_out   [M] float32 device or NULL: Z = sum_i w_i for active points, 0
- *           elsewhere. Keep it for gpf_radiance_bwd in GPF_NORMALIZED mode.
+ *           elsewhere (GPF_DISK_KDE: the number of photons gathered). Keep it
+ *           for gpf_radiance_bwd in GPF_NORMALIZED mode.
  * Sums run in float32 in a fixed order: results are bitwise reproducible
  * for a given build.
  * The pair loop is a persistent kernel whose warps take tiles of hit points

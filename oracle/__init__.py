@@ -15,7 +15,9 @@ What it computes (paper arxiv 2512.12459):
   * the analytic gradient of that output with respect to every Gaussian
     parameter (Sec. 4.2, Differentiable Accumulation), by the chain rule;
   * the MSE loss of Sec. 4.3 and its gradient;
-  * the Adam update of Sec. A.2 (lr 5e-4).
+  * the Adam update of Sec. A.2 (lr 5e-4);
+  * the per-view photon density estimate the field replaces (Sec. 3.2,
+    Eq. kde; the gather of Algorithm S1), a disk kernel over photons.
 
 Everything is a brute-force sum over all Gaussians in float64; the inputs are
 the float32 values the GPU path receives, widened exactly.
@@ -31,6 +33,7 @@ from .gpf_oracle import (  # noqa: F401
     falloff_psi,
     radiance_fwd,
     radiance_bwd,
+    disk_kde,
     mse_loss,
     mse_loss_grad,
     adam_step,

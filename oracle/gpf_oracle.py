@@ -254,6 +254,45 @@ def radiance_bwd(mean, quat, logscale, spectrum, x, n, wo, grad_out, albedo=None
             "spectrum": g_phi.T.copy(), "fwd": fwd}
 
 
+def disk_kde(position, flux, x, n, wo, radius: float, albedo=None, valid=None,
+             band: float = 1e-5) -> Dict[str, np.ndarray]:
+    """The per-view photon density estimate that the field replaces (Sec. 3.2,
+    Eq. kde; the gather of Algorithm S1): at hit point x, the flux of every
+    photon p with |x - x_p| <= r, divided by the disk area pi r^2, modulated
+    like the field's query (albedo times the hemisphere gate):
+
+        O_c = rho_c (1 / (pi r^2)) sum_{p : |x - x_p| <= r} Phi_pc [n.w_o > 0]
+
+    position [3,P], flux [C,P]. Returns out [C,M], count [M] (photons
+    gathered), denom [C,M] (the same sum of |Phi|, the scale of the error),
+    near [M] (some photon lies within band r^2 of the disk's edge in squared
+    distance, where float32 and float64 may disagree)."""
+    pos = np.asarray(position, dtype=_F64).T
+    phi = np.asarray(flux, dtype=_F64).T
+    X = np.asarray(x, dtype=_F64).T
+    M, C = X.shape[0], phi.shape[1]
+    r2 = float(radius) ** 2
+    mask = _query_mask(n, wo, valid, M)
+    rho = np.ones((M, C)) if albedo is None else np.asarray(albedo, dtype=_F64).T
+    out = np.zeros((M, C))
+    den = np.zeros((M, C))
+    count = np.zeros(M)
+    near = np.zeros(M, dtype=bool)
+    step = _chunk(pos.shape[0])
+    for a in range(0, M, step):
+        xs = X[a:a + step]
+        d2 = np.sum((xs[:, None, :] - pos[None, :, :]) ** 2, axis=2)
+        inc = d2 <= r2
+        out[a:a + step] = inc.astype(_F64) @ phi
+        den[a:a + step] = inc.astype(_F64) @ np.abs(phi)
+        count[a:a + step] = inc.sum(axis=1)
+        near[a:a + step] = np.any(np.abs(d2 - r2) <= band * r2, axis=1)
+    area = np.pi * r2
+    g = mask[:, None].astype(_F64)
+    return {"out": (rho * out / area * g).T, "denom": (rho * den / area * g).T,
+            "count": count * mask, "near": near}
+
+
 def mse_loss(out, target, valid=None) -> float:
     """Sec. 4.3: (1/|V|) sum_{x in V} |O(x) - O_ref(x)|_2^2 over the valid points."""
     O = np.asarray(out, dtype=_F64)

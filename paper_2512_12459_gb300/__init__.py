@@ -7,14 +7,15 @@ raises if libgpf.so has not been built (there is no fallback path)."""
 
 from . import _abi
 from ._abi import GPFError, LIB_PATH, load
-from .api import (GPF_NORMALIZED, GPF_SUM, PAPER_EPS, PAPER_LR, PAPER_R, AdamState, Field,
-                  GridConfig, Index, Queries, gpf_adam_step, gpf_count_pairs,
+from .api import (GPF_DISK_KDE, GPF_NORMALIZED, GPF_SUM, PAPER_EPS, PAPER_LR, PAPER_R,
+                  AdamState, Field, GridConfig, Index, Queries, gpf_adam_step, gpf_count_pairs,
                   gpf_launch_count, gpf_mse_loss_grad, gpf_radiance_bwd, gpf_radiance_fwd,
-                  grid_for_bounds)
+                  grid_for_bounds, photon_field)
 from .autograd import GPFRadiance, gpf_radiance
 
 __all__ = [
-    "GPFError", "LIB_PATH", "load", "GPF_NORMALIZED", "GPF_SUM", "PAPER_EPS", "PAPER_LR",
+    "GPFError", "LIB_PATH", "load", "GPF_NORMALIZED", "GPF_SUM", "GPF_DISK_KDE", "PAPER_EPS",
+    "PAPER_LR", "photon_field",
     "PAPER_R", "AdamState", "Field", "GridConfig", "Index", "Queries", "gpf_adam_step",
     "gpf_mse_loss_grad", "gpf_radiance_bwd", "gpf_radiance_fwd", "grid_for_bounds",
     "gpf_count_pairs", "gpf_launch_count",

@@ -19,6 +19,7 @@ GPF_ERR_MISMATCH = 6
 
 GPF_SUM = 0
 GPF_NORMALIZED = 1
+GPF_DISK_KDE = 2
 GPF_MAX_CHANNELS = 8
 GPF_MAX_DIM = 1024
 GPF_MAX_LEVELS = 16

@@ -14,10 +14,10 @@ from typing import Optional, Sequence
 import torch
 
 from . import _abi
-from ._abi import GPF_NORMALIZED, GPF_SUM, GPFError, check, load
+from ._abi import GPF_DISK_KDE, GPF_NORMALIZED, GPF_SUM, GPFError, check, load
 
 __all__ = [
-    "GPF_SUM", "GPF_NORMALIZED", "GPFError", "GridConfig", "Field", "Queries", "Index",
+    "GPF_SUM", "GPF_NORMALIZED", "GPF_DISK_KDE", "GPFError", "GridConfig", "Field", "Queries", "Index",
     "grid_for_bounds", "gpf_radiance_fwd", "gpf_radiance_bwd", "gpf_mse_loss_grad",
     "gpf_adam_step", "AdamState", "PAPER_R", "PAPER_EPS", "PAPER_LR",
 ]
@@ -136,6 +136,20 @@ class Field:
         mean = self.mean if self.storage == _abi.GPF_BF16_MEAN32 else a[:3] + self.mean.float()
         return Field(mean.contiguous(), self.quat.float(),
                      (a[3:4] + self.logscale.float()).contiguous(), self.spectrum.float())
+
+
+def photon_field(position: torch.Tensor, flux: torch.Tensor, radius: float,
+                 cutoff_sigma: float = 3.0) -> Field:
+    """Photons as a Field for the GPF_DISK_KDE gather: mean = position [3,N],
+    spectrum = flux [C,N], identity rotations and isotropic log-scales
+    log(radius / cutoff_sigma), so that each photon's k-sigma box is the box
+    of its gather disk."""
+    n = int(position.shape[1])
+    quat = torch.zeros((4, n), dtype=torch.float32, device=position.device)
+    quat[0] = 1.0
+    lsc = torch.full((3, n), math.log(radius / cutoff_sigma), dtype=torch.float32,
+                     device=position.device)
+    return Field(position.float().contiguous(), quat, lsc, flux.float().contiguous())
 
 
 @dataclasses.dataclass

@@ -159,8 +159,10 @@ gpf_status check_queries(const gpf_index* ix, const gpf_queries* q) {
 
 gpf_status check_params(const gpf_query_params* p) {
   if (!p) return fail(GPF_ERR_INVALID_ARG, "params is NULL");
-  if (p->mode != GPF_SUM && p->mode != GPF_NORMALIZED)
-    return fail(GPF_ERR_INVALID_ARG, "params.mode = %d is not GPF_SUM or GPF_NORMALIZED", p->mode);
+  if (p->mode != GPF_SUM && p->mode != GPF_NORMALIZED && p->mode != GPF_DISK_KDE)
+    return fail(GPF_ERR_INVALID_ARG, "params.mode = %d is not a gpf_mode", p->mode);
+  if (p->mode == GPF_DISK_KDE && !(p->r_max > 0.0f && isfinite(p->r_max)))
+    return fail(GPF_ERR_INVALID_ARG, "GPF_DISK_KDE needs a finite gather radius r_max > 0");
   if (isnan(p->r_max) || p->r_max < 0.0f)
     return fail(GPF_ERR_INVALID_ARG, "params.r_max must be >= 0 or +INF");
   if (!(p->eps > 0.0f) || !isfinite(p->eps))
@@ -425,6 +427,8 @@ gpf_status gpf_radiance_bwd(const gpf_index* index, const gpf_field* field,
   if ((s = check_queries(index, queries)) != GPF_OK) return s;
   if ((s = check_params(params)) != GPF_OK) return s;
   if ((s = check_same(index, field, queries)) != GPF_OK) return s;
+  if (params->mode == GPF_DISK_KDE)
+    return fail(GPF_ERR_INVALID_ARG, "GPF_DISK_KDE (the photon density estimate) has no gradient");
   if (!grads) return fail(GPF_ERR_INVALID_ARG, "grads is NULL");
   if (grads->reserved != 0) return fail(GPF_ERR_INVALID_ARG, "grads.reserved must be 0");
   if (field->n > 0) {

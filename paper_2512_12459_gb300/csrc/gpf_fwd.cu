@@ -50,6 +50,7 @@ struct FwdArgs {
   int mode;
   float r, r2, inv_rr;     // falloff radius, its square, 1/max(r, 1e-6)
   float eps;
+  float kde_scale;         // disk kernel: 1 / (pi r^2)
   float cut, cut2;         // k, k^2
   float* out;              // [C,M]
   float* z;                // [M] or null
@@ -68,13 +69,28 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-// Weight of one pair: w = exp(-Q/2) psi(|d|) when Q <= k^2 (hit = true).
-// In count mode only the evaluated and included pairs are counted.
-template <bool PSI, bool COUNT>
+// Pair kernels: the Gaussian weight alone, with the soft falloff psi, or the
+// disk of the photon density estimate.
+constexpr int kKernGauss = 0, kKernFalloff = 1, kKernDisk = 2;
+
+// Weight of one pair: w = exp(-Q/2) psi(|d|) when Q <= k^2 (hit = true); for
+// the disk kernel w = 1 when |d| <= r (Eq. kde; 1/(pi r^2) is applied once
+// per hit point). In count mode only evaluated and included pairs are counted.
+template <int KERN, bool COUNT>
 __device__ __forceinline__ float pair_weight(const float* __restrict__ r, float px, float py,
                                              float pz, const FwdArgs& a, bool& hit,
                                              uint32_t& n_eval, uint32_t& n_inc) {
   const float dx = px - r[0], dy = py - r[1], dz = pz - r[2];
+  if (KERN == kKernDisk) {
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    hit = d2 <= a.r2;
+    if (COUNT) {
+      ++n_eval;
+      n_inc += hit ? 1u : 0u;
+      hit = false;
+    }
+    return hit ? 1.0f : 0.0f;
+  }
   const float u0 = fmaf(r[4], dx, fmaf(r[5], dy, r[6] * dz));
   const float u1 = fmaf(r[7], dx, fmaf(r[8], dy, r[9] * dz));
   const float u2 = fmaf(r[10], dx, fmaf(r[11], dy, r[12] * dz));
@@ -88,7 +104,7 @@ __device__ __forceinline__ float pair_weight(const float* __restrict__ r, float 
   hit = Q <= a.cut2;
   if (!hit) return 0.0f;
   float e = -0.5f * Q;
-  if (PSI) {
+  if (KERN == kKernFalloff) {
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     if (d2 > a.r2) {
       // correctly rounded: the exponent's sensitivity to |d| is 6 t (t + 1) / |d|
@@ -101,12 +117,12 @@ __device__ __forceinline__ float pair_weight(const float* __restrict__ r, float 
 }
 
 // Accumulate one Gaussian record r into this lane's sums (or count it).
-template <int C, bool PSI, bool COUNT>
+template <int C, int KERN, bool COUNT>
 __device__ __forceinline__ void eval_pair(const float* __restrict__ r, float px, float py, float pz,
                                           const FwdArgs& a, float (&L)[C], float& Z,
                                           uint32_t& n_eval, uint32_t& n_inc) {
   bool hit;
-  const float w = pair_weight<PSI, COUNT>(r, px, py, pz, a, hit, n_eval, n_inc);
+  const float w = pair_weight<KERN, COUNT>(r, px, py, pz, a, hit, n_eval, n_inc);
   if (hit) {
 #pragma unroll
     for (int c = 0; c < C; ++c) L[c] = fmaf(w, r[13 + c], L[c]);
@@ -160,7 +176,7 @@ __device__ __forceinline__ void load_rec(const float* __restrict__ rec, uint32_t
 }
 
 // COUNT: count the evaluated and included pairs instead of summing radiance.
-template <int C, bool BRUTE, bool PSI, bool COUNT>
+template <int C, bool BRUTE, int KERN, bool COUNT>
 __global__ void __launch_bounds__(kFwdThreads)
 fwd_kernel(FwdArgs a) {
   constexpr int RS = rec_stride(C);
@@ -223,7 +239,7 @@ fwd_kernel(FwdArgs a) {
       __syncwarp();
       if (active)
         for (int s = 0; s < cnt; ++s)
-          eval_pair<C, PSI, COUNT>(my_rec + s * RS, px, py, pz, a, L, Z, n_eval, n_inc);
+          eval_pair<C, KERN, COUNT>(my_rec + s * RS, px, py, pz, a, L, Z, n_eval, n_inc);
       __syncwarp();
     }
   } else {
@@ -323,7 +339,7 @@ fwd_kernel(FwdArgs a) {
             const int nk = __popc(kb);
             if (active)
               for (int s = 0; s < nk; ++s)
-                eval_pair<C, PSI, COUNT>(my_rec + s * RS, px, py, pz, a, L, Z, n_eval, n_inc);
+                eval_pair<C, KERN, COUNT>(my_rec + s * RS, px, py, pz, a, L, Z, n_eval, n_inc);
             __syncwarp();
             v = vn;
           }
@@ -389,7 +405,7 @@ fwd_kernel(FwdArgs a) {
             load_rec<RS>(a.rec, v & G.id_mask, rr);
             if (rec_level(rr[3]) == (uint32_t)lev) {
               bool hit;
-              const float w = pair_weight<PSI, COUNT>(rr, qx, qy, qz, a, hit, n_eval, n_inc);
+              const float w = pair_weight<KERN, COUNT>(rr, qx, qy, qz, a, hit, n_eval, n_inc);
               if (hit) {
 #pragma unroll
                 for (int c = 0; c < C; ++c) pc[c] = fmaf(w, rr[13 + c], pc[c]);
@@ -412,6 +428,7 @@ fwd_kernel(FwdArgs a) {
     if (active) {
       float scale = 1.0f;
       if (a.mode == GPF_NORMALIZED) scale = 1.0f / fmaxf(Z, a.eps);
+      else if (a.mode == GPF_DISK_KDE) scale = a.kde_scale;
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         const float rho = a.albedo ? a.albedo[(int64_t)c * a.m + q] : 1.0f;
@@ -465,6 +482,7 @@ cudaError_t launch_forward(const IndexDims& d, const IndexBuffers& b, const gpf_
   a.r2 = psi ? p.r_max * p.r_max : 0.0f;
   a.inv_rr = psi ? 1.0f / fmaxf(p.r_max, 1e-6f) : 0.0f;
   a.eps = p.eps;
+  a.kde_scale = psi ? (float)(1.0 / (M_PI * (double)p.r_max * (double)p.r_max)) : 0.0f;
   a.cut = d.cutoff;
   a.cut2 = isinf(d.cutoff) ? INFINITY : d.cutoff * d.cutoff;
   a.out = out;
@@ -483,22 +501,20 @@ cudaError_t launch_forward(const IndexDims& d, const IndexBuffers& b, const gpf_
         reinterpret_cast<const void*>(&fwd_kernel<CC, BR, PS, CN>), kFwdThreads, want);   \
     fwd_kernel<CC, BR, PS, CN><<<blocks, kFwdThreads, 0, stream>>>(a);                    \
   } while (0)
-#define GPF_FWD_MODES(CC, BR, PS)                   \
-  do {                                              \
-    if (counts) GPF_FWD_LAUNCH(CC, BR, false, true); \
-    else GPF_FWD_LAUNCH(CC, BR, PS, false);         \
+#define GPF_FWD_MODES(CC, BR)                                          \
+  do {                                                                 \
+    if (counts) GPF_FWD_LAUNCH(CC, BR, kKernGauss, true);              \
+    else if (kern == kKernDisk) GPF_FWD_LAUNCH(CC, BR, kKernDisk, false); \
+    else if (kern == kKernFalloff) GPF_FWD_LAUNCH(CC, BR, kKernFalloff, false); \
+    else GPF_FWD_LAUNCH(CC, BR, kKernGauss, false);                    \
   } while (0)
-#define GPF_FWD_CASE(CC)                                                   \
-  case CC:                                                                 \
-    if (d.brute) {                                                         \
-      if (psi) GPF_FWD_MODES(CC, true, true);                              \
-      else GPF_FWD_MODES(CC, true, false);                                 \
-    } else {                                                               \
-      if (psi) GPF_FWD_MODES(CC, false, true);                             \
-      else GPF_FWD_MODES(CC, false, false);                                \
-    }                                                                      \
-    note_launches(1);                                                      \
+#define GPF_FWD_CASE(CC)                  \
+  case CC:                                \
+    if (d.brute) GPF_FWD_MODES(CC, true); \
+    else GPF_FWD_MODES(CC, false);        \
+    note_launches(1);                     \
     break;
+  const int kern = p.mode == GPF_DISK_KDE ? kKernDisk : psi ? kKernFalloff : kKernGauss;
   if (ev.start) {
     const cudaError_t e = cudaEventRecord(ev.start, stream);
     if (e != cudaSuccess) return e;

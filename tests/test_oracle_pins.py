@@ -425,3 +425,49 @@ def test_pins_catch_a_wrong_cutoff(monkeypatch):
     monkeypatch.setattr(go, "_pairs", lambda P, xs, r, c: good(P, xs, r, c * c if math.isfinite(c) else c))
     _expect_failure(test_volume_integral_of_one_gaussian, 3.0, chi2.cdf(9.0, 3), 3e-3)
     _expect_failure(test_worked_examples_closed_forms)
+
+
+# ---- the photon density estimate (Sec. 3.2, Eq. kde)
+
+def _lattice(h, half, flux=1.0):
+    ij = np.array([(i, j) for i in range(-half, half + 1) for j in range(-half, half + 1)], float)
+    pos = np.zeros((3, len(ij)))
+    pos[:2] = ij.T * h
+    return pos, np.full((1, len(ij)), flux)
+
+
+def _gauss_circle(radius_in_cells):
+    """Lattice points (i, j) with i^2 + j^2 <= R^2, by integer enumeration."""
+    R2 = radius_in_cells ** 2
+    k = int(np.floor(radius_in_cells)) + 1
+    return sum(1 for i in range(-k, k + 1) for j in range(-k, k + 1) if i * i + j * j <= R2)
+
+
+@pytest.mark.parametrize("R,count", [(5.0, 81), (2.5, 21), (1.0, 5), (0.5, 1)])
+def test_disk_kde_counts_lattice_photons(R, count):
+    """Photons on a square lattice (spacing h, unit flux), gathered at a
+    lattice point with radius R h: the Gauss circle count, edge included
+    (R = 5 puts (3, 4) and (5, 0) on the edge), over the disk area."""
+    h = 0.25
+    pos, flux = _lattice(h, 8)
+    assert _gauss_circle(R) == count
+    x = np.zeros((3, 1))
+    n = np.array([[0.0], [0.0], [1.0]])
+    out = oracle.disk_kde(pos, flux, x, n, n, R * h)
+    np.testing.assert_allclose(out["out"][0, 0], count / (np.pi * (R * h) ** 2), rtol=1e-14)
+    assert out["count"][0] == count
+
+
+def test_disk_kde_single_photon_gate_and_albedo():
+    pos = np.array([[0.1], [0.0], [0.0]])
+    flux = np.array([[2.0], [4.0]])
+    x = np.array([[0.0, 0.0, 0.0, 0.5], [0.0, 0.0, 0.0, 0.0], [0.0, 0.0, 0.0, 0.0]])
+    n = np.array([[0.0] * 4, [0.0] * 4, [1.0] * 4])
+    wo = n.copy()
+    wo[2, 1] = -1.0                                  # facing away
+    alb = np.array([[0.5] * 4, [0.25] * 4])
+    valid = np.array([1, 1, 0, 1], np.uint8)
+    out = oracle.disk_kde(pos, flux, x, n, wo, 0.2, albedo=alb, valid=valid)["out"]
+    a = np.pi * 0.04
+    np.testing.assert_allclose(out[:, 0], [0.5 * 2 / a, 0.25 * 4 / a], rtol=1e-14)
+    assert np.all(out[:, 1:] == 0)                   # gate, invalid, out of reach
