@@ -427,7 +427,7 @@ def run_kde(args):
     import torch
     import synth
     import paper_2512_12459_gb300 as gpf
-    from paper_2512_12459_gb300.setup_index import make_index
+    from paper_2512_12459_gb300.setup_index import autotune, make_index
 
     torch.cuda.set_device(0)
     pos, flux = synth.caustic_photons(N_PHOTONS, seed=0)
@@ -437,7 +437,9 @@ def run_kde(args):
                                torch.as_tensor(flux.T.copy(), dtype=torch.float32, device="cuda"),
                                R_MAX)
     queries = gpf.Queries.from_numpy(qnp)
-    idx = make_index(photons, queries, query_cell=CELL, max_span=3, coop_cells=8)
+    grid, _ = autotune(photons, queries, mode=gpf.GPF_DISK_KDE, r_max=R_MAX, repeats=1,
+                       max_spans=(3, 4, 6, 8), coop_options=(1, 2, 4, 8), backward=False)
+    idx = make_index(photons, queries, grid=grid)
     out = torch.empty((3, queries.m), device="cuda")
     z = torch.empty((queries.m,), device="cuda")
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -470,7 +472,83 @@ def run_kde(args):
         "gather_queries_per_s": n_active / (gather_ms / 1e3),
         "ms_breakdown": {"build": build_ms, "gather": gather_ms},
         "photons_gathered": gathered, "photons_per_hit_point": gathered / max(n_active, 1),
+        "grid": {"query_cell": grid.cell_size * (1 << grid.query_level), "levels": grid.levels,
+                 "max_span": grid.max_span, "coop_cells": grid.coop_cells},
     }
+    print(json.dumps(line), flush=True)
+
+
+def run_scaling(args):
+    """Table S1's experiment as throughput: the caustic scene's training step
+    (build, forward, MSE, backward, Adam; autotuned grid) on the 1024x1024
+    view for the paper's field sizes (10K-200K Gaussians) and this build's
+    (0.5M-2M), L2 flushed between steps; one JSON object per size."""
+    import torch
+    import synth
+    import paper_2512_12459_gb300 as gpf
+    from paper_2512_12459_gb300.setup_index import autotune, make_index
+
+    torch.cuda.set_device(0)
+    qnp = synth.pinhole_hitpoints(EYE0, LOOK_AT, VIEW, VIEW)
+    queries = gpf.Queries.from_numpy(qnp)
+    n_active = int(qnp.valid.sum())
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    rows = []
+    for n in (10_000, 50_000, 100_000, 200_000, 500_000, 1_000_000, 2_000_000):
+        pos, flux = synth.caustic_photons(n, seed=0)
+        fnp = synth.field_from_photons(pos, flux, seed=0)
+        tgt = gpf.Field.from_numpy(synth.perturbed_copy(fnp, seed=1))
+        field = gpf.Field.from_numpy(fnp)
+        ti = make_index(tgt, queries, query_cell=CELL)
+        ti.build(tgt, queries)
+        target = gpf.gpf_radiance_fwd(ti, tgt, queries, gpf.GPF_SUM, r_max=R_MAX)[0].clone()
+        del ti
+        grid, _ = autotune(field, queries, r_max=R_MAX, repeats=1)
+        idx = make_index(field, queries, grid=grid, headroom=1.25)
+        state = gpf.AdamState.zeros_like(field)
+        grads = gpf.Field.zeros_like(field)
+        out = torch.empty((3, queries.m), device="cuda")
+        z = torch.empty((queries.m,), device="cuda")
+        gout = torch.empty_like(out)
+
+        def step(ev=None):
+            if ev:
+                ev[0].record()
+            idx.build(field, queries)
+            gpf.gpf_radiance_fwd(idx, field, queries, gpf.GPF_SUM, r_max=R_MAX, out=out, z=z)
+            if ev:
+                ev[1].record()
+            gpf.gpf_mse_loss_grad(out, target, queries.valid, grad=gout)
+            gpf.gpf_radiance_bwd(idx, field, queries, gout, out, z, gpf.GPF_SUM, r_max=R_MAX,
+                                 grads=grads)
+            gpf.gpf_adam_step(field, grads, state, lr=LR)
+            if ev:
+                ev[2].record()
+
+        for _ in range(args.warmup):
+            step()
+        marks = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            step(ev)
+            marks.append(ev)
+        torch.cuda.synchronize()
+        fwd_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in marks]))
+        step_ms = float(np.mean([e[0].elapsed_time(e[2]) for e in marks]))
+        pairs = gpf.gpf_count_pairs(idx, field, queries)
+        rows.append({"gaussians": n, "ms_per_step": step_ms, "queries_per_s": n_active / step_ms * 1e3,
+                     "build_fwd_ms": fwd_ms, "included_pairs_per_query": pairs["included"] / n_active})
+        del idx, field, state, grads, target
+        torch.cuda.empty_cache()
+    line = {"metric": "training step time vs number of Gaussians (Table S1 replay)",
+            "value": rows[-1]["queries_per_s"], "unit": "queries/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"caustic scene, {VIEW}x{VIEW} view, r={R_MAX}",
+                       "active_hit_points": n_active, "l2": "flushed between steps"},
+            "rows": rows,
+            "paper_table_s1_s": {"10000": 7.230, "50000": 12.70, "100000": 16.37, "200000": 24.35}}
     print(json.dumps(line), flush=True)
 
 
@@ -488,7 +566,7 @@ def main():
                     help="Gaussians (smaller cases are for profiling only)")
     ap.add_argument("--view", type=int, default=VIEW, help="view side in pixels")
     ap.add_argument("--workload", default="single",
-                    choices=["single", "batched", "bf16", "kde"],
+                    choices=["single", "batched", "bf16", "kde", "scaling"],
                     help="single: the 1M-Gaussian 1024x1024 step (default line); batched: "
                          "64 uneven views over 2M Gaussians, graph replay vs per-view launches")
     ap.add_argument("--batched-views", type=int, default=64)
@@ -516,6 +594,9 @@ def main():
         return
     if args.workload == "kde":
         run_kde(args)
+        return
+    if args.workload == "scaling":
+        run_scaling(args)
         return
 
     import torch

@@ -154,25 +154,30 @@ struct GaussianRegs {
   float M[9];
 };
 
-// One (Gaussian, hit point) pair of the backward.
+// A packed hit point, all of it (one 32-byte sector for C <= 3): the loads
+// of a pair are issued together, before its arithmetic.
+template <int C>
+__device__ __forceinline__ void load_qrec(const float* __restrict__ qr,
+                                          float (&q)[qrec_stride(C)]) {
+#pragma unroll
+  for (int v = 0; v < qrec_stride(C) / 4; ++v) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(qr) + v);
+    q[4 * v] = t.x; q[4 * v + 1] = t.y; q[4 * v + 2] = t.z; q[4 * v + 3] = t.w;
+  }
+}
+
+// One (Gaussian, hit point) pair of the backward, the hit point in q.
 template <int C, bool PSI>
-__device__ __forceinline__ void bwd_pair(const GaussianRegs& G, const float (&phi)[C],
-                                         const float* __restrict__ qr, const BwdArgs& a,
-                                         Acc<C>& acc) {
-  constexpr int QS = qrec_stride(C);
-  const float4 q0 = __ldg(reinterpret_cast<const float4*>(qr));
-  const float dx = q0.x - G.mx, dy = q0.y - G.my, dz = q0.z - G.mz;
+__device__ __forceinline__ void bwd_pair_q(const GaussianRegs& G, const float (&phi)[C],
+                                           const float (&q)[qrec_stride(C)], const BwdArgs& a,
+                                           Acc<C>& acc) {
+  const float dx = q[0] - G.mx, dy = q[1] - G.my, dz = q[2] - G.mz;
   const float u0 = fmaf(G.M[0], dx, fmaf(G.M[1], dy, G.M[2] * dz));
   const float u1 = fmaf(G.M[3], dx, fmaf(G.M[4], dy, G.M[5] * dz));
   const float u2 = fmaf(G.M[6], dx, fmaf(G.M[7], dy, G.M[8] * dz));
   const float Q = fmaf(u0, u0, fmaf(u1, u1, u2 * u2));
   if (!(Q <= a.cut2)) return;
-  float qv[QS - 4];
-#pragma unroll
-  for (int v = 0; v < (QS - 4) / 4; ++v) {
-    const float4 t = __ldg(reinterpret_cast<const float4*>(qr + 4 + 4 * v));
-    qv[4 * v] = t.x; qv[4 * v + 1] = t.y; qv[4 * v + 2] = t.z; qv[4 * v + 3] = t.w;
-  }
+  const float* qv = q + 4;
   float e = -0.5f * Q;
   float pcoef = 0.0f;  // 6 t / (r' |d|), the falloff's share of dw/dmu per unit w
   if (PSI) {
@@ -185,7 +190,7 @@ __device__ __forceinline__ void bwd_pair(const GaussianRegs& G, const float (&ph
     }
   }
   const float w = ex2_approx(e * kLog2e);
-  const float zeta = q0.w, kappa = qv[0];
+  const float zeta = q[3], kappa = qv[0];
   float gp = 0.0f;
 #pragma unroll
   for (int c = 0; c < C; ++c) gp = fmaf(qv[1 + c], phi[c], gp);
@@ -209,6 +214,15 @@ __device__ __forceinline__ void bwd_pair(const GaussianRegs& G, const float (&ph
   const float wz = w * zeta;
 #pragma unroll
   for (int c = 0; c < C; ++c) acc.P[c] = fmaf(qv[1 + c], wz, acc.P[c]);
+}
+
+template <int C, bool PSI>
+__device__ __forceinline__ void bwd_pair(const GaussianRegs& G, const float (&phi)[C],
+                                         const float* __restrict__ qr, const BwdArgs& a,
+                                         Acc<C>& acc) {
+  float q[qrec_stride(C)];
+  load_qrec<C>(qr, q);
+  bwd_pair_q<C, PSI>(G, phi, q, a, acc);
 }
 
 // Gradients of one Gaussian from its reduced sums (runs on one lane).

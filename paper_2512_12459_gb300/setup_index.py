@@ -125,8 +125,8 @@ def make_index(field: Field, queries: Queries, cutoff_sigma: float = 3.0,
 
 
 def time_step(index: Index, field: Field, queries: Queries, mode: int = 0, r_max: float = 0.02,
-              repeats: int = 3) -> float:
-    """Median milliseconds of build + forward + backward with `index`."""
+              repeats: int = 3, backward: bool = True) -> float:
+    """Median milliseconds of build + forward (+ backward) with `index`."""
     from . import api
     out = torch.empty((field.channels, queries.m), device=field.mean.device)
     z = torch.empty((queries.m,), device=field.mean.device)
@@ -139,7 +139,9 @@ def time_step(index: Index, field: Field, queries: Queries, mode: int = 0, r_max
         e0.record()
         index.build(field, queries)
         api.gpf_radiance_fwd(index, field, queries, mode, r_max=r_max, out=out, z=z)
-        api.gpf_radiance_bwd(index, field, queries, gout, out, z, mode, r_max=r_max, grads=grads)
+        if backward:
+            api.gpf_radiance_bwd(index, field, queries, gout, out, z, mode, r_max=r_max,
+                                 grads=grads)
         e1.record()
         e1.synchronize()
         if i:                       # the first run pays one-off costs
@@ -150,14 +152,16 @@ def time_step(index: Index, field: Field, queries: Queries, mode: int = 0, r_max
 def autotune(field: Field, queries: Queries, cutoff_sigma: float = 3.0, mode: int = 0,
              r_max: float = 0.02, query_cells: Optional[Sequence[float]] = None,
              max_spans: Sequence[int] = (3, 4, 6), coop_options: Sequence[int] = (2, 4, 8),
-             repeats: int = 3, headroom: float = 1.25):
+             repeats: int = 3, headroom: float = 1.25, backward: bool = True):
     """Chooses the grid geometry and the forward tile shape for this field
     and batch of hit points by timing build + forward + backward, one knob at
     a time: the query cell size (the hit-point grid), then the largest span of
     a Gaussian's box in cells of its level (the cell size of every level),
     then the cooperative-mode threshold of the forward's 32-point tiles.
     Returns (best GridConfig, report), report = [(knobs, ms), ...] in the
-    order tried. Results are independent of the choice; only speed differs."""
+    order tried. Results are independent of the choice; only speed differs.
+    backward=False times build + forward only (a query without gradient,
+    such as the GPF_DISK_KDE gather)."""
     if query_cells is None:
         query_cells = (0.01, 0.02, 0.04, 0.08)
     best = {"query_cell": 0.02, "max_span": 4, "coop_cells": 4}
@@ -170,7 +174,7 @@ def autotune(field: Field, queries: Queries, cutoff_sigma: float = 3.0, mode: in
             idx = make_index(field, queries, cutoff_sigma=cutoff_sigma, headroom=headroom,
                              query_cell=knobs["query_cell"], max_span=knobs["max_span"],
                              coop_cells=knobs["coop_cells"])
-            ms = time_step(idx, field, queries, mode, r_max, repeats)
+            ms = time_step(idx, field, queries, mode, r_max, repeats, backward)
             cache[key] = (ms, idx.grid)
             report.append((dict(knobs), ms))
             del idx
