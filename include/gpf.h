@@ -133,12 +133,26 @@ typedef struct gpf_queries {
 } gpf_queries;
 
 /* Query parameters. */
+/* Neighbourhood of a hit point (gpf_query_params.neighbourhood). */
+#define GPF_NB_KSIGMA 0    /* {i : Q_i <= k^2}, k = the index's cutoff_sigma   */
+#define GPF_NB_BALL_KNN 1  /* the paper's hybrid query (Sec. 4.2, Neighborhood
+                              Search; Algorithm S3): the Gaussians whose mean
+                              lies within ball_r of x, or, when there are
+                              fewer than k_min of them, the k_min nearest
+                              means (ties: the smaller index). No truncation
+                              of the weights. ball_r = 0: kNN only; k_min = 0:
+                              ball only. Forward only (no gradient).         */
+#define GPF_MAX_KMIN 16
+
 typedef struct gpf_query_params {
   int32_t mode;          /* gpf_mode                                         */
   float r_max;           /* falloff radius r (paper: 0.02); +INF disables psi;
                             GPF_DISK_KDE: the gather radius (finite, > 0)    */
   float eps;             /* normalisation floor (paper: 1e-6)                */
-  int32_t reserved;      /* must be 0                                        */
+  int32_t neighbourhood; /* GPF_NB_KSIGMA or GPF_NB_BALL_KNN                 */
+  float ball_r;          /* GPF_NB_BALL_KNN: ball radius (paper: 0.02), at
+                            most the index's ball_radius                     */
+  int32_t k_min;         /* GPF_NB_BALL_KNN: 0..GPF_MAX_KMIN (paper: 3)      */
 } gpf_query_params;
 
 /* Multi-level uniform grid and capacities of an index.
@@ -172,6 +186,10 @@ typedef struct gpf_grid_config {
   int32_t field_storage; /* storage of the fields built from: GPF_F32,
                             GPF_BF16 or GPF_BF16_MEAN32 (the 16-bit forms
                             reserve float32 decode arrays)                   */
+  float ball_radius;     /* > 0: also list every Gaussian once under the cell
+                            of its mean on the first level whose cells are
+                            >= ball_radius, for GPF_NB_BALL_KNN queries with
+                            a ball of at most this radius; 0: none           */
   int64_t max_gaussians; /* capacity N_max                                   */
   int64_t max_queries;   /* capacity M_max                                   */
   int64_t max_pairs;     /* capacity of (cell, Gaussian) entries             */

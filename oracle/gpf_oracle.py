@@ -254,6 +254,71 @@ def radiance_bwd(mean, quat, logscale, spectrum, x, n, wo, grad_out, albedo=None
             "spectrum": g_phi.T.copy(), "fwd": fwd}
 
 
+def hybrid_fwd(mean, quat, logscale, spectrum, x, n, wo, albedo=None, valid=None,
+               mode: int = GPF_NORMALIZED, r_max: float = 0.02, eps: float = 1e-6,
+               ball_r: float = 0.02, k_min: int = 3, band: float = 1e-5) -> Dict[str, np.ndarray]:
+    """The paper's hybrid neighbourhood (Sec. 4.2, Neighborhood Search; the
+    query listing of Algorithm S3): N(x) = the Gaussians whose mean lies
+    within ball_r of x if there are at least k_min of them, else the k_min
+    nearest means (ties: the smaller index); the union with the ball is the
+    same set, since every mean in the ball is nearer than every mean outside.
+    Weights w_i = exp(-Q_i/2) psi(|d_i|) over N(x), no truncation; output as
+    radiance_fwd (GPF_SUM or GPF_NORMALIZED).
+
+    Returns out, L, Z, denom (as radiance_fwd), logw_max [M] (the largest log
+    weight in N(x)), n_nb [M] (|N(x)|), knn [M] (the k_min nearest were used)
+    and near [M]: the selection is sensitive to rounding (a mean within
+    band*ball_r^2 of the ball's edge in squared distance, or, in kNN mode, the
+    k-th and (k+1)-th squared distances within a relative band of each other)."""
+    P = _Prepared(mean, quat, logscale, spectrum)
+    X = np.asarray(x, dtype=_F64).T
+    M, C, N = X.shape[0], P.c, P.n
+    mask = _query_mask(n, wo, valid, M)
+    rho = np.ones((M, C)) if albedo is None else np.asarray(albedo, dtype=_F64).T
+    L = np.zeros((M, C))
+    Z = np.zeros(M)
+    den = np.zeros((M, C))
+    n_nb = np.zeros(M, dtype=np.int64)
+    knn = np.zeros(M, dtype=bool)
+    near = np.zeros(M, dtype=bool)
+    logw = np.full(M, -np.inf)
+    r2 = float(ball_r) ** 2
+    idx = np.arange(N)
+    step = _chunk(N)
+    for a in range(0, M, step):
+        xs = X[a:a + step]
+        d, _, _, _, _, w = _pairs(P, xs, r_max, math.inf)        # every pair, untruncated
+        d2 = d[..., 0] ** 2 + d[..., 1] ** 2 + d[..., 2] ** 2
+        for j in range(xs.shape[0]):
+            ball = d2[j] <= r2
+            sel = ball
+            if ball.sum() < k_min:
+                order = np.lexsort((idx, d2[j]))                 # by distance, then index
+                sel = np.zeros(N, dtype=bool)
+                sel[order[:min(k_min, N)]] = True
+                knn[a + j] = True
+                if N > k_min:
+                    dk, dk1 = d2[j][order[k_min - 1]], d2[j][order[k_min]]
+                    near[a + j] |= abs(dk1 - dk) <= band * max(dk, 1e-300)
+            if r2 > 0:
+                near[a + j] |= bool(np.any(np.abs(d2[j] - r2) <= band * r2))
+            wj = np.where(sel, w[j], 0.0)
+            with np.errstate(divide="ignore"):
+                logw[a + j] = np.log(wj.max()) if sel.any() else -np.inf
+            L[a + j] = wj @ P.phi
+            Z[a + j] = wj.sum()
+            den[a + j] = wj @ np.abs(P.phi)
+            n_nb[a + j] = sel.sum()
+    g = mask.astype(_F64)[:, None]
+    if mode == GPF_NORMALIZED:
+        zz = np.maximum(Z, eps)[:, None]
+        out, denom = rho * L / zz * g, rho * den / zz * g
+    else:
+        out, denom = rho * L * g, rho * den * g
+    return {"out": out.T, "L": L.T, "Z": Z * mask, "denom": denom.T, "n_nb": n_nb * mask,
+            "knn": knn & mask, "near": near & mask, "logw_max": logw}
+
+
 def disk_kde(position, flux, x, n, wo, radius: float, albedo=None, valid=None,
              band: float = 1e-5) -> Dict[str, np.ndarray]:
     """The per-view photon density estimate that the field replaces (Sec. 3.2,

@@ -7,7 +7,7 @@ raises if libgpf.so has not been built (there is no fallback path)."""
 
 from . import _abi
 from ._abi import GPFError, LIB_PATH, load
-from .api import (GPF_DISK_KDE, GPF_NORMALIZED, GPF_SUM, PAPER_EPS, PAPER_LR, PAPER_R,
+from .api import (GPF_DISK_KDE, GPF_NB_BALL_KNN, GPF_NB_KSIGMA, GPF_NORMALIZED, GPF_SUM, PAPER_EPS, PAPER_LR, PAPER_R,
                   AdamState, Field, GridConfig, Index, Queries, gpf_adam_step, gpf_count_pairs,
                   gpf_launch_count, gpf_mse_loss_grad, gpf_radiance_bwd, gpf_radiance_fwd,
                   grid_for_bounds, photon_field)
@@ -15,6 +15,7 @@ from .autograd import GPFRadiance, gpf_radiance
 
 __all__ = [
     "GPFError", "LIB_PATH", "load", "GPF_NORMALIZED", "GPF_SUM", "GPF_DISK_KDE", "PAPER_EPS",
+    "GPF_NB_KSIGMA", "GPF_NB_BALL_KNN",
     "PAPER_LR", "photon_field",
     "PAPER_R", "AdamState", "Field", "GridConfig", "Index", "Queries", "gpf_adam_step",
     "gpf_mse_loss_grad", "gpf_radiance_bwd", "gpf_radiance_fwd", "grid_for_bounds",

@@ -28,6 +28,9 @@ GPF_F32 = 0
 GPF_BF16 = 1
 GPF_BF16_MEAN32 = 2
 GPF_BF16_GROUP = 16
+GPF_NB_KSIGMA = 0
+GPF_NB_BALL_KNN = 1
+GPF_MAX_KMIN = 16
 
 c_i32, c_i64, c_f32, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p
 
@@ -43,14 +46,16 @@ class gpf_queries(ctypes.Structure):
 
 
 class gpf_query_params(ctypes.Structure):
-    _fields_ = [("mode", c_i32), ("r_max", c_f32), ("eps", c_f32), ("reserved", c_i32)]
+    _fields_ = [("mode", c_i32), ("r_max", c_f32), ("eps", c_f32), ("neighbourhood", c_i32),
+                ("ball_r", c_f32), ("k_min", c_i32)]
 
 
 class gpf_grid_config(ctypes.Structure):
     _fields_ = [("origin", c_f32 * 3), ("cell_size", c_f32), ("levels", c_i32),
                 ("max_span", c_i32), ("query_level", c_i32), ("dims", c_i32 * 3),
                 ("hash_bits", c_i32), ("channels", c_i32), ("cutoff_sigma", c_f32), ("brute_force", c_i32),
-                ("coop_cells", c_i32), ("field_storage", c_i32), ("max_gaussians", c_i64), ("max_queries", c_i64), ("max_pairs", c_i64)]
+                ("coop_cells", c_i32), ("field_storage", c_i32), ("ball_radius", c_f32),
+                ("max_gaussians", c_i64), ("max_queries", c_i64), ("max_pairs", c_i64)]
 
 
 class gpf_index_stats_t(ctypes.Structure):

@@ -14,7 +14,8 @@ from typing import Optional, Sequence
 import torch
 
 from . import _abi
-from ._abi import GPF_DISK_KDE, GPF_NORMALIZED, GPF_SUM, GPFError, check, load
+from ._abi import (GPF_DISK_KDE, GPF_NB_BALL_KNN, GPF_NB_KSIGMA, GPF_NORMALIZED, GPF_SUM,
+                   GPFError, check, load)
 
 __all__ = [
     "GPF_SUM", "GPF_NORMALIZED", "GPF_DISK_KDE", "GPFError", "GridConfig", "Field", "Queries", "Index",
@@ -207,6 +208,7 @@ class GridConfig:
     brute_force: bool = False
     coop_cells: int = 0        # forward tile shape (0 = library default, 4)
     field_storage: int = 0     # GPF_F32 or GPF_BF16 fields
+    ball_radius: float = 0.0   # > 0: centre entries for GPF_NB_BALL_KNN queries
 
     def c_struct(self) -> _abi.gpf_grid_config:
         return _abi.gpf_grid_config((ctypes.c_float * 3)(*self.origin), float(self.cell_size),
@@ -215,7 +217,7 @@ class GridConfig:
                                     int(self.hash_bits), int(self.channels),
                                     float(self.cutoff_sigma), 1 if self.brute_force else 0,
                                     int(self.coop_cells), int(self.field_storage),
-                                    int(self.max_gaussians),
+                                    float(self.ball_radius), int(self.max_gaussians),
                                     int(self.max_queries),
                                     int(self.max_pairs))
 
@@ -306,15 +308,20 @@ def _event_handle(ev):
     return h
 
 
-def _params(mode, r_max, eps) -> _abi.gpf_query_params:
-    return _abi.gpf_query_params(int(mode), float(r_max), float(eps), 0)
+def _params(mode, r_max, eps, neighbourhood=0, ball_r=0.0, k_min=0) -> _abi.gpf_query_params:
+    return _abi.gpf_query_params(int(mode), float(r_max), float(eps), int(neighbourhood),
+                                 float(ball_r), int(k_min))
 
 
 def gpf_radiance_fwd(index: Index, field: Field, queries: Queries, mode: int = GPF_SUM,
                      r_max: float = math.inf, eps: float = PAPER_EPS,
                      out: Optional[torch.Tensor] = None, z: Optional[torch.Tensor] = None,
-                     want_z: bool = True, stream=None):
-    """Radiance O [C,M] (and Z [M]) at the hit points the index was built for."""
+                     want_z: bool = True, stream=None, neighbourhood: int = 0,
+                     ball_r: float = PAPER_R, k_min: int = 3):
+    """Radiance O [C,M] (and Z [M]) at the hit points the index was built for.
+    neighbourhood GPF_NB_KSIGMA (default): the index's k-sigma ellipsoids;
+    GPF_NB_BALL_KNN: the paper's ball(ball_r) or k_min nearest means (the
+    index needs ball_radius >= ball_r)."""
     m, c = queries.m, field.channels
     dev = queries.x.device
     if out is None:
@@ -324,7 +331,8 @@ def gpf_radiance_fwd(index: Index, field: Field, queries: Queries, mode: int = G
     _need(out, "out", c, m)
     if z is not None:
         _need(z, "z", 0, m)
-    fs, qs, ps = field.c_struct(), queries.c_struct(c), _params(mode, r_max, eps)
+    fs, qs = field.c_struct(), queries.c_struct(c)
+    ps = _params(mode, r_max, eps, neighbourhood, ball_r, k_min)
     check(index._lib.gpf_radiance_fwd(index.handle, ctypes.byref(fs), ctypes.byref(qs),
                                       ctypes.byref(ps), out.data_ptr(), _ptr(z),
                                       _stream(stream)), "gpf_radiance_fwd")
@@ -351,9 +359,10 @@ def gpf_radiance_bwd(index: Index, field: Field, queries: Queries, grad_out: tor
                      out: Optional[torch.Tensor] = None, z: Optional[torch.Tensor] = None,
                      mode: int = GPF_SUM, r_max: float = math.inf, eps: float = PAPER_EPS,
                      grads: Optional[Field] = None, accumulate: bool = False,
-                     stream=None) -> Field:
+                     stream=None, neighbourhood: int = 0) -> Field:
     """Gradients (a Field of tensors) of sum(grad_out * O) w.r.t. mean, quat,
-    logscale and spectrum."""
+    logscale and spectrum (the k-sigma neighbourhood; the library refuses
+    others)."""
     m, c = queries.m, field.channels
     _need(grad_out, "grad_out", c, m)
     if grads is None:       # float32 gradients for either storage
@@ -368,7 +377,7 @@ def gpf_radiance_bwd(index: Index, field: Field, queries: Queries, grad_out: tor
             raise ValueError("GPF_NORMALIZED backward needs the forward's out and z")
         _need(out, "out", c, m)
         _need(z, "z", 0, m)
-    fs, qs, ps = field.c_struct(), queries.c_struct(c), _params(mode, r_max, eps)
+    fs, qs, ps = field.c_struct(), queries.c_struct(c), _params(mode, r_max, eps, neighbourhood)
     gs = _abi.gpf_field_grad(_ptr(grads.mean), _ptr(grads.quat), _ptr(grads.logscale),
                              _ptr(grads.spectrum), 1 if accumulate else 0, 0)
     check(index._lib.gpf_radiance_bwd(index.handle, ctypes.byref(fs), ctypes.byref(qs),

@@ -167,7 +167,16 @@ gpf_status check_params(const gpf_query_params* p) {
     return fail(GPF_ERR_INVALID_ARG, "params.r_max must be >= 0 or +INF");
   if (!(p->eps > 0.0f) || !isfinite(p->eps))
     return fail(GPF_ERR_INVALID_ARG, "params.eps must be finite and > 0");
-  if (p->reserved != 0) return fail(GPF_ERR_INVALID_ARG, "params.reserved must be 0");
+  if (p->neighbourhood != GPF_NB_KSIGMA && p->neighbourhood != GPF_NB_BALL_KNN)
+    return fail(GPF_ERR_INVALID_ARG, "params.neighbourhood = %d is unknown", p->neighbourhood);
+  if (p->neighbourhood == GPF_NB_BALL_KNN) {
+    if (p->mode == GPF_DISK_KDE)
+      return fail(GPF_ERR_INVALID_ARG, "GPF_DISK_KDE gathers a disk, not GPF_NB_BALL_KNN");
+    if (!(p->ball_r >= 0.0f) || !isfinite(p->ball_r))
+      return fail(GPF_ERR_INVALID_ARG, "params.ball_r must be finite and >= 0");
+    if (p->k_min < 0 || p->k_min > GPF_MAX_KMIN)
+      return fail(GPF_ERR_INVALID_ARG, "params.k_min = %d outside 0..%d", p->k_min, GPF_MAX_KMIN);
+  }
   return GPF_OK;
 }
 
@@ -253,6 +262,10 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
       cfg->field_storage != GPF_BF16_MEAN32)
     return fail(GPF_ERR_INVALID_ARG, "field_storage = %d is not a storage form",
                 cfg->field_storage);
+  if (!(cfg->ball_radius >= 0.0f) || !isfinite(cfg->ball_radius))
+    return fail(GPF_ERR_INVALID_ARG, "ball_radius must be finite and >= 0");
+  if (cfg->ball_radius > 0.0f && (double)cfg->ball_radius > (double)cfg->cell_size * (1u << 19))
+    return fail(GPF_ERR_INVALID_ARG, "ball_radius exceeds 2^19 finest cells");
   if (cfg->coop_cells < 0 || cfg->coop_cells > GPF_MAX_COOP_CELLS)
     return fail(GPF_ERR_INVALID_ARG, "coop_cells = %d outside 0..%d", cfg->coop_cells,
                 GPF_MAX_COOP_CELLS);
@@ -277,6 +290,12 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
   d.grid.levels = cfg->levels;
   d.grid.max_span = cfg->max_span;
   d.grid.coop = cfg->coop_cells ? cfg->coop_cells : 4;
+  d.grid.blevel = -1;
+  if (cfg->ball_radius > 0.0f) {
+    int L = 0;
+    while ((double)cfg->cell_size * (double)(1u << L) < (double)cfg->ball_radius && L < 19) ++L;
+    d.grid.blevel = L;
+  }
   d.grid.qlevel = cfg->query_level;
   d.grid.hash_bits = cfg->hash_bits;
   d.grid.n_buckets = 1u << cfg->hash_bits;
@@ -378,12 +397,23 @@ gpf_status gpf_radiance_fwd(const gpf_index* index, const gpf_field* field,
   if ((s = check_queries(index, queries)) != GPF_OK) return s;
   if ((s = check_params(params)) != GPF_OK) return s;
   if ((s = check_same(index, field, queries)) != GPF_OK) return s;
+  if (params->neighbourhood == GPF_NB_BALL_KNN) {
+    if (index->dims.grid.blevel < 0)
+      return fail(GPF_ERR_INVALID_ARG, "the index has no centre entries (ball_radius = 0)");
+    if (params->ball_r > index->cfg.ball_radius)
+      return fail(GPF_ERR_INVALID_ARG, "params.ball_r = %g exceeds the index's ball_radius %g",
+                  params->ball_r, index->cfg.ball_radius);
+  }
   if (queries->m > 0) {
     GPF_CHECK_PTR(out, "out");
     if (z_out && !aligned(z_out, 4)) return fail(GPF_ERR_INVALID_ARG, "z_out is not aligned");
   }
-  cudaError_t e = launch_forward(index->dims, index->buf, *queries, *params, field->n, out, z_out,
-                                 nullptr, index->fwd_ev, reinterpret_cast<cudaStream_t>(stream));
+  cudaError_t e =
+      params->neighbourhood == GPF_NB_BALL_KNN
+          ? launch_hybrid_forward(index->dims, index->buf, *queries, *params, field->n, out, z_out,
+                                  index->fwd_ev, reinterpret_cast<cudaStream_t>(stream))
+          : launch_forward(index->dims, index->buf, *queries, *params, field->n, out, z_out,
+                           nullptr, index->fwd_ev, reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "gpf_radiance_fwd");
   return GPF_OK;
 }
@@ -429,6 +459,8 @@ gpf_status gpf_radiance_bwd(const gpf_index* index, const gpf_field* field,
   if ((s = check_same(index, field, queries)) != GPF_OK) return s;
   if (params->mode == GPF_DISK_KDE)
     return fail(GPF_ERR_INVALID_ARG, "GPF_DISK_KDE (the photon density estimate) has no gradient");
+  if (params->neighbourhood != GPF_NB_KSIGMA)
+    return fail(GPF_ERR_INVALID_ARG, "the backward supports the GPF_NB_KSIGMA neighbourhood only");
   if (!grads) return fail(GPF_ERR_INVALID_ARG, "grads is NULL");
   if (grads->reserved != 0) return fail(GPF_ERR_INVALID_ARG, "grads.reserved must be 0");
   if (field->n > 0) {

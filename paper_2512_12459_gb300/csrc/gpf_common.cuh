@@ -114,6 +114,7 @@ struct Grid {
   uint32_t odx, ody;       // cells per axis on that level
   int obits;               // bits of an order key (cell key and 2 class bits)
   int coop;                // forward: cooperative mode up to this many cells
+  int blevel;              // centre level of the ball query (-1: no centre entries)
 };
 
 // Level-0 cell coordinate of v along one axis: floor((v - o) / c0) in float32,
@@ -139,10 +140,15 @@ struct CellHash {
   uint32_t bucket;
   uint32_t tag;     // entry word bits above id_bits
 };
+// Salt of the centre-cell keys (one entry per Gaussian, in the cell of its
+// mean on the centre level): a key space apart from the box entries'.
+constexpr uint64_t kCentreSalt = 0xd1b54a32d192ed03ull;
+
 __host__ __device__ __forceinline__ CellHash cell_hash(const Grid& g, int L, uint32_t ix,
-                                                       uint32_t iy, uint32_t iz) {
-  uint64_t z = (uint64_t)ix | ((uint64_t)iy << 20) | ((uint64_t)iz << 40) |
-               ((uint64_t)L << 60);
+                                                       uint32_t iy, uint32_t iz,
+                                                       uint64_t salt = 0) {
+  uint64_t z = ((uint64_t)ix | ((uint64_t)iy << 20) | ((uint64_t)iz << 40) |
+                ((uint64_t)L << 60)) ^ salt;
   z += 0x9e3779b97f4a7c15ull;
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;

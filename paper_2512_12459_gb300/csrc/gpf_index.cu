@@ -191,8 +191,9 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
             for (uint32_t ix = lx; ix <= lx + sx; ++ix)
               cnt += occupied(occ, bucket_of(grid, L, ix, iy, iz)) ? 1u : 0u;
       }
-      gcount[g] = cnt;
       live = cnt > 0;
+      if (grid.blevel >= 0) ++cnt;      // the centre entry (kept for every Gaussian)
+      gcount[g] = cnt;
       if (!live) cls = 2;
       small = live && cls == 0;
     }
@@ -248,7 +249,8 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
 // box, in the box's cell order, at the Gaussian's offset (the exclusive scan
 // of the counts). A Gaussian whose cells share a bucket appears there on
 // consecutive entries; the pair loops take only the first.
-__global__ void emit_kernel(Grid grid, int64_t n, int64_t p_max, const uint4* __restrict__ box,
+__global__ void emit_kernel(Grid grid, int64_t n, int64_t p_max, const float* __restrict__ rec,
+                            int rs, const uint4* __restrict__ box,
                             const uint32_t* __restrict__ occ, const uint32_t* __restrict__ goffset,
                             uint32_t* __restrict__ gkey, uint32_t* __restrict__ gval,
                             DeviceHeader* header) {
@@ -256,9 +258,23 @@ __global__ void emit_kernel(Grid grid, int64_t n, int64_t p_max, const uint4* __
   if (g == 0 && (int64_t)header->n_pairs > p_max) atomicExch(&header->overflow, 1u);
   if (g >= n) return;
   const uint4 bw = box[g];
+  int64_t pos = goffset[g];
+  if (grid.blevel >= 0) {
+    // the centre entry: the cell of the mean on the centre level
+    const float* r = rec + g * rs;
+    const int Lb = grid.blevel;
+    const CellHash h = cell_hash(grid, Lb, coord0(r[0], grid.ox, grid.inv_cell0, grid.max0x) >> Lb,
+                                 coord0(r[1], grid.oy, grid.inv_cell0, grid.max0y) >> Lb,
+                                 coord0(r[2], grid.oz, grid.inv_cell0, grid.max0z) >> Lb,
+                                 kCentreSalt);
+    if (pos < p_max) {
+      gkey[pos] = h.bucket;
+      gval[pos] = (uint32_t)g | h.tag;
+    }
+    ++pos;
+  }
   if (bw.x == kNoBox) return;
   const LevelBox b = unpack_box(bw);
-  int64_t pos = goffset[g];
   for (uint32_t iz = b.lz; iz <= b.hz; ++iz)
     for (uint32_t iy = b.ly; iy <= b.hy; ++iy)
       for (uint32_t ix = b.lx; ix <= b.hx; ++ix) {
@@ -352,7 +368,8 @@ cudaError_t launch_build(const IndexDims& d, const IndexBuffers& b, const gpf_fi
   // 5. (bucket, Gaussian) entries: scan, emit, sort, bucket starts
   e = exclusive_scan_u32(b.gcount, b.goffset, f.n, &b.header->n_pairs, b.scan_ws, stream);
   if (e != cudaSuccess) return e;
-  emit_kernel<<<blocks_for(f.n), kThreads, 0, stream>>>(grid, f.n, d.p_max, b.box, b.occ,
+  emit_kernel<<<blocks_for(f.n), kThreads, 0, stream>>>(grid, f.n, d.p_max, b.rec,
+                                                        rec_stride(d.channels), b.box, b.occ,
                                                         b.goffset, b.gkey[0], b.gval[0], b.header);
   note_launches(1);
   e = radix_sort_pairs(b.gkey[0], b.gval[0], b.gkey[1], b.gval[1], d.p_max, &b.header->n_pairs,

@@ -92,6 +92,11 @@ cudaError_t launch_forward(const IndexDims& dims, const IndexBuffers& b, const g
                            const gpf_query_params& p, int64_t n, float* out, float* z,
                            unsigned long long* counts, const KernelEvents& ev,
                            cudaStream_t stream);
+// The GPF_NB_BALL_KNN forward (gpf_hybrid.cu).
+cudaError_t launch_hybrid_forward(const IndexDims& dims, const IndexBuffers& b,
+                                  const gpf_queries& q, const gpf_query_params& p, int64_t n,
+                                  float* out, float* z, const KernelEvents& ev,
+                                  cudaStream_t stream);
 cudaError_t launch_backward(const IndexDims& dims, const IndexBuffers& b, const gpf_field& f,
                             const gpf_queries& q, const gpf_query_params& p,
                             const float* grad_out, const float* out, const float* z,

@@ -49,7 +49,7 @@ def test_version_and_status_strings(lib):
 def _cfg(**kw):
     from paper_2512_12459_gb300 import _abi
     c = _abi.gpf_grid_config((ctypes.c_float * 3)(0, 0, 0), 0.1, 4, 4, 0,
-                             (ctypes.c_int32 * 3)(10, 10, 10), 16, 3, 3.0, 0, 0, 0, 100, 200, 1000)
+                             (ctypes.c_int32 * 3)(10, 10, 10), 16, 3, 3.0, 0, 0, 0, 0.0, 100, 200, 1000)
     for k, v in kw.items():
         if k == "dims":
             c.dims = (ctypes.c_int32 * 3)(*v)
@@ -65,7 +65,8 @@ def _cfg(**kw):
                                  dict(dims=(1024, 1024, 1024)), dict(levels=0), dict(levels=17),
                                  dict(max_span=0), dict(hash_bits=7), dict(hash_bits=29),
                                  dict(query_level=16), dict(query_level=11, dims=(1024, 4, 4)),
-                                 dict(coop_cells=-1), dict(coop_cells=9), dict(field_storage=3)])
+                                 dict(coop_cells=-1), dict(coop_cells=9), dict(field_storage=3),
+                                 dict(ball_radius=-1.0), dict(ball_radius=math.inf)])
 def test_index_create_rejects_bad_configs(lib, bad):
     h = ctypes.c_void_p()
     cfg = _cfg(**bad)

@@ -12,6 +12,7 @@ from scipy.spatial.transform import Rotation
 from scipy.stats import chi2, multivariate_normal, norm
 
 import oracle
+import synth
 from golden_util import load_constants, load_examples
 
 
@@ -471,3 +472,67 @@ def test_disk_kde_single_photon_gate_and_albedo():
     a = np.pi * 0.04
     np.testing.assert_allclose(out[:, 0], [0.5 * 2 / a, 0.25 * 4 / a], rtol=1e-14)
     assert np.all(out[:, 1:] == 0)                   # gate, invalid, out of reach
+
+
+# ---- the hybrid neighbourhood (Sec. 4.2, Neighborhood Search; Algorithm S3)
+
+def _line_field(dists, phis, s=0.02):
+    """Isotropic Gaussians on the x axis at the given distances from the origin."""
+    n = len(dists)
+    mean = np.zeros((3, n))
+    mean[0] = dists
+    quat = np.zeros((4, n))
+    quat[0] = 1.0
+    return mean, quat, np.full((3, n), np.log(s)), np.array([phis], float)
+
+
+def _w_line(d, s=0.02, r=0.02):
+    """exp(-d^2 / (2 s^2)) psi(d) for a Gaussian at distance d on the axis."""
+    psi = 1.0 if d <= r else math.exp(-3.0 * ((d - r) / r) ** 2)
+    return math.exp(-0.5 * (d / s) ** 2) * psi
+
+
+@pytest.mark.parametrize("ball_r,k_min,members", [
+    (0.02, 3, [0, 1, 2]),        # one mean in the ball, fewer than 3: the 3 nearest
+    (0.06, 3, [0, 1, 2]),        # exactly 3 in the ball: the ball
+    (0.08, 3, [0, 1, 2, 3]),     # 4 in the ball: the ball
+    (0.02, 0, [0]),              # ball only (Table 3, w_radius)
+    (0.0, 2, [0, 1]),            # kNN only (Table 3, w_knn)
+    (0.005, 0, []),              # empty ball, no kNN: nothing
+])
+def test_hybrid_neighbourhood_selects_the_paper_sets(ball_r, k_min, members):
+    dists = [0.01, 0.03, 0.05, 0.07, 0.2]
+    phis = [1.0, 2.0, 4.0, 8.0, 16.0]
+    mean, quat, lsc, spec = _line_field(dists, phis)
+    x = np.zeros((3, 1))
+    nrm = np.array([[0.0], [0.0], [1.0]])
+    for mode in (oracle.GPF_SUM, oracle.GPF_NORMALIZED):
+        out = oracle.hybrid_fwd(mean, quat, lsc, spec, x, nrm, nrm, mode=mode, r_max=0.02,
+                                ball_r=ball_r, k_min=k_min)
+        L = sum(_w_line(dists[i]) * phis[i] for i in members)
+        Z = sum(_w_line(dists[i]) for i in members)
+        want = L if mode == oracle.GPF_SUM else L / max(Z, 1e-6)
+        np.testing.assert_allclose(out["out"][0, 0], want, rtol=1e-13, atol=1e-300)
+        assert out["n_nb"][0] == len(members)
+
+
+def test_hybrid_knn_ties_go_to_the_smaller_index():
+    # Gaussians 1 and 2 at the same distance: with k_min = 2 the pair {0, 1}
+    mean, quat, lsc, spec = _line_field([0.01, 0.05, -0.05], [1.0, 2.0, 4.0])
+    x = np.zeros((3, 1))
+    nrm = np.array([[0.0], [0.0], [1.0]])
+    out = oracle.hybrid_fwd(mean, quat, lsc, spec, x, nrm, nrm, mode=oracle.GPF_SUM,
+                            r_max=0.02, ball_r=0.02, k_min=2)
+    want = _w_line(0.01) * 1.0 + _w_line(0.05) * 2.0
+    np.testing.assert_allclose(out["out"][0, 0], want, rtol=1e-13)
+    assert out["knn"][0] and out["near"][0]          # a tie is flagged as sensitive
+
+
+def test_hybrid_with_a_ball_holding_everything_is_the_untruncated_sum():
+    fnp, qnp = synth.config1_random(seed=33, n=60, m=40)
+    a = oracle.hybrid_fwd(fnp.mean, fnp.quat, fnp.logscale, fnp.spectrum, qnp.x, qnp.n, qnp.wo,
+                          mode=oracle.GPF_NORMALIZED, r_max=0.05, ball_r=10.0, k_min=3)
+    b = oracle.radiance_fwd(fnp.mean, fnp.quat, fnp.logscale, fnp.spectrum, qnp.x, qnp.n,
+                            qnp.wo, mode=oracle.GPF_NORMALIZED, r_max=0.05,
+                            cutoff_sigma=math.inf)
+    np.testing.assert_allclose(a["out"], b["out"], rtol=1e-12, atol=1e-300)

@@ -74,7 +74,7 @@ def test_bf16_fields_are_validated():
     fake = 1 << 40
     cfg = _abi.gpf_grid_config((ctypes.c_float * 3)(0, 0, 0), 0.1, 4, 4, 0,
                                (ctypes.c_int32 * 3)(10, 10, 10), 16, 3, 3.0, 0, 0,
-                               _abi.GPF_BF16, 100, 200, 1000)
+                               _abi.GPF_BF16, 0.0, 100, 200, 1000)
     h = ctypes.c_void_p()
     assert lib.gpf_index_create(ctypes.byref(cfg), ctypes.byref(h)) == 0
     sz = ctypes.c_size_t()
