@@ -541,6 +541,42 @@ def run_scaling(args):
                      "build_fwd_ms": fwd_ms, "included_pairs_per_query": pairs["included"] / n_active})
         del idx, field, state, grads, target
         torch.cuda.empty_cache()
+    # the paper's own query (ball r = 0.02 or the k_min nearest, normalised):
+    # build + forward against the field size (Table S1) and against k_min at
+    # 100K Gaussians (Table S2)
+    hyb_rows, k_rows = [], []
+
+    def hybrid_ms(n, k_min):
+        pos, flux = synth.caustic_photons(n, seed=0)
+        field = gpf.Field.from_numpy(synth.field_from_photons(pos, flux, seed=0))
+        idx = make_index(field, queries, query_cell=CELL, ball_radius=R_MAX)
+        out = torch.empty((3, queries.m), device="cuda")
+        z = torch.empty((queries.m,), device="cuda")
+        times = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            idx.build(field, queries)
+            gpf.gpf_radiance_fwd(idx, field, queries, gpf.GPF_NORMALIZED, r_max=R_MAX, out=out,
+                                 z=z, neighbourhood=gpf.GPF_NB_BALL_KNN, ball_r=R_MAX,
+                                 k_min=k_min)
+            e1.record()
+            e1.synchronize()
+            if i >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+        del idx, field
+        torch.cuda.empty_cache()
+        return float(np.mean(times))
+
+    for n in (10_000, 50_000, 100_000, 200_000):
+        ms = hybrid_ms(n, 3)
+        hyb_rows.append({"gaussians": n, "k_min": 3, "build_fwd_ms": ms,
+                         "queries_per_s": n_active / ms * 1e3})
+    for k in (1, 3, 5, 10):
+        ms = hybrid_ms(100_000, k)
+        k_rows.append({"gaussians": 100_000, "k_min": k, "build_fwd_ms": ms,
+                       "queries_per_s": n_active / ms * 1e3})
     line = {"metric": "training step time vs number of Gaussians (Table S1 replay)",
             "value": rows[-1]["queries_per_s"], "unit": "queries/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
@@ -548,7 +584,9 @@ def run_scaling(args):
             "config": {"workload": f"caustic scene, {VIEW}x{VIEW} view, r={R_MAX}",
                        "active_hit_points": n_active, "l2": "flushed between steps"},
             "rows": rows,
-            "paper_table_s1_s": {"10000": 7.230, "50000": 12.70, "100000": 16.37, "200000": 24.35}}
+            "hybrid_query_rows": hyb_rows, "hybrid_k_rows": k_rows,
+            "paper_table_s1_s": {"10000": 7.230, "50000": 12.70, "100000": 16.37, "200000": 24.35},
+            "paper_table_s2_s": {"1": 16.21, "3": 16.37, "5": 16.48, "10": 16.34}}
     print(json.dumps(line), flush=True)
 
 
