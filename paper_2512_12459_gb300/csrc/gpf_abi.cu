@@ -324,7 +324,7 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
     const uint64_t ocells = (uint64_t)d.grid.odx * d.grid.ody * ((d.grid.max0z >> d.grid.oshift) + 1);
     int ob = 1;
     while ((1ull << ob) < ocells) ++ob;
-    d.grid.obits = ob + 2;
+    d.grid.obits = ob + kOrderSizeBits + 2;
   }
   d.channels = cfg->channels;
   d.cutoff = cfg->cutoff_sigma;

@@ -337,7 +337,8 @@ __device__ void bwd_lane_gaussian(const BwdArgs& a, int64_t pos, int64_t gi) {
     dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
 }
 
-// Grid path. The Gaussians come in mean-cell order, the small ones first:
+// Grid path. The Gaussians come in (class, size, mean-cell) order, the small
+// ones first and the large ones largest first:
 // the first ceil(n_small / 32) warps give each lane one small Gaussian; every
 // later warp runs one large Gaussian over the hit points of every
 // query-level cell its k-sigma bounds overlap. Gaussians whose level box

@@ -61,6 +61,10 @@ __device__ __forceinline__ uint16_t f32_to_bf16(float x) {
   return (uint16_t)(u >> 16);
 }
 
+// Bits of the backward's order key that rank the large Gaussians by size
+// (largest first), between the class and the coarse cell of the mean.
+constexpr int kOrderSizeBits = 3;
+
 constexpr int kLevelBits = 4;  // levels < 2^kLevelBits = kMaxLevels
 constexpr uint32_t kLevelMask = (1u << kLevelBits) - 1u;
 static_assert(kMaxLevels <= (1 << kLevelBits), "a level must fit in kLevelBits");

@@ -153,22 +153,32 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
     for (int c = 0; c < f.channels; ++c) r[13 + c] = spec[(int64_t)c * n + g];
     for (int c = 13 + f.channels; c < rs; ++c) r[c] = 0.0f;
     // the order the backward walks Gaussians in: class (0 = bounds within
-    // 2 x 2 x 2 query-level cells, 1 = larger, 2 = no hit point in reach),
-    // then the cell of the mean on a coarse level
+    // 2 x 2 x 2 query-level cells, 1 = larger, 2 = no hit point in reach);
+    // the large ones largest first (log4 of their bounds' volume in query
+    // cells), so that none of them starts last; then the cell of the mean on
+    // a coarse level
     const int K = grid.qlevel, os = grid.oshift;
     const uint32_t mkey =
         ((coord0(mu[2], grid.oz, grid.inv_cell0, grid.max0z) >> os) * grid.ody +
          (coord0(mu[1], grid.oy, grid.inv_cell0, grid.max0y) >> os)) * grid.odx +
         (coord0(mu[0], grid.ox, grid.inv_cell0, grid.max0x) >> os);
     const int cls_shift = grid.obits - 2;
-    uint32_t cls = 1;
+    const int size_shift = cls_shift - kOrderSizeBits;
+    uint32_t cls = 1, size_rank = 0;
     oval[g] = (uint32_t)g;
     if (!brute) {
       uint32_t lo[3], hi[3];
       gaussian_cells0(grid, fr, mu, cutoff, lo, hi);
       if ((hi[0] >> K) - (lo[0] >> K) <= 1 && (hi[1] >> K) - (lo[1] >> K) <= 1 &&
-          (hi[2] >> K) - (lo[2] >> K) <= 1)
+          (hi[2] >> K) - (lo[2] >> K) <= 1) {
         cls = 0;
+      } else {
+        const uint64_t vq = (uint64_t)((hi[0] >> K) - (lo[0] >> K) + 1) *
+                            ((hi[1] >> K) - (lo[1] >> K) + 1) * ((hi[2] >> K) - (lo[2] >> K) + 1);
+        const uint32_t lg = 63u - (uint32_t)__clzll((long long)vq);
+        const uint32_t top = (1u << kOrderSizeBits) - 1u;
+        size_rank = top - min(lg >> 1, top);
+      }
       int L = 0;
       for (; L < grid.levels - 1; ++L) {
         const uint32_t sx = (hi[0] >> L) - (lo[0] >> L), sy = (hi[1] >> L) - (lo[1] >> L),
@@ -197,7 +207,7 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
       if (!live) cls = 2;
       small = live && cls == 0;
     }
-    okey[g] = mkey | (cls << cls_shift);
+    okey[g] = mkey | (size_rank << size_shift) | (cls << cls_shift);
   }
   const uint32_t m = __reduce_or_sync(kFullMask, level_bit);
   if ((threadIdx.x & 31) == 0 && m) atomicOr(&header->level_mask, m);
