@@ -104,6 +104,8 @@ size_t layout(const gpf_index* ix, char* base, IndexBuffers* b) {
   t.qstart = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * ncp));
   t.qrec = reinterpret_cast<float*>(take(sizeof(float) * M * qrec_stride(d.channels)));
   t.gacc = reinterpret_cast<float*>(take(sizeof(float) * N * gacc_stride(d.channels)));
+  t.bpart = reinterpret_cast<float*>(take(sizeof(float) * std::min<int64_t>(N, kSplitMax) *
+                                          kSplitWays * gacc_stride(d.channels)));
   for (int k = 0; k < 2; ++k) {
     t.gkey[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (P > 0 ? P : 1)));
     t.gval[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (P > 0 ? P : 1)));

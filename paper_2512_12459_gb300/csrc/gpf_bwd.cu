@@ -44,6 +44,7 @@ struct BwdArgs {
   int64_t m;
   float* qrec;
   float* gacc;            // [N * NS] per-Gaussian sums, by position in the order
+  float* bpart;           // [kSplitMax * kSplitWays * NS] split Gaussians' partials
   const float* rec;
   const uint4* box;
   const uint32_t* order;  // Gaussian ids in mean-cell order
@@ -338,22 +339,26 @@ __device__ void bwd_lane_gaussian(const BwdArgs& a, int64_t pos, int64_t gi) {
 }
 
 // Grid path. The Gaussians come in (class, size, mean-cell) order, the small
-// ones first and the large ones largest first:
+// ones first and the large ones largest first; the largest (up to kSplitMax)
+// are split into kSplitWays work units, each over every kSplitWays-th block
+// of 32 rows, whose partial sums the epilogue adds in part order:
 // the first ceil(n_small / 32) warps give each lane one small Gaussian; every
 // later warp runs one large Gaussian over the hit points of every
 // query-level cell its k-sigma bounds overlap. Gaussians whose level box
 // holds no hit point come last and are skipped (zero gradient).
 template <int C, bool PSI>
-__global__ void __launch_bounds__(kBwdThreads)
+__global__ void __launch_bounds__(kBwdThreads, 7)
 bwd_grid_kernel(BwdArgs a) {
   constexpr int QS = qrec_stride(C);
   const int lane = threadIdx.x & 31;
   if (a.header->overflow) return;
   const int64_t n_small = a.header->n_small, n_live = a.header->n_live;
   const int64_t small_warps = (n_small + kWarp - 1) / kWarp;
-  const int64_t units = small_warps + (n_live - n_small);
-  // persistent: every warp takes the next work unit (32 small Gaussians, or
-  // one large one) until none is left
+  const int64_t n_split = min((int64_t)a.header->n_huge, kSplitMax);
+  const int64_t units = small_warps + n_split * kSplitWays + (n_live - n_small - n_split);
+  // persistent: every warp takes the next work unit (32 small Gaussians, one
+  // of the kSplitWays parts of a huge Gaussian, or one large Gaussian) until
+  // none is left
   for (;;) {
   unsigned long long w_u = 0;
   if (lane == 0) w_u = atomicAdd(a.next_work, 1ull);
@@ -365,7 +370,11 @@ bwd_grid_kernel(BwdArgs a) {
     __syncwarp();
     continue;
   }
-  const int64_t j = n_small + (w - small_warps);
+  const int64_t u = w - small_warps;
+  const bool split = u < n_split * kSplitWays;
+  const int64_t j = split ? n_small + u / kSplitWays : n_small + n_split + (u - n_split * kSplitWays);
+  const int part = split ? (int)(u % kSplitWays) : 0;       // this unit's share of the rows
+  const int row_step = split ? kSplitWays * kWarp : kWarp;
   const Grid& Gd = a.grid;
   const int64_t gi = a.order[j];
   GaussianRegs G;
@@ -389,7 +398,7 @@ bwd_grid_kernel(BwdArgs a) {
   const float rcx = Gd.ox + (lx + 0.5f * nx) * cellK, rhx = 0.5f * nx * cellK * 1.001f;
   Acc<C> acc;
   acc.zero();
-  for (int rb = 0; rb < rows; rb += kWarp) {
+  for (int rb = part * kWarp; rb < rows; rb += row_step) {
     const int ri = rb + lane;
     uint32_t qs = 0, cnt = 0;
     if (ri < rows) {
@@ -436,7 +445,9 @@ bwd_grid_kernel(BwdArgs a) {
   acc.to_array(v);
   int slot;
   const float sum = reduce_scatter<Acc<C>::NS>(v, lane, &slot);
-  if (Acc<C>::NS == 32 || (lane & 1) == 0) a.gacc[j * Acc<C>::NS + slot] = sum;
+  float* dst = split ? a.bpart + ((j - n_small) * kSplitWays + part) * Acc<C>::NS
+                     : a.gacc + j * Acc<C>::NS;
+  if (Acc<C>::NS == 32 || (lane & 1) == 0) dst[slot] = sum;
   (void)fr;
   }  // work loop
 }
@@ -474,7 +485,21 @@ __global__ void bwd_epilogue_kernel(BwdArgs a, int brute) {
   if (j >= count) return;
   const int64_t gi = brute ? j : a.order[j];
   Acc<C> acc;
-  acc.from_array(a.gacc + j * Acc<C>::NS);
+  const int64_t n_small = brute ? 0 : (int64_t)a.header->n_small;
+  const int64_t n_split = brute ? 0 : min((int64_t)a.header->n_huge, kSplitMax);
+  if (j >= n_small && j < n_small + n_split) {
+    // a split Gaussian: its parts' sums, in part order
+    float s[Acc<C>::NS];
+    const float* p = a.bpart + (j - n_small) * kSplitWays * Acc<C>::NS;
+#pragma unroll
+    for (int i = 0; i < Acc<C>::NS; ++i) s[i] = p[i];
+    for (int b = 1; b < kSplitWays; ++b)
+#pragma unroll
+      for (int i = 0; i < Acc<C>::NS; ++i) s[i] += p[b * Acc<C>::NS + i];
+    acc.from_array(s);
+  } else {
+    acc.from_array(a.gacc + j * Acc<C>::NS);
+  }
   const Frame fr = gaussian_frame(a.quat, a.logscale, a.n, gi);
   bwd_epilogue<C>(a, gi, fr, acc);
 }
@@ -541,6 +566,7 @@ cudaError_t launch_backward(const IndexDims& d, const IndexBuffers& b, const gpf
   a.m = q.m;
   a.qrec = b.qrec;
   a.gacc = b.gacc;
+  a.bpart = b.bpart;
   a.rec = b.rec;
   a.box = b.box;
   a.order = b.oval[b.osorted];

@@ -28,10 +28,12 @@ struct DeviceHeader {
   uint32_t level_mask;   // bit L set when some Gaussian lives on level L
   uint32_t n_live;       // Gaussians whose level box holds a hit point
   uint32_t n_small;      // live Gaussians spanning <= 2 query-level cells per axis
+  uint32_t n_huge;       // live large Gaussians of the top size rank (split in the backward)
+  uint32_t reserved0;
   // work counters of the persistent pair loops (reset before each launch)
   unsigned long long next_tile;       // forward: next tile of 32 hit points
   unsigned long long next_work;       // backward: next work item
-  uint32_t pad[54];
+  uint32_t pad[52];
 };
 static_assert(sizeof(DeviceHeader) == 256, "header is one 256-byte block");
 
@@ -64,6 +66,11 @@ __device__ __forceinline__ uint16_t f32_to_bf16(float x) {
 // Bits of the backward's order key that rank the large Gaussians by size
 // (largest first), between the class and the coarse cell of the mean.
 constexpr int kOrderSizeBits = 3;
+// The backward splits each Gaussian of the top size rank (bounds over at
+// least 2^14 query-level cells), up to kSplitMax of them, into kSplitWays
+// work units over its rows of cells, summing their partial sums in order.
+constexpr int kSplitWays = 16;
+constexpr int64_t kSplitMax = 16384;
 
 constexpr int kLevelBits = 4;  // levels < 2^kLevelBits = kMaxLevels
 constexpr uint32_t kLevelMask = (1u << kLevelBits) - 1u;

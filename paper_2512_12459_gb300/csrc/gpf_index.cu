@@ -132,7 +132,7 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = f.n;
   uint32_t level_bit = 0;
-  bool live = false, small = false;
+  bool live = false, small = false, huge = false;
   if (g < n) {
     const float* mean = static_cast<const float*>(f.mean);
     const float* spec = static_cast<const float*>(f.spectrum);
@@ -206,6 +206,7 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
       gcount[g] = cnt;
       if (!live) cls = 2;
       small = live && cls == 0;
+      huge = live && cls == 1 && size_rank == 0;
     }
     okey[g] = mkey | (size_rank << size_shift) | (cls << cls_shift);
   }
@@ -215,6 +216,8 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
   const uint32_t bsmall = __ballot_sync(kFullMask, small);
   if ((threadIdx.x & 31) == 0 && blive) atomicAdd(&header->n_live, __popc(blive));
   if ((threadIdx.x & 31) == 0 && bsmall) atomicAdd(&header->n_small, __popc(bsmall));
+  const uint32_t bhuge = __ballot_sync(kFullMask, huge);
+  if ((threadIdx.x & 31) == 0 && bhuge) atomicAdd(&header->n_huge, __popc(bhuge));
 }
 
 __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,

@@ -49,6 +49,8 @@ struct IndexBuffers {
   uint32_t* qstart;     // [n_keys + 2] per-cell start of the sorted hit points
   float* qrec;          // [M_max * qrec_stride] packed hit points of the backward
   float* gacc;          // [N_max * gacc_stride] per-Gaussian sums of the backward
+  float* bpart;         // [kSplitMax * kSplitWays * gacc_stride] partial sums of
+                        // the backward's split Gaussians
   uint32_t* occ;        // [n_buckets / 32] occupancy bits of (level, cell) buckets
   uint32_t* gkey[2];    // [P_max] (bucket, Gaussian) entries, sort ping-pong
   uint32_t* gval[2];
