@@ -137,20 +137,21 @@ def measured_peaks():
 
 # DRAM bytes (read + write) per launch of the pair-loop kernels on this
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
-# second warm-up step of `python bench.py --steps 3 --warmup 3
-# --no-cpu-baseline`), with the SHA-256 of the sources the kernel was built
-# from; reported only while those sources are unchanged.
+# third warm-up step of `python bench.py --steps 3 --warmup 3
+# --no-cpu-baseline --grid 0.0308,3,8`, the grid the autotuner chooses for
+# this scene), with the SHA-256 of the sources the kernel was built from;
+# reported only while those sources are unchanged.
 PROFILED_TRAFFIC = {
-    "fwd_kernel": {"bytes": 432348672 + 11620352, "sources": {
+    "fwd_kernel": {"bytes": 388961536 + 11347456, "sources": {
         "paper_2512_12459_gb300/csrc/gpf_fwd.cu":
-            "e4c41578d5b68051aa52e9f10cf1d448251403cd9bc04d416ac704d1ad3cf07f",
+            "b61c01608854304c5660cd1748fb95b95a94d40a2a70ad6fa3875151127d0675",
         "paper_2512_12459_gb300/csrc/gpf_common.cuh":
-            "3ee18429921eb65442208a104407f4d68a54b6b6d21ff58ea35d3e204a0e3593"}},
-    "bwd_grid_kernel": {"bytes": 175708928 + 52078848, "sources": {
+            "db9d6658e9a544dec5572a1f3090988aca9bfa099bf711f6eefc7c1975c09761"}},
+    "bwd_grid_kernel": {"bytes": 190804736 + 50388736, "sources": {
         "paper_2512_12459_gb300/csrc/gpf_bwd.cu":
-            "e1fb6e0a9d81d03f900c23325e663f7076bf84d93600dfdb0756aee71164ed0f",
+            "f1727f45a1a88d011e66b34fce215841f7a97d240f7daf214fed690a6ff00919",
         "paper_2512_12459_gb300/csrc/gpf_common.cuh":
-            "3ee18429921eb65442208a104407f4d68a54b6b6d21ff58ea35d3e204a0e3593"}},
+            "db9d6658e9a544dec5572a1f3090988aca9bfa099bf711f6eefc7c1975c09761"}},
 }
 
 
@@ -611,6 +612,10 @@ def main():
     ap.add_argument("--batched-photons", type=int, default=2_000_000)
     ap.add_argument("--bf16-photons", type=int, default=4_000_000)
     ap.add_argument("--bf16-views", type=int, default=16)
+    ap.add_argument("--grid", default=None, metavar="QUERY_CELL,MAX_SPAN,COOP",
+                    help="single workload: this grid instead of the autotuned one (the "
+                         "profiling commands pin the grid the autotuner chose, so that every "
+                         "run captures the same launches)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if (args.photons, args.view) != (N_PHOTONS, VIEW):
@@ -666,8 +671,13 @@ def main():
     # grid geometry and forward tile shape chosen by timing candidates on this
     # scene (outside the timed region); headroom for the pairs to grow as
     # Adam moves the Gaussians
-    tuned, _ = autotune(field, queries, cutoff_sigma=CUTOFF, r_max=R_MAX, repeats=2)
-    idx = make_index(field, queries, grid=tuned, headroom=1.25)
+    if args.grid:
+        qc, span, coop = args.grid.split(",")
+        idx = make_index(field, queries, cutoff_sigma=CUTOFF, headroom=1.25,
+                         query_cell=float(qc), max_span=int(span), coop_cells=int(coop))
+    else:
+        tuned, _ = autotune(field, queries, cutoff_sigma=CUTOFF, r_max=R_MAX, repeats=2)
+        idx = make_index(field, queries, grid=tuned, headroom=1.25)
     state = gpf.AdamState.zeros_like(field)
     grads = gpf.Field(*(torch.empty_like(t) for t in field.tensors()))
     out = torch.empty((3, queries.m), device="cuda")
@@ -818,7 +828,8 @@ def main():
                        "grid": {"query_cell": idx.grid.cell_size * (1 << idx.grid.query_level),
                                 "levels": idx.grid.levels, "finest_cell": idx.grid.cell_size,
                                 "max_span": idx.grid.max_span,
-                                "coop_cells": idx.grid.coop_cells, "autotuned": True}},
+                                "coop_cells": idx.grid.coop_cells,
+                                "autotuned": not args.grid}},
             "fwd_queries_per_s": n_active / (ms["fwd"] / 1e3),
             "fwd_bwd_queries_per_s": n_active / ((ms["fwd"] + ms["bwd"] + ms["loss"]) / 1e3),
             "ms_breakdown": {k: v for k, v in ms.items() if k != "step"},

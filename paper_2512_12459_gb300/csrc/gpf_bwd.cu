@@ -184,10 +184,12 @@ __device__ __forceinline__ void bwd_pair_q(const GaussianRegs& G, const float (&
   if (PSI) {
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     if (d2 > a.r2) {
-      const float dist = sqrtf(d2);
+      // |d| and 1/|d| from one reciprocal square root (d2 > r^2 > 0)
+      const float inv_d = rsqrtf(d2);
+      const float dist = d2 * inv_d;
       const float t = (dist - a.r) * a.inv_rr;
       e = fmaf(-3.0f * t, t, e);
-      pcoef = 6.0f * t * a.inv_rr / dist;
+      pcoef = 6.0f * t * a.inv_rr * inv_d;
     }
   }
   const float w = ex2_approx(e * kLog2e);

@@ -139,19 +139,21 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
     const float mu[3] = {mean[g], mean[n + g], mean[2 * n + g]};
     const Frame fr = gaussian_frame(static_cast<const float*>(f.quat),
                                     static_cast<const float*>(f.logscale), n, g);
-    float* r = rec + g * rs;
+    // the record's first 16 floats in registers, stored as four float4 once
+    // the level is known (rs is a multiple of 4, the record 16-byte aligned)
+    float rv[16];
     const float smax = fmaxf(fr.s[0], fmaxf(fr.s[1], fr.s[2]));
-    r[0] = mu[0]; r[1] = mu[1]; r[2] = mu[2];
+    rv[0] = mu[0]; rv[1] = mu[1]; rv[2] = mu[2];
     // bounding sphere of the k-sigma ellipsoid, widened by 1e-4 for rounding
-    r[3] = isinf(cutoff) ? INFINITY : cutoff * smax * 1.0001f;
+    rv[3] = isinf(cutoff) ? INFINITY : cutoff * smax * 1.0001f;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const float inv = 1.0f / fr.s[j];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) r[4 + 3 * j + k] = fr.R[k][j] * inv;
+      for (int k = 0; k < 3; ++k) rv[4 + 3 * j + k] = fr.R[k][j] * inv;
     }
-    for (int c = 0; c < f.channels; ++c) r[13 + c] = spec[(int64_t)c * n + g];
-    for (int c = 13 + f.channels; c < rs; ++c) r[c] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rv[13 + c] = c < f.channels ? spec[(int64_t)c * n + g] : 0.0f;
     // the order the backward walks Gaussians in: class (0 = bounds within
     // 2 x 2 x 2 query-level cells, 1 = larger, 2 = no hit point in reach);
     // the large ones largest first (log4 of their bounds' volume in query
@@ -194,7 +196,7 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
         atomicExch(&header->overflow, 1u);
       } else {
         box[g] = make_uint4(lx | ((uint32_t)L << 20), ly, lz, sx | (sy << 8) | (sz << 16));
-        r[3] = rec_radius_with_level(r[3], (uint32_t)L);
+        rv[3] = rec_radius_with_level(rv[3], (uint32_t)L);
         level_bit = 1u << L;
         for (uint32_t iz = lz; iz <= lz + sz; ++iz)
           for (uint32_t iy = ly; iy <= ly + sy; ++iy)
@@ -209,6 +211,12 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
       huge = live && cls == 1 && size_rank == 0;
     }
     okey[g] = mkey | (size_rank << size_shift) | (cls << cls_shift);
+    float4* r4 = reinterpret_cast<float4*>(rec + g * rs);
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      r4[v] = make_float4(rv[4 * v], rv[4 * v + 1], rv[4 * v + 2], rv[4 * v + 3]);
+    for (int c = 16; c < rs; ++c)
+      rec[g * rs + c] = c - 13 < f.channels ? spec[(int64_t)(c - 13) * n + g] : 0.0f;
   }
   const uint32_t m = __reduce_or_sync(kFullMask, level_bit);
   if ((threadIdx.x & 31) == 0 && m) atomicOr(&header->level_mask, m);
