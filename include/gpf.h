@@ -45,9 +45,11 @@
  *   - Every call returns a gpf_status. Arguments are validated on the host
  *     before anything is enqueued; on an error nothing is enqueued and
  *     gpf_last_error() describes it. No call aborts or throws.
- *   - Problems found on the device (a full pair buffer) set a flag in the
- *     index workspace. Kernels that see it leave their outputs untouched;
- *     gpf_index_stats() reads it back and reports GPF_ERR_CAPACITY.
+ *   - Problems found on the device (a full pair buffer; a wait of the index
+ *     build's single-pass sort that ran out of its poll limit) set a flag in
+ *     the index workspace. Kernels that see it leave their outputs untouched;
+ *     gpf_index_stats() reads it back and reports GPF_ERR_CAPACITY or
+ *     GPF_ERR_TIMEOUT.
  */
 #ifndef GPF_H
 #define GPF_H
@@ -69,7 +71,8 @@ typedef enum gpf_status {
   GPF_ERR_WORKSPACE_TOO_SMALL = 3,/* workspace smaller than the reported size  */
   GPF_ERR_CAPACITY = 4,           /* the (cell, Gaussian) pair buffer was full */
   GPF_ERR_NOT_BUILT = 5,          /* index used before gpf_build_index         */
-  GPF_ERR_MISMATCH = 6            /* field/queries differ from those indexed   */
+  GPF_ERR_MISMATCH = 6,           /* field/queries differ from those indexed   */
+  GPF_ERR_TIMEOUT = 7             /* a bounded device-side wait gave up        */
 } gpf_status;
 
 typedef enum gpf_mode { GPF_SUM = 0, GPF_NORMALIZED = 1, GPF_DISK_KDE = 2 } gpf_mode;
@@ -190,9 +193,9 @@ typedef struct gpf_grid_config {
                             of its mean on the first level whose cells are
                             >= ball_radius, for GPF_NB_BALL_KNN queries with
                             a ball of at most this radius; 0: none           */
-  int64_t max_gaussians; /* capacity N_max                                   */
-  int64_t max_queries;   /* capacity M_max                                   */
-  int64_t max_pairs;     /* capacity of (cell, Gaussian) entries             */
+  int64_t max_gaussians; /* capacity N_max (< 2^30)                          */
+  int64_t max_queries;   /* capacity M_max (< 2^30)                          */
+  int64_t max_pairs;     /* capacity of (cell, Gaussian) entries (< 2^30)    */
 } gpf_grid_config;
 
 /* Opaque host-side handle. It holds sizes and pointers into the workspace;
@@ -457,6 +460,47 @@ gpf_status gpf_adam_step(const gpf_field *params, const gpf_field_grad *grads,
  * Errors: GPF_ERR_INVALID_ARG, GPF_ERR_CUDA.
  */
 gpf_status gpf_field_quantize(const gpf_field *src, const gpf_field *dst, gpf_stream stream);
+
+/*
+ * gpf_sort_pairs_workspace_size / gpf_sort_pairs / gpf_sort_pairs_check -
+ * the index build's stable LSD radix sort of (uint32 key, uint32 value)
+ * pairs by key bits [0, bits), 8 bits per pass (a step of the cell-list
+ * build, Sec. 4.2), exported for tests and reuse.
+ *   keys, vals          device [n]: the pairs (input, and scratch)
+ *   keys_alt, vals_alt  device [n]: the other half of the ping-pong
+ *   n                   0 <= n < 2^30
+ *   bits                0..32 (0: nothing to do)
+ *   workspace           device, 256-byte aligned, at least
+ *                       gpf_sort_pairs_workspace_size(n) bytes, owned by the
+ *                       caller and kept until gpf_sort_pairs_check; its
+ *                       first 4 bytes receive the stall flag
+ *   *result_in_alt      (host, written) 1 if the sorted pairs end in
+ *                       keys_alt / vals_alt (an odd number of passes), 0 if
+ *                       in keys / vals
+ * Equal keys keep their input order. Each pass is one single-pass kernel
+ * whose tiles take their offsets from the earlier tiles (decoupled
+ * look-back, every wait bounded). Asynchronous on stream.
+ * gpf_sort_pairs_check synchronises the stream and returns GPF_ERR_TIMEOUT
+ * if a wait gave up (the output is then invalid), else GPF_OK.
+ * Errors: GPF_ERR_INVALID_ARG, GPF_ERR_WORKSPACE_TOO_SMALL, GPF_ERR_CUDA.
+ */
+gpf_status gpf_sort_pairs_workspace_size(int64_t n, size_t *bytes);
+gpf_status gpf_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
+                          uint32_t *vals_alt, int64_t n, int32_t bits, void *workspace,
+                          size_t workspace_bytes, int32_t *result_in_alt, gpf_stream stream);
+gpf_status gpf_sort_pairs_check(const void *workspace, gpf_stream stream);
+
+/*
+ * gpf_test_sort_wait_timeout - failure-detection test of the sort's bounded
+ * wait, with no fault: one block of a single-pass sort kernel takes the
+ * second of two tiles whose first tile no block processes, so its walk back
+ * polls status words that nothing writes, spin_limit times (1 .. 2^22),
+ * gives up, sets the stall flag and finishes. Synchronous (allocates and
+ * frees its own device buffer). Returns GPF_ERR_TIMEOUT when the wait gave
+ * up and said so (the expected outcome), GPF_OK if it did not.
+ * Errors: GPF_ERR_INVALID_ARG (spin_limit outside 1 .. 2^22), GPF_ERR_CUDA.
+ */
+gpf_status gpf_test_sort_wait_timeout(uint32_t spin_limit, gpf_stream stream);
 
 #ifdef __cplusplus
 }

@@ -10,7 +10,7 @@ from ._abi import GPFError, LIB_PATH, load
 from .api import (GPF_DISK_KDE, GPF_NB_BALL_KNN, GPF_NB_KSIGMA, GPF_NORMALIZED, GPF_SUM, PAPER_EPS, PAPER_LR, PAPER_R,
                   AdamState, Field, GridConfig, Index, Queries, gpf_adam_step, gpf_count_pairs,
                   gpf_launch_count, gpf_mse_loss_grad, gpf_radiance_bwd, gpf_radiance_fwd,
-                  grid_for_bounds, photon_field)
+                  gpf_sort_pairs, grid_for_bounds, photon_field)
 from .autograd import GPFRadiance, gpf_radiance
 
 __all__ = [
@@ -19,6 +19,6 @@ __all__ = [
     "PAPER_LR", "photon_field",
     "PAPER_R", "AdamState", "Field", "GridConfig", "Index", "Queries", "gpf_adam_step",
     "gpf_mse_loss_grad", "gpf_radiance_bwd", "gpf_radiance_fwd", "grid_for_bounds",
-    "gpf_count_pairs", "gpf_launch_count",
+    "gpf_count_pairs", "gpf_launch_count", "gpf_sort_pairs",
     "GPFRadiance", "gpf_radiance", "_abi",
 ]

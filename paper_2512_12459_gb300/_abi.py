@@ -16,6 +16,7 @@ GPF_ERR_WORKSPACE_TOO_SMALL = 3
 GPF_ERR_CAPACITY = 4
 GPF_ERR_NOT_BUILT = 5
 GPF_ERR_MISMATCH = 6
+GPF_ERR_TIMEOUT = 7
 
 GPF_SUM = 0
 GPF_NORMALIZED = 1
@@ -101,6 +102,11 @@ SIGNATURES = {
     "gpf_adam_step": (c_i32, [ctypes.POINTER(gpf_field), ctypes.POINTER(gpf_field_grad),
                               ctypes.POINTER(gpf_field_grad), ctypes.POINTER(gpf_field_grad),
                               ctypes.POINTER(gpf_adam_hparams), c_vp]),
+    "gpf_sort_pairs_workspace_size": (c_i32, [c_i64, ctypes.POINTER(ctypes.c_size_t)]),
+    "gpf_sort_pairs": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, ctypes.c_size_t,
+                               ctypes.POINTER(c_i32), c_vp]),
+    "gpf_sort_pairs_check": (c_i32, [c_vp, c_vp]),
+    "gpf_test_sort_wait_timeout": (c_i32, [ctypes.c_uint32, c_vp]),
 }
 
 _lib = None

@@ -386,6 +386,32 @@ def gpf_radiance_bwd(index: Index, field: Field, queries: Queries, grad_out: tor
     return grads
 
 
+def gpf_sort_pairs(keys: torch.Tensor, vals: torch.Tensor, bits: int = 32, check_wait: bool = True,
+                   stream=None):
+    """The index build's stable radix sort of uint32 (key, value) pairs by key
+    bits [0, bits), as int32 CUDA tensors of one length (bit patterns of
+    uint32). Returns new (keys, vals) tensors in key order, equal keys in
+    input order. check_wait=True synchronises and raises GPFError
+    (GPF_ERR_TIMEOUT) if a bounded wait of the sort gave up."""
+    n = int(keys.numel())
+    for t, name in ((keys, "keys"), (vals, "vals")):
+        if t.dtype != torch.int32 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+            raise ValueError(f"{name}: contiguous int32 CUDA tensor of {n} elements expected")
+    lib = load()
+    sz = ctypes.c_size_t()
+    check(lib.gpf_sort_pairs_workspace_size(n, ctypes.byref(sz)), "gpf_sort_pairs_workspace_size")
+    ws = torch.empty(int(sz.value), dtype=torch.uint8, device=keys.device)
+    k0, v0 = keys.clone(), vals.clone()
+    k1, v1 = torch.empty_like(k0), torch.empty_like(v0)
+    alt = ctypes.c_int32()
+    check(lib.gpf_sort_pairs(k0.data_ptr(), v0.data_ptr(), k1.data_ptr(), v1.data_ptr(), n, bits,
+                             ws.data_ptr(), ws.numel(), ctypes.byref(alt), _stream(stream)),
+          "gpf_sort_pairs")
+    if check_wait:
+        check(lib.gpf_sort_pairs_check(ws.data_ptr(), _stream(stream)), "gpf_sort_pairs_check")
+    return (k1, v1) if alt.value else (k0, v0)
+
+
 class _MseWorkspace:
     cache = {}
 

@@ -225,6 +225,7 @@ const char* gpf_status_string(gpf_status s) {
     case GPF_ERR_CAPACITY: return "GPF_ERR_CAPACITY";
     case GPF_ERR_NOT_BUILT: return "GPF_ERR_NOT_BUILT";
     case GPF_ERR_MISMATCH: return "GPF_ERR_MISMATCH";
+    case GPF_ERR_TIMEOUT: return "GPF_ERR_TIMEOUT";
   }
   return "GPF_ERR_UNKNOWN";
 }
@@ -273,9 +274,9 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
                 GPF_MAX_COOP_CELLS);
   if (cfg->max_gaussians < 0 || cfg->max_queries < 0 || cfg->max_pairs < 0)
     return fail(GPF_ERR_INVALID_ARG, "capacities must be >= 0");
-  if (cfg->max_gaussians >= (int64_t)kIdMask || cfg->max_queries >= (int64_t)0xffffffffLL ||
-      cfg->max_pairs >= (int64_t)0xffffffffLL)
-    return fail(GPF_ERR_INVALID_ARG, "capacities must be below 2^31 (Gaussians) / 2^32");
+  if (cfg->max_gaussians >= kMaxSortN || cfg->max_queries >= kMaxSortN ||
+      cfg->max_pairs >= kMaxSortN)
+    return fail(GPF_ERR_INVALID_ARG, "capacities must be below 2^30");
   const uint64_t cells = (uint64_t)cfg->dims[0] * cfg->dims[1] * cfg->dims[2];
   if (cells > (1ull << 28))
     return fail(GPF_ERR_INVALID_ARG, "grid has %llu cells, more than 2^28",
@@ -384,6 +385,8 @@ gpf_status gpf_index_stats(const gpf_index* index, gpf_index_stats_t* stats, gpf
   stats->n_pairs = h.n_pairs;
   stats->n_active = h.n_active;
   stats->overflow = (int32_t)h.overflow;
+  if (h.stalled)
+    return fail(GPF_ERR_TIMEOUT, "a bounded wait of the index build's sort gave up");
   if (h.overflow)
     return fail(GPF_ERR_CAPACITY, "pair buffer overflow: %u entries needed, capacity %lld",
                 h.n_pairs, (long long)index->dims.p_max);
@@ -592,6 +595,76 @@ gpf_status gpf_field_quantize(const gpf_field* src, const gpf_field* dst, gpf_st
   }
   const cudaError_t e = launch_quantize(*src, *dst, reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "gpf_field_quantize");
+  return GPF_OK;
+}
+
+gpf_status gpf_sort_pairs_workspace_size(int64_t n, size_t* bytes) {
+  if (!bytes) return fail(GPF_ERR_INVALID_ARG, "bytes is NULL");
+  if (n < 0 || n >= kMaxSortN)
+    return fail(GPF_ERR_INVALID_ARG, "n = %lld outside [0, 2^30)", (long long)n);
+  *bytes = 256 + radix_sort_workspace_bytes(n > 0 ? n : 1);
+  return GPF_OK;
+}
+
+gpf_status gpf_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                          int64_t n, int32_t bits, void* workspace, size_t workspace_bytes,
+                          int32_t* result_in_alt, gpf_stream stream) {
+  if (!result_in_alt) return fail(GPF_ERR_INVALID_ARG, "result_in_alt is NULL");
+  size_t need = 0;
+  gpf_status s = gpf_sort_pairs_workspace_size(n, &need);
+  if (s != GPF_OK) return s;
+  if (bits < 0 || bits > 32) return fail(GPF_ERR_INVALID_ARG, "bits = %d outside 0..32", bits);
+  GPF_CHECK_PTR_AL(workspace, 256, "workspace");
+  if (workspace_bytes < need)
+    return fail(GPF_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes, %zu needed",
+                workspace_bytes, need);
+  if (n > 0) {
+    GPF_CHECK_PTR(keys, "keys");
+    GPF_CHECK_PTR(vals, "vals");
+    GPF_CHECK_PTR(keys_alt, "keys_alt");
+    GPF_CHECK_PTR(vals_alt, "vals_alt");
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint32_t* stalled = static_cast<uint32_t*>(workspace);
+  cudaError_t e = cudaMemsetAsync(stalled, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess && n > 0)
+    e = radix_sort_pairs(keys, vals, keys_alt, vals_alt, n, nullptr, bits,
+                         static_cast<char*>(workspace) + 256, stalled, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gpf_sort_pairs");
+  *result_in_alt = n > 0 ? radix_sort_passes(bits) % 2 : 0;
+  return GPF_OK;
+}
+
+gpf_status gpf_sort_pairs_check(const void* workspace, gpf_stream stream) {
+  GPF_CHECK_PTR_AL(workspace, 256, "workspace");
+  uint32_t flag = 0;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(&flag, workspace, sizeof(flag), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "gpf_sort_pairs_check");
+  if (flag) return fail(GPF_ERR_TIMEOUT, "a bounded wait of the sort gave up");
+  return GPF_OK;
+}
+
+gpf_status gpf_test_sort_wait_timeout(uint32_t spin_limit, gpf_stream stream) {
+  if (spin_limit < 1 || spin_limit > (1u << 22))
+    return fail(GPF_ERR_INVALID_ARG, "spin_limit = %u outside 1 .. 2^22", spin_limit);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  void* buf = nullptr;
+  uint32_t* stalled = nullptr;
+  cudaError_t e = cudaMalloc(&buf, sort_wait_probe_bytes());
+  if (e == cudaSuccess) e = cudaMalloc(&stalled, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(stalled, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = launch_sort_wait_probe(buf, spin_limit, stalled, st);
+  uint32_t flag = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&flag, stalled, sizeof(flag), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (buf) cudaFree(buf);
+  if (stalled) cudaFree(stalled);
+  if (e != cudaSuccess) return cuda_fail(e, "gpf_test_sort_wait_timeout");
+  if (flag) return fail(GPF_ERR_TIMEOUT, "the wait gave up after %u polls and set the flag",
+                        spin_limit);
   return GPF_OK;
 }
 

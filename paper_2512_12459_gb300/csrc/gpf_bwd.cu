@@ -61,7 +61,7 @@ template <int C>
 __global__ void pack_qrec_kernel(BwdArgs a) {
   constexpr int QS = qrec_stride(C);
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= (int64_t)a.header->n_active) return;
+  if (index_unusable(a.header) || k >= (int64_t)a.header->n_active) return;
   const uint32_t q = a.qval[k];
   float gam[C];
   float kappa = 0.0f, zeta = 1.0f;
@@ -349,11 +349,11 @@ __device__ void bwd_lane_gaussian(const BwdArgs& a, int64_t pos, int64_t gi) {
 // query-level cell its k-sigma bounds overlap. Gaussians whose level box
 // holds no hit point come last and are skipped (zero gradient).
 template <int C, bool PSI>
-__global__ void __launch_bounds__(kBwdThreads, 7)
+__global__ void __launch_bounds__(kBwdThreads, 8)
 bwd_grid_kernel(BwdArgs a) {
   constexpr int QS = qrec_stride(C);
   const int lane = threadIdx.x & 31;
-  if (a.header->overflow) return;
+  if (index_unusable(a.header)) return;
   const int64_t n_small = a.header->n_small, n_live = a.header->n_live;
   const int64_t small_warps = (n_small + kWarp - 1) / kWarp;
   const int64_t n_split = min((int64_t)a.header->n_huge, kSplitMax);
@@ -461,7 +461,7 @@ bwd_brute_kernel(BwdArgs a) {
   constexpr int QS = qrec_stride(C);
   const int lane = threadIdx.x & 31;
   const int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (gi >= a.n) return;
+  if (gi >= a.n || index_unusable(a.header)) return;
   const int64_t n_act = a.header->n_active;
   GaussianRegs G;
   float phi[C];
@@ -482,7 +482,7 @@ bwd_brute_kernel(BwdArgs a) {
 template <int C>
 __global__ void bwd_epilogue_kernel(BwdArgs a, int brute) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (!brute && a.header->overflow) return;
+  if (index_unusable(a.header)) return;
   const int64_t count = brute ? a.n : (int64_t)a.header->n_live;
   if (j >= count) return;
   const int64_t gi = brute ? j : a.order[j];

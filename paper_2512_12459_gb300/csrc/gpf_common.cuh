@@ -29,13 +29,19 @@ struct DeviceHeader {
   uint32_t n_live;       // Gaussians whose level box holds a hit point
   uint32_t n_small;      // live Gaussians spanning <= 2 query-level cells per axis
   uint32_t n_huge;       // live large Gaussians of the top size rank (split in the backward)
-  uint32_t reserved0;
+  uint32_t stalled;      // 1 if a bounded wait of the build's sort gave up
   // work counters of the persistent pair loops (reset before each launch)
   unsigned long long next_tile;       // forward: next tile of 32 hit points
   unsigned long long next_work;       // backward: next work item
   uint32_t pad[52];
 };
 static_assert(sizeof(DeviceHeader) == 256, "header is one 256-byte block");
+
+// The index of the last build cannot be used (a full pair buffer or a sort
+// that gave up waiting): the kernels that read it return at once.
+__device__ __forceinline__ bool index_unusable(const DeviceHeader* h) {
+  return (h->overflow | h->stalled) != 0u;
+}
 
 // Per-Gaussian record read by the pair loops, float32, stride rec_stride(C):
 //   [0..2]  mu

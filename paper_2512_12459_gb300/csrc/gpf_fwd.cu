@@ -187,7 +187,7 @@ fwd_kernel(FwdArgs a) {
   __shared__ float s_acc[kFwdWarps][C + 1][kWarp];  // pooled-mode sums per hit point
 
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  if (a.header->overflow) return;
+  if (index_unusable(a.header)) return;
   const int64_t n_act = a.header->n_active;
   const int64_t n_tiles = (a.m + kWarp - 1) / kWarp;
   uint32_t n_eval = 0, n_inc = 0;

@@ -201,7 +201,7 @@ hybrid_fwd_kernel(HybArgs a) {
   constexpr int RS = rec_stride(C);
   __shared__ __align__(16) float s_rec[kHybWarps][kWarp * RS];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  if (a.header->overflow) return;
+  if (index_unusable(a.header)) return;
   const Grid& G = a.grid;
   const int Lb = G.blevel;
   const int64_t n_act = a.header->n_active;

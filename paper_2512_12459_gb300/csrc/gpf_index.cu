@@ -236,6 +236,8 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
                                   uint32_t* __restrict__ qcount, DeviceHeader* header) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool active = false;
+  uint32_t k = grid.key_inactive;
+  uint32_t c0[3] = {0u, 0u, 0u};   // level-0 cell of an active hit point
   if (i < m) {
     // hemisphere gate n . w_o > 0, summed in float64 in a fixed order (the
     // three products of float32 values are exact in float64)
@@ -243,25 +245,34 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
                                    __dmul_rn((double)nrm[m + i], (double)wo[m + i])),
                          __dmul_rn((double)nrm[2 * m + i], (double)wo[2 * m + i]));
     active = d > 0.0 && (valid == nullptr || valid[i] != 0);
-    uint32_t k = grid.key_inactive;
     if (active) {
       const uint32_t cx = coord0(x[i], grid.ox, grid.inv_cell0, grid.max0x);
       const uint32_t cy = coord0(x[m + i], grid.oy, grid.inv_cell0, grid.max0y);
       const uint32_t cz = coord0(x[2 * m + i], grid.oz, grid.inv_cell0, grid.max0z);
       const int K = grid.qlevel;
       k = qkey_of(grid, cx >> K, cy >> K, cz >> K);
-      atomicAdd(&qcount[k], 1u);
-      if (mark) {
-        for (int L = 0; L < grid.levels; ++L) {
-          const uint32_t b = bucket_of(grid, L, cx >> L, cy >> L, cz >> L);
-          const uint32_t bit = 1u << (b & 31u);
-          if (!(occ[b >> 5] & bit)) atomicOr(&occ[b >> 5], bit);
-        }
-      }
+      c0[0] = cx; c0[1] = cy; c0[2] = cz;
     }
     key[i] = k;
     val[i] = (uint32_t)i;
   }
+  if (mark) {
+    // occupancy bits of every level; lanes in the same cell of a level (all
+    // of a warp's on the coarse ones) set its bit once
+    for (int L = 0; L < grid.levels; ++L) {
+      const uint32_t b = active ? bucket_of(grid, L, c0[0] >> L, c0[1] >> L, c0[2] >> L)
+                                : 0xffffffffu;
+      const uint32_t same = __match_any_sync(kFullMask, b);
+      if (active && (same & lanemask_lt()) == 0) {
+        const uint32_t bit = 1u << (b & 31u);
+        if (!(occ[b >> 5] & bit)) atomicOr(&occ[b >> 5], bit);
+      }
+    }
+  }
+  // per-cell counts: one atomic per distinct cell of the warp (neighbouring
+  // pixels share query cells)
+  const uint32_t peers = __match_any_sync(kFullMask, active ? k : 0xffffffffu);
+  if (active && (peers & lanemask_lt()) == 0) atomicAdd(&qcount[k], (uint32_t)__popc(peers));
   const uint32_t ballot = __ballot_sync(kFullMask, active);
   if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(&header->n_active, __popc(ballot));
 }
@@ -311,10 +322,11 @@ __global__ void emit_kernel(Grid grid, int64_t n, int64_t p_max, const float* __
 
 // [start, end) of every non-empty bucket from the boundaries of the sorted
 // keys (the other buckets keep the [0, 0) of the memset).
-__global__ void bucket_range_kernel(const uint32_t* __restrict__ keys, const uint32_t* d_n,
+__global__ void bucket_range_kernel(const uint32_t* __restrict__ keys, const DeviceHeader* header,
                                     int64_t n_cap, uint2* __restrict__ range) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t n = *d_n;
+  if (header->stalled) return;
+  int64_t n = header->n_pairs;
   if (n > n_cap) n = n_cap;
   if (i >= n) return;
   const uint32_t k = keys[i];
@@ -376,14 +388,14 @@ cudaError_t launch_build(const IndexDims& d, const IndexBuffers& b, const gpf_fi
   }
   // 3. hit points sorted by query-level cell (inactive ones last), cell starts
   e = radix_sort_pairs(b.qkey[0], b.qval[0], b.qkey[1], b.qval[1], q.m, nullptr, grid.key_bits,
-                       b.qsort_ws, stream);
+                       b.qsort_ws, &b.header->stalled, stream);
   if (e != cudaSuccess) return e;
   e = exclusive_scan_u32(b.qstart, b.qstart, (int64_t)grid.n_keys + 2, nullptr, b.scan_ws,
                          stream);
   if (e != cudaSuccess) return e;
   // 4. Gaussians in the backward's order
   e = radix_sort_pairs(b.okey[0], b.oval[0], b.okey[1], b.oval[1], f.n, nullptr, grid.obits,
-                       b.osort_ws, stream);
+                       b.osort_ws, &b.header->stalled, stream);
   if (e != cudaSuccess) return e;
   if (d.brute || f.n == 0) return cudaGetLastError();
   // 5. (bucket, Gaussian) entries: scan, emit, sort, bucket starts
@@ -394,14 +406,14 @@ cudaError_t launch_build(const IndexDims& d, const IndexBuffers& b, const gpf_fi
                                                         b.goffset, b.gkey[0], b.gval[0], b.header);
   note_launches(1);
   e = radix_sort_pairs(b.gkey[0], b.gval[0], b.gkey[1], b.gval[1], d.p_max, &b.header->n_pairs,
-                       grid.hash_bits, b.gsort_ws, stream);
+                       grid.hash_bits, b.gsort_ws, &b.header->stalled, stream);
   if (e != cudaSuccess) return e;
   // bucket ranges from the boundaries of the sorted keys
   e = cudaMemsetAsync(b.brange, 0, sizeof(uint2) * (size_t)grid.n_buckets, stream);
   if (e != cudaSuccess) return e;
   if (d.p_max > 0) {
     bucket_range_kernel<<<blocks_for(d.p_max), kThreads, 0, stream>>>(
-        b.gkey[b.gsorted], &b.header->n_pairs, d.p_max, b.brange);
+        b.gkey[b.gsorted], b.header, d.p_max, b.brange);
     note_launches(1);
   }
   return cudaGetLastError();

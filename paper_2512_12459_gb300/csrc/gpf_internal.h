@@ -25,15 +25,23 @@ size_t scan_workspace_bytes(int64_t n_max);
 // out[i] = sum_{j<i} in[j] for i < n (host-known n); *total_out = sum (device, may be null).
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_out,
                                void* ws, cudaStream_t stream);
+// The sort's element count limit: status words hold 30-bit counts.
+constexpr int64_t kMaxSortN = int64_t(1) << 30;
 int64_t radix_tiles(int64_t n_max);
 size_t radix_sort_workspace_bytes(int64_t n_max);
 int radix_sort_passes(int bits);
 // Stable sort of min(*d_n, n_max) pairs (n_max pairs when d_n is null) by
 // key bits [0, bits). The result is in (k0, v0) after an even number of
-// passes, in (k1, v1) after an odd one.
+// passes, in (k1, v1) after an odd one. *stalled (device) is set to 1 if a
+// bounded wait of the single-pass sort gave up (the output is then invalid).
 cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                              int64_t n_max, const uint32_t* d_n, int bits, void* ws,
-                             cudaStream_t stream);
+                             uint32_t* stalled, cudaStream_t stream);
+// The failure-detection probe of the single-pass sort's bounded wait (a
+// look-back whose predecessor tile is never processed): buffer size, launch.
+size_t sort_wait_probe_bytes();
+cudaError_t launch_sort_wait_probe(void* buf, uint32_t spin_limit, uint32_t* stalled,
+                                   cudaStream_t stream);
 
 // ---- index build (gpf_index.cu)
 struct IndexBuffers {

@@ -1,18 +1,31 @@
 // Device-wide exclusive scan of uint32 values and a stable LSD radix sort of
 // (uint32 key, uint32 value) pairs, 8 bits per pass.
 //
-// Sort pass, for a tile of 2048 keys per block:
-//   1. histogram: per-tile digit counts, stored digit-major (digit * tiles + tile)
-//   2. exclusive scan of the digit-major counts: global base of (digit, tile)
-//   3. scatter: the stable rank of every key inside its tile comes from warp
-//      __match_any_sync groups, combined across warps and rounds in shared
-//      memory; keys are first ordered by digit in shared memory and then written
-//      out so that runs of equal digits land on consecutive addresses.
+// Sort (single pass per digit, decoupled look-back; Merrill and Garland,
+// "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016, and
+// Adinets and Merrill, "Onesweep", 2022):
+//   0. one kernel counts the digits of every pass over all keys (the global
+//      digit counts do not depend on the order the earlier passes leave);
+//   1. per pass, one kernel: a block claims the next tile of 2048 keys from
+//      an atomic counter (so every earlier tile is held by a block that is
+//      already running); each warp ranks its own 256 keys, 32 at a time
+//      (__match_any_sync groups, per-warp digit counters in shared memory);
+//      the block publishes its digit counts, orders its keys by digit in
+//      shared memory, adds up the counts the earlier tiles published for each
+//      digit, walking back until a tile whose inclusive prefix is known,
+//      publishes its own inclusive prefix and writes its keys out in digit
+//      order (runs of equal digits land on consecutive addresses).
+//   Every wait in the walk is bounded: after kSpinLimit polls the block sets
+//   the caller's stall flag, stops waiting and writes only in-bounds
+//   addresses; the sorted output is then invalid and the flag says so.
+//   Counts are below kMaxSortN = 2^30 (30-bit status values).
 // The element count may live on the device (it is produced by an earlier
 // kernel); grids are sized for the capacity and blocks past the count return
 // early, so a whole build can be captured in a CUDA graph.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "gpf_internal.h"
 
@@ -119,93 +132,141 @@ __device__ __forceinline__ uint32_t load_count(const uint32_t* d_n, int64_t n_ma
   return (int64_t)n > n_max ? (uint32_t)n_max : n;
 }
 
-__global__ void radix_hist_kernel(const uint32_t* __restrict__ keys, const uint32_t* d_n,
-                                  int64_t n_max, int shift, uint32_t* __restrict__ hist,
-                                  int64_t n_tiles) {
-  __shared__ uint32_t cnt[kBins];
-  const uint32_t n = load_count(d_n, n_max);
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  for (int d = threadIdx.x; d < kBins; d += kSortThreads) cnt[d] = 0;
+// ---- single-pass (decoupled look-back) sort
+
+constexpr int kMaxPasses = 4;                  // 32-bit keys
+constexpr uint32_t kFlagAgg = 1u << 30;        // the tile's own count is published
+constexpr uint32_t kFlagPre = 2u << 30;        // the inclusive prefix is published
+constexpr uint32_t kValMask = kFlagAgg - 1u;
+constexpr uint32_t kSpinLimit = 1u << 22;      // polls of one status word before giving up
+
+__device__ __forceinline__ uint32_t ld_status(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_status(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Digit counts of every pass over all keys: ghist[pass * 256 + digit].
+__global__ void onesweep_hist_kernel(const uint32_t* __restrict__ keys, const uint32_t* d_n,
+                                     int64_t n_max, int passes, uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t cnt[kMaxPasses * kBins];
+  for (int i = threadIdx.x; i < kMaxPasses * kBins; i += blockDim.x) cnt[i] = 0;
   __syncthreads();
-  if (base < (int64_t)n) {
-#pragma unroll
-    for (int r = 0; r < kSortPerThread; ++r) {
-      int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
-      bool ok = i < (int64_t)n;
-      uint32_t d = ok ? (keys[i] >> shift) & (kBins - 1) : kBins;
-      uint32_t peers = __match_any_sync(kFullMask, d);
-      if (ok && (peers & lanemask_lt()) == 0) atomicAdd(&cnt[d], __popc(peers));
-    }
+  const uint32_t n = load_count(d_n, n_max);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // plain shared-memory atomics: cheaper here than grouping equal digits first
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)n; i += stride) {
+    const uint32_t k = keys[i];
+    for (int p = 0; p < passes; ++p) atomicAdd(&cnt[p * kBins + ((k >> (8 * p)) & (kBins - 1))], 1u);
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < kBins; d += kSortThreads)
-    hist[(int64_t)d * n_tiles + blockIdx.x] = cnt[d];
+  for (int i = threadIdx.x; i < passes * kBins; i += blockDim.x)
+    if (cnt[i]) atomicAdd(&ghist[i], cnt[i]);
 }
 
 __global__ void __launch_bounds__(kSortThreads)
-radix_scatter_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+onesweep_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                      uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                      const uint32_t* d_n, int64_t n_max, int shift,
-                     const uint32_t* __restrict__ hist, const uint32_t* __restrict__ offs,
-                     int64_t n_tiles) {
+                     const uint32_t* __restrict__ ghist, uint32_t* status,
+                     uint32_t* tile_counter, uint32_t tile_base, uint32_t spin_limit,
+                     uint32_t* stalled) {
+  constexpr int kWarpKeys = kSortPerThread * kWarp;   // each warp ranks its own 256 keys
   __shared__ uint32_t s_keys[kSortTile];
   __shared__ uint32_t s_vals[kSortTile];
-  __shared__ uint32_t warp_cnt[kSortWarps][kBins];   // (round << 16) | count
-  __shared__ uint32_t warp_base[kSortWarps][kBins];
+  __shared__ uint32_t wcnt[kSortWarps][kBins];   // digit counts of each warp, then its bases
   __shared__ uint32_t tile_start[kBins];
-  __shared__ uint32_t running[kBins];
+  __shared__ uint32_t out_base[kBins];
   __shared__ uint32_t total;
+  __shared__ uint32_t s_tile;
 
+  const int t = threadIdx.x;        // kSortThreads == kBins: thread t owns digit t
+  const int lane = t & 31, warp = t >> 5;
+  if (t == 0) s_tile = tile_base + atomicAdd(tile_counter, 1u);
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) wcnt[w][t] = 0;
+  __syncthreads();
   const uint32_t n = load_count(d_n, n_max);
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  if (base >= (int64_t)n) return;
+  const uint32_t tile = s_tile;
+  const int64_t base = (int64_t)tile * kSortTile;
+  if (base >= (int64_t)n) return;                    // the whole block
   const int tile_n = (int)min((int64_t)kSortTile, (int64_t)n - base);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  // digit starts inside this tile (kSortThreads == kBins: one digit per thread)
-  {
-    uint32_t c = hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x];
-    tile_start[threadIdx.x] = block_exclusive_scan(c, &total);
-    running[threadIdx.x] = 0;
-    for (int w = 0; w < kSortWarps; ++w) warp_cnt[w][threadIdx.x] = 0xffff0000u;
-  }
-  __syncthreads();
-
-  for (int r = 0; r < kSortPerThread; ++r) {
-    const int li = r * kSortThreads + threadIdx.x;
+  // 1. ranks inside the warp's 256 keys (taken 32 at a time in order):
+  //    (rank << 9) | digit, digit kBins for the positions past the tile
+  uint32_t rd[kSortPerThread];
+#pragma unroll
+  for (int it = 0; it < kSortPerThread; ++it) {
+    const int li = warp * kWarpKeys + it * kWarp + lane;
     const bool ok = li < tile_n;
-    uint32_t key = ok ? keys_in[base + li] : 0u;
-    uint32_t val = ok ? vals_in[base + li] : 0u;
-    uint32_t d = ok ? (key >> shift) & (kBins - 1) : kBins;
-    uint32_t peers = __match_any_sync(kFullMask, d);
-    uint32_t lt = peers & lanemask_lt();
-    if (ok && lt == 0) warp_cnt[warp][d] = ((uint32_t)r << 16) | (uint32_t)__popc(peers);
-    __syncthreads();
-    {
-      const int t = threadIdx.x;
-      uint32_t run = running[t];
-      for (int w = 0; w < kSortWarps; ++w) {
-        uint32_t e = warp_cnt[w][t];
-        uint32_t c = (e >> 16) == (uint32_t)r ? (e & 0xffffu) : 0u;
-        warp_base[w][t] = run;
-        run += c;
-      }
-      running[t] = run;
-    }
-    __syncthreads();
-    if (ok) {
-      uint32_t pos = tile_start[d] + warp_base[warp][d] + (uint32_t)__popc(lt);
-      s_keys[pos] = key;
-      s_vals[pos] = val;
-    }
+    const uint32_t d = ok ? (keys_in[base + li] >> shift) & (kBins - 1) : kBins;
+    const uint32_t peers = __match_any_sync(kFullMask, d);
+    uint32_t r0 = 0;
+    if (ok) r0 = wcnt[warp][d];
+    __syncwarp();
+    if (ok && (peers & lanemask_lt()) == 0) wcnt[warp][d] = r0 + (uint32_t)__popc(peers);
+    __syncwarp();
+    rd[it] = ((r0 + (uint32_t)__popc(peers & lanemask_lt())) << 9) | d;
   }
   __syncthreads();
-  for (int p = threadIdx.x; p < tile_n; p += kSortThreads) {
-    uint32_t key = s_keys[p];
-    uint32_t d = (key >> shift) & (kBins - 1);
-    uint32_t dst = offs[(int64_t)d * n_tiles + blockIdx.x] + ((uint32_t)p - tile_start[d]);
-    keys_out[dst] = key;
-    vals_out[dst] = s_vals[p];
+  // 2. digit t: the warps' bases and the tile's count; publish the count
+  //    (tile 0: its inclusive prefix)
+  uint32_t c = 0;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) {
+    const uint32_t x = wcnt[w][t];
+    wcnt[w][t] = c;
+    c += x;
+  }
+  st_status(status + (int64_t)tile * kBins + t, (tile == 0 ? kFlagPre : kFlagAgg) | c);
+  tile_start[t] = block_exclusive_scan(c, &total);
+  const uint32_t digit_start = block_exclusive_scan(ghist[t], &total);
+  // 3. keys in digit order in shared memory (reloaded: the tile is in L1/L2)
+#pragma unroll
+  for (int it = 0; it < kSortPerThread; ++it) {
+    const uint32_t d = rd[it] & 511u;
+    if (d < (uint32_t)kBins) {
+      const int li = warp * kWarpKeys + it * kWarp + lane;
+      const uint32_t pos = tile_start[d] + wcnt[warp][d] + (rd[it] >> 9);
+      s_keys[pos] = keys_in[base + li];
+      s_vals[pos] = vals_in[base + li];
+    }
+  }
+  // 4. digit t in the earlier tiles: walk back to the nearest inclusive prefix
+  uint32_t excl = 0;
+  if (tile > 0) {
+    int64_t j = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    while (j >= 0) {
+      const uint32_t sv = ld_status(status + j * kBins + t);
+      const uint32_t flag = sv & ~kValMask;
+      if (flag == 0u) {
+        if (++spins >= spin_limit) {
+          atomicExch(stalled, 1u);
+          break;
+        }
+        __nanosleep(64);
+        continue;
+      }
+      excl += sv & kValMask;
+      if (flag == kFlagPre) break;
+      --j;
+    }
+    st_status(status + (int64_t)tile * kBins + t, kFlagPre | ((excl + c) & kValMask));
+  }
+  out_base[t] = digit_start + excl - tile_start[t];
+  __syncthreads();
+  // 5. out in digit order: runs of one digit go to consecutive addresses
+  for (int p = t; p < tile_n; p += kSortThreads) {
+    const uint32_t k = s_keys[p];
+    const uint32_t dst = out_base[(k >> shift) & (kBins - 1)] + (uint32_t)p;
+    if (dst < n) {
+      keys_out[dst] = k;
+      vals_out[dst] = s_vals[p];
+    }
   }
 }
 
@@ -234,40 +295,73 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n,
 
 int64_t radix_tiles(int64_t n_max) { return (n_max + kSortTile - 1) / kSortTile; }
 
+// The digit counts and tile counters of every pass, then the per-pass tile
+// status words.
 size_t radix_sort_workspace_bytes(int64_t n_max) {
   const int64_t hist_n = radix_tiles(n_max) * kBins;
-  return 2 * align_up((size_t)hist_n * sizeof(uint32_t)) + scan_workspace_bytes(hist_n);
+  return align_up(sizeof(uint32_t) * (kMaxPasses * kBins + kMaxPasses)) +
+         align_up((size_t)kMaxPasses * hist_n * sizeof(uint32_t));
 }
 
 int radix_sort_passes(int bits) { return bits <= 0 ? 0 : (bits + 7) / 8; }
 
+// Two tiles of keys and values in and out, the digit counts and tile
+// counter of one pass, two tiles of status words.
+size_t sort_wait_probe_bytes() {
+  return sizeof(uint32_t) * (8 * (size_t)kSortTile + kBins + 1 + 2 * kBins);
+}
+
+cudaError_t launch_sort_wait_probe(void* buf, uint32_t spin_limit, uint32_t* stalled,
+                                   cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(buf, 0, sort_wait_probe_bytes(), stream);
+  if (e != cudaSuccess) return e;
+  uint32_t* w = static_cast<uint32_t*>(buf);
+  uint32_t* keys_in = w;
+  uint32_t* vals_in = w + 2 * kSortTile;
+  uint32_t* keys_out = w + 4 * kSortTile;
+  uint32_t* vals_out = w + 6 * kSortTile;
+  uint32_t* ghist = w + 8 * kSortTile;
+  uint32_t* counter = ghist + kBins;
+  uint32_t* status = counter + 1;
+  // one block, claiming tile 1 (tile_base 1): tile 0 is never processed, so
+  // its status words stay 0 and the walk back from tile 1 waits on them
+  onesweep_pass_kernel<<<1, kSortThreads, 0, stream>>>(
+      keys_in, vals_in, keys_out, vals_out, nullptr, 2 * kSortTile, 0, ghist, status, counter,
+      1u, spin_limit, stalled);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                              int64_t n_max, const uint32_t* d_n, int bits, void* ws,
-                             cudaStream_t stream) {
+                             uint32_t* stalled, cudaStream_t stream) {
   if (n_max <= 0) return cudaSuccess;
+  if (n_max >= kMaxSortN) return cudaErrorInvalidValue;
   const int64_t tiles = radix_tiles(n_max);
-  const int64_t hist_n = tiles * kBins;
-  char* p = static_cast<char*>(ws);
-  uint32_t* hist = reinterpret_cast<uint32_t*>(p);
-  p += align_up((size_t)hist_n * sizeof(uint32_t));
-  uint32_t* offs = reinterpret_cast<uint32_t*>(p);
-  p += align_up((size_t)hist_n * sizeof(uint32_t));
-  void* scan_ws = p;
   const int passes = radix_sort_passes(bits);
+  if (passes == 0) return cudaSuccess;
+  char* p = static_cast<char*>(ws);
+  uint32_t* ghist = reinterpret_cast<uint32_t*>(p);        // [kMaxPasses][kBins]
+  uint32_t* counters = ghist + kMaxPasses * kBins;          // [kMaxPasses]
+  p += align_up(sizeof(uint32_t) * (kMaxPasses * kBins + kMaxPasses));
+  uint32_t* status = reinterpret_cast<uint32_t*>(p);        // [passes][tiles][kBins]
+  cudaError_t e = cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * (kMaxPasses * kBins + kMaxPasses),
+                                  stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(status, 0, sizeof(uint32_t) * (size_t)passes * tiles * kBins, stream);
+  if (e != cudaSuccess) return e;
+  const unsigned hblocks = (unsigned)std::min<int64_t>(tiles, 1024);
+  onesweep_hist_kernel<<<hblocks, kSortThreads, 0, stream>>>(k0, d_n, n_max, passes, ghist);
   uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
   for (int pass = 0; pass < passes; ++pass) {
-    const int shift = pass * 8;
-    radix_hist_kernel<<<(unsigned)tiles, kSortThreads, 0, stream>>>(ki, d_n, n_max, shift, hist,
-                                                                     tiles);
-    cudaError_t e = exclusive_scan_u32(hist, offs, hist_n, nullptr, scan_ws, stream);
-    if (e != cudaSuccess) return e;
-    radix_scatter_kernel<<<(unsigned)tiles, kSortThreads, 0, stream>>>(
-        ki, vi, ko, vo, d_n, n_max, shift, hist, offs, tiles);
-    note_launches(2);
-    uint32_t* t;
-    t = ki; ki = ko; ko = t;
-    t = vi; vi = vo; vo = t;
+    onesweep_pass_kernel<<<(unsigned)tiles, kSortThreads, 0, stream>>>(
+        ki, vi, ko, vo, d_n, n_max, pass * 8, ghist + pass * kBins,
+        status + (size_t)pass * tiles * kBins, counters + pass, 0u, kSpinLimit, stalled);
+    uint32_t* tmp;
+    tmp = ki; ki = ko; ko = tmp;
+    tmp = vi; vi = vo; vo = tmp;
   }
+  note_launches(1 + passes);
   return cudaGetLastError();
 }
 

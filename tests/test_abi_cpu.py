@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(lib, root_dir):
 def test_version_and_status_strings(lib):
     assert b"sm_103a" in lib.gpf_version()
     for s, name in [(0, b"GPF_OK"), (1, b"GPF_ERR_INVALID_ARG"), (4, b"GPF_ERR_CAPACITY"),
-                    (6, b"GPF_ERR_MISMATCH")]:
+                    (6, b"GPF_ERR_MISMATCH"), (7, b"GPF_ERR_TIMEOUT")]:
         assert lib.gpf_status_string(s) == name
     assert lib.gpf_status_string(99) == b"GPF_ERR_UNKNOWN"
 
@@ -66,7 +66,9 @@ def _cfg(**kw):
                                  dict(max_span=0), dict(hash_bits=7), dict(hash_bits=29),
                                  dict(query_level=16), dict(query_level=11, dims=(1024, 4, 4)),
                                  dict(coop_cells=-1), dict(coop_cells=9), dict(field_storage=3),
-                                 dict(ball_radius=-1.0), dict(ball_radius=math.inf)])
+                                 dict(ball_radius=-1.0), dict(ball_radius=math.inf),
+                                 dict(max_pairs=1 << 30), dict(max_queries=1 << 30),
+                                 dict(max_gaussians=1 << 30)])
 def test_index_create_rejects_bad_configs(lib, bad):
     h = ctypes.c_void_p()
     cfg = _cfg(**bad)
@@ -158,6 +160,27 @@ def test_loss_and_adam_validation(lib):
     assert lib.gpf_adam_step(ctypes.byref(f), ctypes.byref(g), ctypes.byref(g), ctypes.byref(g),
                              ctypes.byref(hp), None) == 1
     assert b"step_counter" in lib.gpf_last_error()
+
+
+def test_sort_validation(lib):
+    fake = 1 << 40
+    sz = ctypes.c_size_t()
+    assert lib.gpf_sort_pairs_workspace_size(10_000_000, ctypes.byref(sz)) == 0
+    small = sz.value
+    assert lib.gpf_sort_pairs_workspace_size(20_000_000, ctypes.byref(sz)) == 0
+    assert sz.value > small > 256
+    assert lib.gpf_sort_pairs_workspace_size(-1, ctypes.byref(sz)) == 1
+    assert lib.gpf_sort_pairs_workspace_size(1 << 31, ctypes.byref(sz)) == 1
+    alt = ctypes.c_int32()
+    args = (fake, fake, fake, fake, 1000)
+    assert lib.gpf_sort_pairs(*args, 33, fake, 1 << 30, ctypes.byref(alt), None) == 1
+    assert lib.gpf_sort_pairs(*args, 24, fake + 16, 1 << 30, ctypes.byref(alt), None) == 1
+    assert lib.gpf_sort_pairs(*args, 24, fake, 16, ctypes.byref(alt), None) == 3
+    assert lib.gpf_sort_pairs(None, fake, fake, fake, 1000, 24, fake, 1 << 30,
+                              ctypes.byref(alt), None) == 1
+    assert lib.gpf_sort_pairs(*args, 24, fake, 1 << 30, None, None) == 1
+    assert lib.gpf_test_sort_wait_timeout(0, None) == 1
+    assert lib.gpf_test_sort_wait_timeout((1 << 22) + 1, None) == 1
 
 
 def test_package_defaults_are_the_papers(lib):
