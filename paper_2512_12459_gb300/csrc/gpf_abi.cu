@@ -92,6 +92,8 @@ size_t layout(const gpf_index* ix, char* base, IndexBuffers* b) {
   t.rec = reinterpret_cast<float*>(take(sizeof(float) * N * rec_stride(d.channels)));
   t.box = reinterpret_cast<uint4*>(take(sizeof(uint4) * N));
   t.gcount = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * N));
+  t.glive = reinterpret_cast<uint8_t*>(take(sizeof(uint8_t) * N));
+  t.gmask = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * N));
   t.goffset = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * N));
   for (int k = 0; k < 2; ++k) {
     t.okey[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * N));

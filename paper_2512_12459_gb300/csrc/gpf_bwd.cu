@@ -22,6 +22,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "gpf_internal.h"
 
 namespace gpf {
@@ -43,7 +45,8 @@ struct BwdArgs {
   const float* z;
   int64_t m;
   float* qrec;
-  float* gacc;            // [N * NS] per-Gaussian sums, by position in the order
+  float* gacc;            // [N * NS] per-Gaussian sums, by Gaussian id
+  const uint8_t* glive;   // [N] 1 if the pair loop visits the Gaussian
   float* bpart;           // [kSplitMax * kSplitWays * NS] split Gaussians' partials
   const float* rec;
   const uint4* box;
@@ -310,7 +313,7 @@ __device__ __forceinline__ void load_gaussian(const BwdArgs& a, int64_t gi, Gaus
 // One lane runs one small Gaussian (bounds within 2 x 2 x 2 query-level
 // cells) alone: no reduction across lanes, the epilogues run side by side.
 template <int C, bool PSI>
-__device__ void bwd_lane_gaussian(const BwdArgs& a, int64_t pos, int64_t gi) {
+__device__ void bwd_lane_gaussian(const BwdArgs& a, int64_t gi) {
   constexpr int QS = qrec_stride(C);
   const Grid& Gd = a.grid;
   GaussianRegs G;
@@ -334,7 +337,7 @@ __device__ void bwd_lane_gaussian(const BwdArgs& a, int64_t pos, int64_t gi) {
     }
   float v[Acc<C>::NS];
   acc.to_array(v);
-  float4* dst = reinterpret_cast<float4*>(a.gacc + pos * Acc<C>::NS);
+  float4* dst = reinterpret_cast<float4*>(a.gacc + gi * Acc<C>::NS);
 #pragma unroll
   for (int i = 0; i < Acc<C>::NS / 4; ++i)
     dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
@@ -343,7 +346,7 @@ __device__ void bwd_lane_gaussian(const BwdArgs& a, int64_t pos, int64_t gi) {
 // Grid path. The Gaussians come in (class, size, mean-cell) order, the small
 // ones first and the large ones largest first; the largest (up to kSplitMax)
 // are split into kSplitWays work units, each over every kSplitWays-th block
-// of 32 rows, whose partial sums the epilogue adds in part order:
+// of 32 rows, whose partial sums bwd_split_combine_kernel adds in part order:
 // the first ceil(n_small / 32) warps give each lane one small Gaussian; every
 // later warp runs one large Gaussian over the hit points of every
 // query-level cell its k-sigma bounds overlap. Gaussians whose level box
@@ -368,7 +371,7 @@ bwd_grid_kernel(BwdArgs a) {
   if (w >= units) break;
   if (w < small_warps) {
     const int64_t idx = w * kWarp + lane;
-    if (idx < n_small) bwd_lane_gaussian<C, PSI>(a, idx, a.order[idx]);
+    if (idx < n_small) bwd_lane_gaussian<C, PSI>(a, a.order[idx]);
     __syncwarp();
     continue;
   }
@@ -448,7 +451,7 @@ bwd_grid_kernel(BwdArgs a) {
   int slot;
   const float sum = reduce_scatter<Acc<C>::NS>(v, lane, &slot);
   float* dst = split ? a.bpart + ((j - n_small) * kSplitWays + part) * Acc<C>::NS
-                     : a.gacc + j * Acc<C>::NS;
+                     : a.gacc + gi * Acc<C>::NS;
   if (Acc<C>::NS == 32 || (lane & 1) == 0) dst[slot] = sum;
   (void)fr;
   }  // work loop
@@ -476,31 +479,47 @@ bwd_brute_kernel(BwdArgs a) {
   if (Acc<C>::NS == 32 || (lane & 1) == 0) a.gacc[gi * Acc<C>::NS + slot] = sum;
 }
 
-// Gradients of every processed Gaussian from its sums, one thread each.
-// Grid path: position j of the order holds Gaussian order[j] (j < n_live);
-// brute force: position j is Gaussian j.
+// The split Gaussians' sums: their kSplitWays parts added in part order,
+// into gacc at the Gaussian's id (one thread per split Gaussian).
 template <int C>
-__global__ void bwd_epilogue_kernel(BwdArgs a, int brute) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void bwd_split_combine_kernel(BwdArgs a) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (index_unusable(a.header)) return;
-  const int64_t count = brute ? a.n : (int64_t)a.header->n_live;
-  if (j >= count) return;
-  const int64_t gi = brute ? j : a.order[j];
+  const int64_t n_split = min((int64_t)a.header->n_huge, kSplitMax);
+  if (s >= n_split) return;
+  const int64_t gi = a.order[(int64_t)a.header->n_small + s];
+  float v[Acc<C>::NS];
+  const float* p = a.bpart + s * kSplitWays * Acc<C>::NS;
+#pragma unroll
+  for (int i = 0; i < Acc<C>::NS; ++i) v[i] = p[i];
+  for (int b = 1; b < kSplitWays; ++b)
+#pragma unroll
+    for (int i = 0; i < Acc<C>::NS; ++i) v[i] += p[b * Acc<C>::NS + i];
+  float4* dst = reinterpret_cast<float4*>(a.gacc + gi * Acc<C>::NS);
+#pragma unroll
+  for (int i = 0; i < Acc<C>::NS / 4; ++i)
+    dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+
+// Gradients of every Gaussian from its sums, one thread per Gaussian id (so
+// that every read and write is coalesced). Gaussians the pair loop did not
+// visit (no hit point in reach) get zero gradients.
+template <int C>
+__global__ void bwd_epilogue_kernel(BwdArgs a) {
+  const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= a.n || index_unusable(a.header)) return;
   Acc<C> acc;
-  const int64_t n_small = brute ? 0 : (int64_t)a.header->n_small;
-  const int64_t n_split = brute ? 0 : min((int64_t)a.header->n_huge, kSplitMax);
-  if (j >= n_small && j < n_small + n_split) {
-    // a split Gaussian: its parts' sums, in part order
-    float s[Acc<C>::NS];
-    const float* p = a.bpart + (j - n_small) * kSplitWays * Acc<C>::NS;
+  if (a.glive[gi]) {
+    const float4* src = reinterpret_cast<const float4*>(a.gacc + gi * Acc<C>::NS);
+    float v[Acc<C>::NS];
 #pragma unroll
-    for (int i = 0; i < Acc<C>::NS; ++i) s[i] = p[i];
-    for (int b = 1; b < kSplitWays; ++b)
-#pragma unroll
-      for (int i = 0; i < Acc<C>::NS; ++i) s[i] += p[b * Acc<C>::NS + i];
-    acc.from_array(s);
+    for (int i = 0; i < Acc<C>::NS / 4; ++i) {
+      const float4 t = src[i];
+      v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+    }
+    acc.from_array(v);
   } else {
-    acc.from_array(a.gacc + j * Acc<C>::NS);
+    acc.zero();
   }
   const Frame fr = gaussian_frame(a.quat, a.logscale, a.n, gi);
   bwd_epilogue<C>(a, gi, fr, acc);
@@ -533,7 +552,12 @@ cudaError_t launch_c(const BwdArgs& a, const IndexDims& d, bool psi, const Kerne
     else bwd_grid_kernel<C, false><<<pblocks, kBwdThreads, 0, stream>>>(a);
   }
   if (ev.stop && (e = cudaEventRecord(ev.stop, stream)) != cudaSuccess) return e;
-  bwd_epilogue_kernel<C><<<(unsigned)((a.n + 255) / 256), 256, 0, stream>>>(a, d.brute ? 1 : 0);
+  if (!d.brute) {
+    const int64_t max_split = std::min<int64_t>(a.n, kSplitMax);
+    bwd_split_combine_kernel<C><<<(unsigned)((max_split + 127) / 128), 128, 0, stream>>>(a);
+    note_launches(1);
+  }
+  bwd_epilogue_kernel<C><<<(unsigned)((a.n + 255) / 256), 256, 0, stream>>>(a);
   note_launches(2);
   return cudaGetLastError();
 }
@@ -568,6 +592,7 @@ cudaError_t launch_backward(const IndexDims& d, const IndexBuffers& b, const gpf
   a.m = q.m;
   a.qrec = b.qrec;
   a.gacc = b.gacc;
+  a.glive = b.glive;
   a.bpart = b.bpart;
   a.rec = b.rec;
   a.box = b.box;

@@ -30,6 +30,8 @@ constexpr int kThreads = 256;
 // Boxes with more cells than this on their level are refused (overflow flag).
 constexpr int64_t kMaxBoxCells = int64_t(1) << 16;
 constexpr uint32_t kNoBox = 0xffffffffu;
+// gmask of a box of more than 31 cells: emit tests every cell's occupancy bit.
+constexpr uint32_t kMaskAll = 0xffffffffu;
 
 __device__ __forceinline__ bool occupied(const uint32_t* occ, uint32_t b) {
   return (occ[b >> 5] >> (b & 31u)) & 1u;
@@ -126,7 +128,8 @@ __global__ void quantize_bf16_kernel(gpf_field src, gpf_field dst) {
 __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brute,
                                   float* __restrict__ rec, int rs, uint4* __restrict__ box,
                                   const uint32_t* __restrict__ occ,
-                                  uint32_t* __restrict__ gcount,
+                                  uint32_t* __restrict__ gcount, uint8_t* __restrict__ glive,
+                                  uint32_t* __restrict__ gmask,
                                   uint32_t* __restrict__ okey, uint32_t* __restrict__ oval,
                                   DeviceHeader* header) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -198,10 +201,34 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
         box[g] = make_uint4(lx | ((uint32_t)L << 20), ly, lz, sx | (sy << 8) | (sz << 16));
         rv[3] = rec_radius_with_level(rv[3], (uint32_t)L);
         level_bit = 1u << L;
-        for (uint32_t iz = lz; iz <= lz + sz; ++iz)
-          for (uint32_t iy = ly; iy <= ly + sy; ++iy)
-            for (uint32_t ix = lx; ix <= lx + sx; ++ix)
-              cnt += occupied(occ, bucket_of(grid, L, ix, iy, iz)) ? 1u : 0u;
+        // bit c of the mask: the c-th cell of the box (x fastest) holds a
+        // hit point; emit walks the set bits only
+        uint32_t mask = 0;
+        if (sx <= 2 && sy <= 2 && sz <= 2) {
+          // at most 3 x 3 x 3 cells: the nine occupancy reads of a z slice
+          // are independent and go out together
+          for (uint32_t dz = 0; dz <= sz; ++dz) {
+#pragma unroll
+            for (uint32_t j = 0; j < 9; ++j) {
+              const uint32_t dy = j / 3, dx = j % 3;
+              if (dy <= sy && dx <= sx &&
+                  occupied(occ, bucket_of(grid, L, lx + dx, ly + dy, lz + dz))) {
+                ++cnt;
+                mask |= 1u << ((dz * (sy + 1) + dy) * (sx + 1) + dx);
+              }
+            }
+          }
+        } else {
+          uint32_t c = 0;
+          for (uint32_t iz = lz; iz <= lz + sz; ++iz)
+            for (uint32_t iy = ly; iy <= ly + sy; ++iy)
+              for (uint32_t ix = lx; ix <= lx + sx; ++ix, ++c)
+                if (occupied(occ, bucket_of(grid, L, ix, iy, iz))) {
+                  ++cnt;
+                  if (c < 32) mask |= 1u << c;
+                }
+        }
+        gmask[g] = vol <= 31 ? mask : kMaskAll;
       }
       live = cnt > 0;
       if (grid.blevel >= 0) ++cnt;      // the centre entry (kept for every Gaussian)
@@ -211,6 +238,7 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
       huge = live && cls == 1 && size_rank == 0;
     }
     okey[g] = mkey | (size_rank << size_shift) | (cls << cls_shift);
+    glive[g] = (brute || live) ? 1 : 0;
     float4* r4 = reinterpret_cast<float4*>(rec + g * rs);
 #pragma unroll
     for (int v = 0; v < 4; ++v)
@@ -257,16 +285,25 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
     val[i] = (uint32_t)i;
   }
   if (mark) {
-    // occupancy bits of every level; lanes in the same cell of a level (all
-    // of a warp's on the coarse ones) set its bit once
-    for (int L = 0; L < grid.levels; ++L) {
-      const uint32_t b = active ? bucket_of(grid, L, c0[0] >> L, c0[1] >> L, c0[2] >> L)
-                                : 0xffffffffu;
+    // occupancy bits of every level: all levels' words are read at once,
+    // then the lanes in the same cell of a level (all of a warp's on the
+    // coarse ones) set its bit once, where it is not set yet
+    uint32_t bkt[kMaxLevels], word[kMaxLevels];
+#pragma unroll
+    for (int L = 0; L < kMaxLevels; ++L) {
+      bkt[L] = active && L < grid.levels
+                   ? bucket_of(grid, L, c0[0] >> L, c0[1] >> L, c0[2] >> L)
+                   : 0xffffffffu;
+      word[L] = bkt[L] != 0xffffffffu ? occ[bkt[L] >> 5] : 0xffffffffu;
+    }
+#pragma unroll
+    for (int L = 0; L < kMaxLevels; ++L) {
+      if (L >= grid.levels) break;
+      const uint32_t b = bkt[L];
       const uint32_t same = __match_any_sync(kFullMask, b);
-      if (active && (same & lanemask_lt()) == 0) {
-        const uint32_t bit = 1u << (b & 31u);
-        if (!(occ[b >> 5] & bit)) atomicOr(&occ[b >> 5], bit);
-      }
+      const uint32_t bit = 1u << (b & 31u);
+      if (b != 0xffffffffu && (same & lanemask_lt()) == 0 && !(word[L] & bit))
+        atomicOr(&occ[b >> 5], bit);
     }
   }
   // per-cell counts: one atomic per distinct cell of the warp (neighbouring
@@ -283,41 +320,56 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
 // consecutive entries; the pair loops take only the first.
 __global__ void emit_kernel(Grid grid, int64_t n, int64_t p_max, const float* __restrict__ rec,
                             int rs, const uint4* __restrict__ box,
-                            const uint32_t* __restrict__ occ, const uint32_t* __restrict__ goffset,
+                            const uint32_t* __restrict__ occ, const uint32_t* __restrict__ gmask,
+                            const uint32_t* __restrict__ goffset,
                             uint32_t* __restrict__ gkey, uint32_t* __restrict__ gval,
+                            int passes, uint32_t* __restrict__ digit_counts,
                             DeviceHeader* header) {
+  // the digit counts of the entry sort, added here as the keys are written
+  __shared__ uint32_t cnt[kSortMaxPasses * kSortBins];
+  for (int i = threadIdx.x; i < passes * kSortBins; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g == 0 && (int64_t)header->n_pairs > p_max) atomicExch(&header->overflow, 1u);
-  if (g >= n) return;
-  const uint4 bw = box[g];
-  int64_t pos = goffset[g];
-  if (grid.blevel >= 0) {
-    // the centre entry: the cell of the mean on the centre level
-    const float* r = rec + g * rs;
-    const int Lb = grid.blevel;
-    const CellHash h = cell_hash(grid, Lb, coord0(r[0], grid.ox, grid.inv_cell0, grid.max0x) >> Lb,
-                                 coord0(r[1], grid.oy, grid.inv_cell0, grid.max0y) >> Lb,
-                                 coord0(r[2], grid.oz, grid.inv_cell0, grid.max0z) >> Lb,
-                                 kCentreSalt);
-    if (pos < p_max) {
-      gkey[pos] = h.bucket;
-      gval[pos] = (uint32_t)g | h.tag;
+  auto put = [&](int64_t pos, uint32_t bucket, uint32_t v) {
+    if (pos >= p_max) return;
+    gkey[pos] = bucket;
+    gval[pos] = v;
+    for (int p = 0; p < passes; ++p) atomicAdd(&cnt[p * kSortBins + ((bucket >> (8 * p)) & 255u)], 1u);
+  };
+  if (g < n) {
+    const uint4 bw = box[g];
+    int64_t pos = goffset[g];
+    if (grid.blevel >= 0) {
+      // the centre entry: the cell of the mean on the centre level
+      const float* r = rec + g * rs;
+      const int Lb = grid.blevel;
+      const CellHash h = cell_hash(grid, Lb,
+                                   coord0(r[0], grid.ox, grid.inv_cell0, grid.max0x) >> Lb,
+                                   coord0(r[1], grid.oy, grid.inv_cell0, grid.max0y) >> Lb,
+                                   coord0(r[2], grid.oz, grid.inv_cell0, grid.max0z) >> Lb,
+                                   kCentreSalt);
+      put(pos, h.bucket, (uint32_t)g | h.tag);
+      ++pos;
     }
-    ++pos;
+    if (bw.x != kNoBox) {
+      const LevelBox b = unpack_box(bw);
+      const uint32_t mask = gmask[g];
+      uint32_t c = 0;
+      for (uint32_t iz = b.lz; iz <= b.hz; ++iz)
+        for (uint32_t iy = b.ly; iy <= b.hy; ++iy)
+          for (uint32_t ix = b.lx; ix <= b.hx; ++ix, ++c) {
+            if (mask != kMaskAll && !((mask >> c) & 1u)) continue;
+            const CellHash h = cell_hash(grid, b.level, ix, iy, iz);
+            if (mask == kMaskAll && !occupied(occ, h.bucket)) continue;
+            put(pos, h.bucket, (uint32_t)g | h.tag);
+            ++pos;
+          }
+    }
   }
-  if (bw.x == kNoBox) return;
-  const LevelBox b = unpack_box(bw);
-  for (uint32_t iz = b.lz; iz <= b.hz; ++iz)
-    for (uint32_t iy = b.ly; iy <= b.hy; ++iy)
-      for (uint32_t ix = b.lx; ix <= b.hx; ++ix) {
-        const CellHash h = cell_hash(grid, b.level, ix, iy, iz);
-        if (!occupied(occ, h.bucket)) continue;
-        if (pos < p_max) {
-          gkey[pos] = h.bucket;
-          gval[pos] = (uint32_t)g | h.tag;
-        }
-        ++pos;
-      }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kSortBins; i += blockDim.x)
+    if (cnt[i]) atomicAdd(&digit_counts[i], cnt[i]);
 }
 
 // [start, end) of every non-empty bucket from the boundaries of the sorted
@@ -383,7 +435,7 @@ cudaError_t launch_build(const IndexDims& d, const IndexBuffers& b, const gpf_fi
   if (f.n > 0) {
     preprocess_kernel<<<blocks_for(f.n), kThreads, 0, stream>>>(
         f, grid, d.cutoff, d.brute ? 1 : 0, b.rec, rec_stride(d.channels), b.box, b.occ,
-        b.gcount, b.okey[0], b.oval[0], b.header);
+        b.gcount, b.glive, b.gmask, b.okey[0], b.oval[0], b.header);
     note_launches(1);
   }
   // 3. hit points sorted by query-level cell (inactive ones last), cell starts
@@ -401,12 +453,15 @@ cudaError_t launch_build(const IndexDims& d, const IndexBuffers& b, const gpf_fi
   // 5. (bucket, Gaussian) entries: scan, emit, sort, bucket starts
   e = exclusive_scan_u32(b.gcount, b.goffset, f.n, &b.header->n_pairs, b.scan_ws, stream);
   if (e != cudaSuccess) return e;
-  emit_kernel<<<blocks_for(f.n), kThreads, 0, stream>>>(grid, f.n, d.p_max, b.rec,
-                                                        rec_stride(d.channels), b.box, b.occ,
-                                                        b.goffset, b.gkey[0], b.gval[0], b.header);
+  e = radix_sort_clear_counts(b.gsort_ws, stream);
+  if (e != cudaSuccess) return e;
+  emit_kernel<<<blocks_for(f.n), kThreads, 0, stream>>>(
+      grid, f.n, d.p_max, b.rec, rec_stride(d.channels), b.box, b.occ, b.gmask, b.goffset,
+      b.gkey[0], b.gval[0], radix_sort_passes(grid.hash_bits), radix_sort_counts(b.gsort_ws),
+      b.header);
   note_launches(1);
   e = radix_sort_pairs(b.gkey[0], b.gval[0], b.gkey[1], b.gval[1], d.p_max, &b.header->n_pairs,
-                       grid.hash_bits, b.gsort_ws, &b.header->stalled, stream);
+                       grid.hash_bits, b.gsort_ws, &b.header->stalled, stream, true);
   if (e != cudaSuccess) return e;
   // bucket ranges from the boundaries of the sorted keys
   e = cudaMemsetAsync(b.brange, 0, sizeof(uint2) * (size_t)grid.n_buckets, stream);

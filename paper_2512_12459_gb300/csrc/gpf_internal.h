@@ -34,9 +34,16 @@ int radix_sort_passes(int bits);
 // key bits [0, bits). The result is in (k0, v0) after an even number of
 // passes, in (k1, v1) after an odd one. *stalled (device) is set to 1 if a
 // bounded wait of the single-pass sort gave up (the output is then invalid).
+// counted: the kernel that wrote the keys has already added their digit
+// counts, digit d of pass p at radix_sort_counts(ws)[p * kSortBins + d],
+// into counts that radix_sort_clear_counts zeroed before it ran.
+constexpr int kSortBins = 256;
+constexpr int kSortMaxPasses = 4;
 cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                              int64_t n_max, const uint32_t* d_n, int bits, void* ws,
-                             uint32_t* stalled, cudaStream_t stream);
+                             uint32_t* stalled, cudaStream_t stream, bool counted = false);
+uint32_t* radix_sort_counts(void* ws);
+cudaError_t radix_sort_clear_counts(void* ws, cudaStream_t stream);
 // The failure-detection probe of the single-pass sort's bounded wait (a
 // look-back whose predecessor tile is never processed): buffer size, launch.
 size_t sort_wait_probe_bytes();
@@ -49,6 +56,8 @@ struct IndexBuffers {
   float* rec;           // [N_max * rec_stride] Gaussian records
   uint4* box;           // [N_max] level boxes
   uint32_t* gcount;     // [N_max] entries per Gaussian
+  uint8_t* glive;       // [N_max] 1 if the backward visits the Gaussian (a hit point in reach)
+  uint32_t* gmask;      // [N_max] occupied cells of the level box (boxes of <= 31 cells)
   uint32_t* goffset;    // [N_max] exclusive scan of gcount
   uint32_t* okey[2];    // [N_max] query-level key of each mean (sort ping-pong)
   uint32_t* oval[2];    // [N_max] Gaussian ids in that order

@@ -11,56 +11,95 @@ namespace gpf {
 
 namespace {
 
-constexpr int kMseThreads = 256;
+constexpr int kMseThreads = 512;
 constexpr int kMsePerBlock = 4096;  // hit points per partial sum
+constexpr int kMsePerThread = kMsePerBlock / kMseThreads;
+constexpr int kMseFinalThreads = 256;
 
-__global__ void mse_partial_kernel(int64_t m, int channels, const float* __restrict__ out,
-                                   const float* __restrict__ target,
-                                   const uint8_t* __restrict__ valid, float* __restrict__ psum,
-                                   uint32_t* __restrict__ pcnt) {
-  __shared__ float ssum[kMseThreads];
-  __shared__ uint32_t scnt[kMseThreads];
-  const int64_t base = (int64_t)blockIdx.x * kMsePerBlock;
+// Per block of kMsePerBlock hit points: the sum of squared differences over
+// its valid points (float32; every thread's points in order, then a fixed
+// reduction tree) and their count. The points' loads are all issued before
+// the arithmetic.
+__global__ void __launch_bounds__(kMseThreads)
+mse_partial_kernel(int64_t m, int channels, const float* __restrict__ out,
+                   const float* __restrict__ target, const uint8_t* __restrict__ valid,
+                   float* __restrict__ psum, uint32_t* __restrict__ pcnt) {
+  __shared__ float wsum[kMseThreads / kWarp];
+  __shared__ uint32_t wcnt[kMseThreads / kWarp];
+  const int64_t base = (int64_t)blockIdx.x * kMsePerBlock + threadIdx.x;
+  bool ok[kMsePerThread];
+#pragma unroll
+  for (int r = 0; r < kMsePerThread; ++r) {
+    const int64_t q = base + (int64_t)r * kMseThreads;
+    ok[r] = q < m && (valid == nullptr || valid[q] != 0);
+  }
   float s = 0.0f;
   uint32_t cnt = 0;
-  for (int i = threadIdx.x; i < kMsePerBlock; i += kMseThreads) {
-    const int64_t q = base + i;
-    if (q >= m) break;
-    if (valid && !valid[q]) continue;
-    ++cnt;
-    for (int c = 0; c < channels; ++c) {
-      const float d = out[(int64_t)c * m + q] - target[(int64_t)c * m + q];
-      s = fmaf(d, d, s);
+  for (int c = 0; c < channels; ++c) {
+    float d[kMsePerThread];
+#pragma unroll
+    for (int r = 0; r < kMsePerThread; ++r) {
+      const int64_t i = (int64_t)c * m + base + (int64_t)r * kMseThreads;
+      d[r] = ok[r] ? out[i] - target[i] : 0.0f;
+    }
+#pragma unroll
+    for (int r = 0; r < kMsePerThread; ++r) s = fmaf(d[r], d[r], s);
+  }
+#pragma unroll
+  for (int r = 0; r < kMsePerThread; ++r) cnt += ok[r] ? 1u : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(kFullMask, s, o);
+    cnt += __shfl_xor_sync(kFullMask, cnt, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    wsum[warp] = s;
+    wcnt[warp] = cnt;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    s = lane < kMseThreads / kWarp ? wsum[lane] : 0.0f;
+    cnt = lane < kMseThreads / kWarp ? wcnt[lane] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(kFullMask, s, o);
+      cnt += __shfl_xor_sync(kFullMask, cnt, o);
+    }
+    if (lane == 0) {
+      psum[blockIdx.x] = s;
+      pcnt[blockIdx.x] = cnt;
     }
   }
-  ssum[threadIdx.x] = s;
-  scnt[threadIdx.x] = cnt;
+}
+
+// The partials summed in float64 in a fixed order (thread t takes partials
+// t, t + 256, ..., then a fixed tree): loss = sum / count, scale = 2 / count.
+__global__ void __launch_bounds__(kMseFinalThreads)
+mse_final_kernel(int64_t nb, const float* __restrict__ psum, const uint32_t* __restrict__ pcnt,
+                 float* __restrict__ loss, float* __restrict__ scale) {
+  __shared__ double ss[kMseFinalThreads];
+  __shared__ unsigned long long sc[kMseFinalThreads];
+  double s = 0.0;
+  unsigned long long c = 0;
+  for (int64_t b = threadIdx.x; b < nb; b += kMseFinalThreads) {
+    s += psum[b];
+    c += pcnt[b];
+  }
+  ss[threadIdx.x] = s;
+  sc[threadIdx.x] = c;
   __syncthreads();
-  for (int o = kMseThreads / 2; o > 0; o >>= 1) {
+  for (int o = kMseFinalThreads / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) {
-      ssum[threadIdx.x] += ssum[threadIdx.x + o];
-      scnt[threadIdx.x] += scnt[threadIdx.x + o];
+      ss[threadIdx.x] += ss[threadIdx.x + o];
+      sc[threadIdx.x] += sc[threadIdx.x + o];
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    psum[blockIdx.x] = ssum[0];
-    pcnt[blockIdx.x] = scnt[0];
+    *loss = sc[0] ? (float)(ss[0] / (double)sc[0]) : 0.0f;
+    *scale = sc[0] ? (float)(2.0 / (double)sc[0]) : 0.0f;
   }
-}
-
-// One thread sums the partials in block order (fixed order, float64).
-__global__ void mse_final_kernel(int64_t nb, const float* __restrict__ psum,
-                                 const uint32_t* __restrict__ pcnt, float* __restrict__ loss,
-                                 float* __restrict__ scale) {
-  double s = 0.0;
-  uint64_t c = 0;
-  for (int64_t b = 0; b < nb; ++b) {
-    s += psum[b];
-    c += pcnt[b];
-  }
-  *loss = c ? (float)(s / (double)c) : 0.0f;
-  *scale = c ? (float)(2.0 / (double)c) : 0.0f;
 }
 
 __global__ void mse_grad_kernel(int64_t m, int channels, const float* __restrict__ out,
@@ -164,7 +203,7 @@ cudaError_t launch_mse(int64_t m, int channels, const float* out, const float* t
                                                                  psum, pcnt);
     note_launches(1);
   }
-  mse_final_kernel<<<1, 1, 0, stream>>>(nb, psum, pcnt, loss, scale);
+  mse_final_kernel<<<1, kMseFinalThreads, 0, stream>>>(nb, psum, pcnt, loss, scale);
   note_launches(1);
   if (m > 0) {
     mse_grad_kernel<<<(unsigned)((m + 255) / 256), 256, 0, stream>>>(m, channels, out, target,

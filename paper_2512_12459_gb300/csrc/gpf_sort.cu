@@ -134,7 +134,8 @@ __device__ __forceinline__ uint32_t load_count(const uint32_t* d_n, int64_t n_ma
 
 // ---- single-pass (decoupled look-back) sort
 
-constexpr int kMaxPasses = 4;                  // 32-bit keys
+constexpr int kMaxPasses = kSortMaxPasses;     // 32-bit keys
+static_assert(kSortBins == kBins, "8-bit digits");
 constexpr uint32_t kFlagAgg = 1u << 30;        // the tile's own count is published
 constexpr uint32_t kFlagPre = 2u << 30;        // the inclusive prefix is published
 constexpr uint32_t kValMask = kFlagAgg - 1u;
@@ -332,9 +333,15 @@ cudaError_t launch_sort_wait_probe(void* buf, uint32_t spin_limit, uint32_t* sta
   return cudaGetLastError();
 }
 
+uint32_t* radix_sort_counts(void* ws) { return static_cast<uint32_t*>(ws); }
+
+cudaError_t radix_sort_clear_counts(void* ws, cudaStream_t stream) {
+  return cudaMemsetAsync(ws, 0, sizeof(uint32_t) * (kMaxPasses * kBins + kMaxPasses), stream);
+}
+
 cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                              int64_t n_max, const uint32_t* d_n, int bits, void* ws,
-                             uint32_t* stalled, cudaStream_t stream) {
+                             uint32_t* stalled, cudaStream_t stream, bool counted) {
   if (n_max <= 0) return cudaSuccess;
   if (n_max >= kMaxSortN) return cudaErrorInvalidValue;
   const int64_t tiles = radix_tiles(n_max);
@@ -345,13 +352,15 @@ cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t*
   uint32_t* counters = ghist + kMaxPasses * kBins;          // [kMaxPasses]
   p += align_up(sizeof(uint32_t) * (kMaxPasses * kBins + kMaxPasses));
   uint32_t* status = reinterpret_cast<uint32_t*>(p);        // [passes][tiles][kBins]
-  cudaError_t e = cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * (kMaxPasses * kBins + kMaxPasses),
-                                  stream);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if (!counted && (e = radix_sort_clear_counts(ws, stream)) != cudaSuccess) return e;
   e = cudaMemsetAsync(status, 0, sizeof(uint32_t) * (size_t)passes * tiles * kBins, stream);
   if (e != cudaSuccess) return e;
-  const unsigned hblocks = (unsigned)std::min<int64_t>(tiles, 1024);
-  onesweep_hist_kernel<<<hblocks, kSortThreads, 0, stream>>>(k0, d_n, n_max, passes, ghist);
+  if (!counted) {
+    const unsigned hblocks = (unsigned)std::min<int64_t>(tiles, 1024);
+    onesweep_hist_kernel<<<hblocks, kSortThreads, 0, stream>>>(k0, d_n, n_max, passes, ghist);
+    note_launches(1);
+  }
   uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
   for (int pass = 0; pass < passes; ++pass) {
     onesweep_pass_kernel<<<(unsigned)tiles, kSortThreads, 0, stream>>>(
@@ -361,7 +370,7 @@ cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t*
     tmp = ki; ki = ko; ko = tmp;
     tmp = vi; vi = vo; vo = tmp;
   }
-  note_launches(1 + passes);
+  note_launches(passes);
   return cudaGetLastError();
 }
 
