@@ -27,6 +27,30 @@ namespace gpf {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kBlockWarps = kThreads / kWarp;
+
+// The sum over a block of kThreads threads of up to four per-thread counts,
+// each in [0, 2^32); thread 0 gets the sums. The header counters take one
+// atomic per block: atomics to one address are serialised, so per-warp
+// updates from 10^6 threads cost tens of microseconds.
+__device__ __forceinline__ void block_counts(uint32_t (&v)[4], uint32_t (*s)[4]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = __reduce_add_sync(kFullMask, v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      uint32_t t = 0;
+      for (int w = 0; w < kBlockWarps; ++w) t += s[w][k];
+      v[k] = t;
+    }
+  }
+}
 // Boxes with more cells than this on their level are refused (overflow flag).
 constexpr int64_t kMaxBoxCells = int64_t(1) << 16;
 constexpr uint32_t kNoBox = 0xffffffffu;
@@ -246,14 +270,21 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
     for (int c = 16; c < rs; ++c)
       rec[g * rs + c] = c - 13 < f.channels ? spec[(int64_t)(c - 13) * n + g] : 0.0f;
   }
+  __shared__ uint32_t s_cnt[kBlockWarps][4];
+  __shared__ uint32_t s_mask;
+  if (threadIdx.x == 0) s_mask = 0;
+  __syncthreads();
   const uint32_t m = __reduce_or_sync(kFullMask, level_bit);
-  if ((threadIdx.x & 31) == 0 && m) atomicOr(&header->level_mask, m);
-  const uint32_t blive = __ballot_sync(kFullMask, live);
-  const uint32_t bsmall = __ballot_sync(kFullMask, small);
-  if ((threadIdx.x & 31) == 0 && blive) atomicAdd(&header->n_live, __popc(blive));
-  if ((threadIdx.x & 31) == 0 && bsmall) atomicAdd(&header->n_small, __popc(bsmall));
-  const uint32_t bhuge = __ballot_sync(kFullMask, huge);
-  if ((threadIdx.x & 31) == 0 && bhuge) atomicAdd(&header->n_huge, __popc(bhuge));
+  if ((threadIdx.x & 31) == 0 && m) atomicOr(&s_mask, m);
+  uint32_t v[4] = {live ? 1u : 0u, small ? 1u : 0u, huge ? 1u : 0u, 0u};
+  block_counts(v, s_cnt);      // its __syncthreads also orders s_mask
+  if (threadIdx.x == 0) {
+    // the level bits: only when this block adds one (the mask fills up early)
+    if (s_mask & ~*(volatile uint32_t*)&header->level_mask) atomicOr(&header->level_mask, s_mask);
+    if (v[0]) atomicAdd(&header->n_live, v[0]);
+    if (v[1]) atomicAdd(&header->n_small, v[1]);
+    if (v[2]) atomicAdd(&header->n_huge, v[2]);
+  }
 }
 
 __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
@@ -269,10 +300,24 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
   if (i < m) {
     // hemisphere gate n . w_o > 0, summed in float64 in a fixed order (the
     // three products of float32 values are exact in float64)
-    double d = __dadd_rn(__dadd_rn(__dmul_rn((double)nrm[i], (double)wo[i]),
-                                   __dmul_rn((double)nrm[m + i], (double)wo[m + i])),
-                         __dmul_rn((double)nrm[2 * m + i], (double)wo[2 * m + i]));
-    active = d > 0.0 && (valid == nullptr || valid[i] != 0);
+    // hemisphere gate n . w_o > 0: the float32 sum when it is far enough
+    // from zero for its sign to be exact (its error is below 3 u sum|a_i b_i|,
+    // u = 2^-24), else the float64 sum (the three products of float32 values
+    // are exact in float64, so its sign is exact)
+    const float a0 = nrm[i], a1 = nrm[m + i], a2 = nrm[2 * m + i];
+    const float b0 = wo[i], b1 = wo[m + i], b2 = wo[2 * m + i];
+    const float d32 = fmaf(a0, b0, fmaf(a1, b1, a2 * b2));
+    const float mag = fabsf(a0 * b0) + fabsf(a1 * b1) + fabsf(a2 * b2);
+    bool facing;
+    if (fabsf(d32) > 1e-6f * mag && mag > 1e-30f) {
+      facing = d32 > 0.0f;
+    } else {
+      const double d = __dadd_rn(__dadd_rn(__dmul_rn((double)a0, (double)b0),
+                                           __dmul_rn((double)a1, (double)b1)),
+                                 __dmul_rn((double)a2, (double)b2));
+      facing = d > 0.0;
+    }
+    active = facing && (valid == nullptr || valid[i] != 0);
     if (active) {
       const uint32_t cx = coord0(x[i], grid.ox, grid.inv_cell0, grid.max0x);
       const uint32_t cy = coord0(x[m + i], grid.oy, grid.inv_cell0, grid.max0y);
@@ -310,8 +355,10 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
   // pixels share query cells)
   const uint32_t peers = __match_any_sync(kFullMask, active ? k : 0xffffffffu);
   if (active && (peers & lanemask_lt()) == 0) atomicAdd(&qcount[k], (uint32_t)__popc(peers));
-  const uint32_t ballot = __ballot_sync(kFullMask, active);
-  if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(&header->n_active, __popc(ballot));
+  __shared__ uint32_t s_cnt[kBlockWarps][4];
+  uint32_t v[4] = {active ? 1u : 0u, 0u, 0u, 0u};
+  block_counts(v, s_cnt);
+  if (threadIdx.x == 0 && v[0]) atomicAdd(&header->n_active, v[0]);
 }
 
 // One (bucket, Gaussian) entry per occupied cell of every Gaussian's level

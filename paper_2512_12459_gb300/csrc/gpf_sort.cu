@@ -6,9 +6,9 @@
 // Adinets and Merrill, "Onesweep", 2022):
 //   0. one kernel counts the digits of every pass over all keys (the global
 //      digit counts do not depend on the order the earlier passes leave);
-//   1. per pass, one kernel: a block claims the next tile of 2048 keys from
+//   1. per pass, one kernel: a block claims the next tile of 3072 keys from
 //      an atomic counter (so every earlier tile is held by a block that is
-//      already running); each warp ranks its own 256 keys, 32 at a time
+//      already running); each warp ranks its own 384 keys, 32 at a time
 //      (__match_any_sync groups, per-warp digit counters in shared memory);
 //      the block publishes its digit counts, orders its keys by digit in
 //      shared memory, adds up the counts the earlier tiles published for each
@@ -39,8 +39,8 @@ constexpr int kScanTile = kScanThreads * kScanPerThread;  // 2048
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / kWarp;
-constexpr int kSortPerThread = 8;
-constexpr int kSortTile = kSortThreads * kSortPerThread;  // 2048
+constexpr int kSortPerThread = 12;
+constexpr int kSortTile = kSortThreads * kSortPerThread;  // 3072
 constexpr int kBins = 256;
 
 // Exclusive scan across a block of kScanThreads threads; returns the prefix
@@ -175,7 +175,7 @@ onesweep_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __res
                      const uint32_t* __restrict__ ghist, uint32_t* status,
                      uint32_t* tile_counter, uint32_t tile_base, uint32_t spin_limit,
                      uint32_t* stalled) {
-  constexpr int kWarpKeys = kSortPerThread * kWarp;   // each warp ranks its own 256 keys
+  constexpr int kWarpKeys = kSortPerThread * kWarp;   // each warp ranks its own 384 keys
   __shared__ uint32_t s_keys[kSortTile];
   __shared__ uint32_t s_vals[kSortTile];
   __shared__ uint32_t wcnt[kSortWarps][kBins];   // digit counts of each warp, then its bases
@@ -196,7 +196,7 @@ onesweep_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __res
   if (base >= (int64_t)n) return;                    // the whole block
   const int tile_n = (int)min((int64_t)kSortTile, (int64_t)n - base);
 
-  // 1. ranks inside the warp's 256 keys (taken 32 at a time in order):
+  // 1. ranks inside the warp's 384 keys (taken 32 at a time in order):
   //    (rank << 9) | digit, digit kBins for the positions past the tile
   uint32_t rd[kSortPerThread];
 #pragma unroll

@@ -1,5 +1,5 @@
 """The index build's radix sort through the C ABI (gpf_sort_pairs): stable
-order against numpy's stable argsort on sizes around the 2048-key tile and
+order against numpy's stable argsort on sizes around the 3072-key tile and
 up to millions of keys, and the bounded wait of its single-pass kernel
 (gpf_test_sort_wait_timeout: a look-back whose predecessor never publishes
 gives up, reports GPF_ERR_TIMEOUT and leaves the context usable)."""
@@ -48,7 +48,7 @@ def _run(gpf, keys_u32, bits):
     assert np.array_equal(got_v, vals[order])
 
 
-@pytest.mark.parametrize("n", [1, 31, 2047, 2048, 2049, 6143, 100_003])
+@pytest.mark.parametrize("n", [1, 31, 2048, 3071, 3072, 3073, 9215, 100_003])
 @pytest.mark.parametrize("bits", [8, 13, 24, 32])
 def test_sort_small_sizes_every_pass_count(gpf, n, bits):
     rng = np.random.default_rng(n * 100 + bits)
@@ -62,7 +62,7 @@ def test_sort_key_distributions(gpf, kind):
 
 
 def test_sort_many_tiles(gpf):
-    """5 M pairs: 2,442 tiles per pass, 3 passes (the entry sort's size)."""
+    """5 M pairs: 1,628 tiles per pass, 3 passes (the entry sort's size)."""
     rng = np.random.default_rng(11)
     _run(gpf, _keys("uniform", 5_000_000, 24, rng), 24)
 
