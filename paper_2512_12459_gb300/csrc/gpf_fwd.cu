@@ -371,17 +371,33 @@ fwd_kernel(FwdArgs a) {
         uint32_t o_first = 0, o_start = 0, o_tag = 0;
         float qx = 0.0f, qy = 0.0f, qz = 0.0f;
         uint32_t carry = 0xffffffffu;
+        // owner of item i: the first lane whose inclusive end exceeds i
+        // (kWarp: none); the entry word of the next chunk is fetched while
+        // the current chunk is evaluated
+        auto owner_of = [&](uint32_t i) {
+          int o = 0;
+#pragma unroll
+          for (int st = 16; st > 0; st >>= 1) {
+            const uint32_t pe = __shfl_sync(kFullMask, incl, o + st - 1);
+            if (pe <= i) o += st;
+          }
+          return i < total ? o : kWarp;
+        };
+        auto entry_of = [&](uint32_t i, int o) {
+          const int src = o & (kWarp - 1);
+          const uint32_t first = __shfl_sync(kFullMask, incl - len, src);
+          const uint32_t start = __shfl_sync(kFullMask, rg.x, src);
+          return i < total ? __ldg(a.gval + start + (i - first)) : 0u;
+        };
+        int own_n = owner_of(lane);
+        uint32_t v_n = entry_of(lane, own_n);
         for (uint32_t b = 0; b < total; b += kWarp) {
           const uint32_t i = b + lane;
           const bool live = i < total;
-          // owner: the first lane whose inclusive end exceeds i (kWarp: none)
-          int own = 0;
-#pragma unroll
-          for (int st = 16; st > 0; st >>= 1) {
-            const uint32_t pe = __shfl_sync(kFullMask, incl, own + st - 1);
-            if (pe <= i) own += st;
-          }
-          if (!live) own = kWarp;
+          const int own = own_n;
+          const uint32_t v = v_n;
+          own_n = owner_of(i + kWarp);
+          v_n = entry_of(i + kWarp, own_n);
           const bool chg = own != cur;
           if (__any_sync(kFullMask, chg)) {
             pooled_flush<C>(s_acc[wib], lane, cur, chg && cur >= 0 && cur < kWarp, pc);
@@ -395,7 +411,6 @@ fwd_kernel(FwdArgs a) {
             cur = own;
           }
           const uint32_t kk = i - o_first;  // position in the owner's list
-          const uint32_t v = live ? __ldg(a.gval + o_start + kk) : 0u;
           // the owner's previous entry is the previous item
           uint32_t vprev = __shfl_up_sync(kFullMask, v, 1);
           if (lane == 0) vprev = carry;
