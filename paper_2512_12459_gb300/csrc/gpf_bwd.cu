@@ -31,6 +31,7 @@ namespace gpf {
 namespace {
 
 constexpr int kBwdWarps = 4;
+constexpr int64_t kGrab = 4;            // work units per atomic of the persistent loop
 constexpr int kBwdThreads = kBwdWarps * kWarp;
 
 struct BwdArgs {
@@ -361,14 +362,17 @@ bwd_grid_kernel(BwdArgs a) {
   const int64_t small_warps = (n_small + kWarp - 1) / kWarp;
   const int64_t n_split = min((int64_t)a.header->n_huge, kSplitMax);
   const int64_t units = small_warps + n_split * kSplitWays + (n_live - n_small - n_split);
-  // persistent: every warp takes the next work unit (32 small Gaussians, one
-  // of the kSplitWays parts of a huge Gaussian, or one large Gaussian) until
-  // none is left
+  // persistent: every warp takes the next kGrab work units (each 32 small
+  // Gaussians, one of the kSplitWays parts of a huge Gaussian, or one large
+  // Gaussian) until none is left; one atomic per kGrab units keeps the work
+  // counter, a single address, from queueing
   for (;;) {
   unsigned long long w_u = 0;
-  if (lane == 0) w_u = atomicAdd(a.next_work, 1ull);
-  const int64_t w = (int64_t)__shfl_sync(kFullMask, w_u, 0);
-  if (w >= units) break;
+  if (lane == 0) w_u = atomicAdd(a.next_work, (unsigned long long)kGrab);
+  const int64_t w0 = (int64_t)__shfl_sync(kFullMask, w_u, 0);
+  if (w0 >= units) break;
+  const int64_t w_end = min(w0 + kGrab, units);
+  for (int64_t w = w0; w < w_end; ++w) {
   if (w < small_warps) {
     const int64_t idx = w * kWarp + lane;
     if (idx < n_small) bwd_lane_gaussian<C, PSI>(a, a.order[idx]);
@@ -454,6 +458,7 @@ bwd_grid_kernel(BwdArgs a) {
                      : a.gacc + gi * Acc<C>::NS;
   if (Acc<C>::NS == 32 || (lane & 1) == 0) dst[slot] = sum;
   (void)fr;
+  }
   }  // work loop
 }
 
