@@ -298,8 +298,6 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
   uint32_t k = grid.key_inactive;
   uint32_t c0[3] = {0u, 0u, 0u};   // level-0 cell of an active hit point
   if (i < m) {
-    // hemisphere gate n . w_o > 0, summed in float64 in a fixed order (the
-    // three products of float32 values are exact in float64)
     // hemisphere gate n . w_o > 0: the float32 sum when it is far enough
     // from zero for its sign to be exact (its error is below 3 u sum|a_i b_i|,
     // u = 2^-24), else the float64 sum (the three products of float32 values
