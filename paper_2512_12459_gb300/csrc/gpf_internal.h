@@ -127,6 +127,12 @@ size_t mse_workspace_bytes(int64_t m);
 cudaError_t launch_mse(int64_t m, int channels, const float* out, const float* target,
                        const uint8_t* valid, float* loss, float* grad, void* ws,
                        cudaStream_t stream);
+// The same three kernels on caller-placed scratch: psum / pcnt of
+// ceil(m / mse_points_per_partial()) partials and one float scale.
+int64_t mse_points_per_partial();
+cudaError_t launch_mse_parts(int64_t m, int channels, const float* out, const float* target,
+                             const uint8_t* valid, float* loss, float* grad, float* psum,
+                             uint32_t* pcnt, float* scale, cudaStream_t stream);
 cudaError_t launch_adam(const gpf_field& params, const gpf_field_grad& g, const gpf_field_grad& m,
                         const gpf_field_grad& v, const gpf_adam_hparams& hp, cudaStream_t stream);
 

@@ -27,8 +27,7 @@ namespace gpf {
 
 namespace {
 
-constexpr int kNoAllocThreads = 256;
-constexpr int kNoAllocPerBlock = 4096;                 // hit points per partial sum
+constexpr int kNoAllocPerBlock = 4096;                 // = mse_points_per_partial()
 constexpr int64_t kNoAllocMaxBlocks = 16384;           // 2^26 hit points at most
 
 // The scratch: partial sums, partial counts and the gradient scale.
@@ -38,69 +37,6 @@ struct NoAllocScratch {
   float scale;
 };
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
-
-__global__ void noalloc_partial_kernel(int64_t m, int channels, const float* __restrict__ out,
-                                       const float* __restrict__ target,
-                                       const uint8_t* __restrict__ valid,
-                                       NoAllocScratch* __restrict__ sc) {
-  __shared__ float ssum[kNoAllocThreads];
-  __shared__ uint32_t scnt[kNoAllocThreads];
-  const int64_t base = (int64_t)blockIdx.x * kNoAllocPerBlock;
-  float s = 0.0f;
-  uint32_t cnt = 0;
-  for (int i = threadIdx.x; i < kNoAllocPerBlock; i += kNoAllocThreads) {
-    const int64_t q = base + i;
-    if (q >= m) break;
-    if (valid && !valid[q]) continue;
-    ++cnt;
-    for (int c = 0; c < channels; ++c) {
-      const float d = out[(int64_t)c * m + q] - target[(int64_t)c * m + q];
-      s = fmaf(d, d, s);
-    }
-  }
-  ssum[threadIdx.x] = s;
-  scnt[threadIdx.x] = cnt;
-  __syncthreads();
-  for (int o = kNoAllocThreads / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      ssum[threadIdx.x] += ssum[threadIdx.x + o];
-      scnt[threadIdx.x] += scnt[threadIdx.x + o];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    sc->psum[blockIdx.x] = ssum[0];
-    sc->pcnt[blockIdx.x] = scnt[0];
-  }
-}
-
-// Sums the nb partials in block order (the order gpf_mse_loss_grad uses).
-__global__ void noalloc_final_kernel(int64_t nb, NoAllocScratch* __restrict__ sc,
-                                     float* __restrict__ loss) {
-  double s = 0.0;
-  uint64_t c = 0;
-  for (int64_t b = 0; b < nb; ++b) {
-    s += sc->psum[b];
-    c += sc->pcnt[b];
-  }
-  *loss = c ? (float)(s / (double)c) : 0.0f;
-  sc->scale = c ? (float)(2.0 / (double)c) : 0.0f;
-}
-
-__global__ void noalloc_grad_kernel(int64_t m, int channels, const float* __restrict__ out,
-                                    const float* __restrict__ target,
-                                    const uint8_t* __restrict__ valid,
-                                    const NoAllocScratch* __restrict__ sc,
-                                    float* __restrict__ grad) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= m) return;
-  const bool ok = valid == nullptr || valid[q] != 0;
-  const float sc_ = sc->scale;
-  for (int c = 0; c < channels; ++c) {
-    const int64_t i = (int64_t)c * m + q;
-    grad[i] = ok ? (out[i] - target[i]) * sc_ : 0.0f;
-  }
-}
 
 // Device address of the scratch array, looked up once per device. In host
 // code the name g_noalloc_scratch only stands for the array; the address the
@@ -132,23 +68,14 @@ int64_t noalloc_max_points() { return kNoAllocMaxBlocks * kNoAllocPerBlock; }
 cudaError_t launch_mse_noalloc(int64_t m, int channels, const float* out, const float* target,
                                const uint8_t* valid, float* loss, float* grad,
                                cudaStream_t stream) {
+  if (mse_points_per_partial() != kNoAllocPerBlock) return cudaErrorInvalidConfiguration;
   NoAllocScratch* sc = nullptr;
   cudaError_t e = noalloc_scratch(&sc);
   if (e != cudaSuccess) return e;
-  const int64_t nb = (m + kNoAllocPerBlock - 1) / kNoAllocPerBlock;
-  if (nb > 0) {
-    noalloc_partial_kernel<<<(unsigned)nb, kNoAllocThreads, 0, stream>>>(m, channels, out, target,
-                                                                         valid, sc);
-    note_launches(1);
-  }
-  noalloc_final_kernel<<<1, 1, 0, stream>>>(nb, sc, loss);
-  note_launches(1);
-  if (m > 0) {
-    noalloc_grad_kernel<<<(unsigned)((m + 255) / 256), 256, 0, stream>>>(m, channels, out, target,
-                                                                         valid, sc, grad);
-    note_launches(1);
-  }
-  return cudaGetLastError();
+  // the kernels of gpf_mse_loss_grad on the library's own scratch: the same
+  // partial sums in the same order, so the results are equal bit for bit
+  return launch_mse_parts(m, channels, out, target, valid, loss, grad, sc->psum, sc->pcnt,
+                          &sc->scale, stream);
 }
 
 }  // namespace gpf

@@ -198,6 +198,15 @@ cudaError_t launch_mse(int64_t m, int channels, const float* out, const float* t
   uint32_t* pcnt = reinterpret_cast<uint32_t*>(p);
   p += align_up(sizeof(uint32_t) * (nb + 1));
   float* scale = reinterpret_cast<float*>(p);
+  return launch_mse_parts(m, channels, out, target, valid, loss, grad, psum, pcnt, scale, stream);
+}
+
+int64_t mse_points_per_partial() { return kMsePerBlock; }
+
+cudaError_t launch_mse_parts(int64_t m, int channels, const float* out, const float* target,
+                             const uint8_t* valid, float* loss, float* grad, float* psum,
+                             uint32_t* pcnt, float* scale, cudaStream_t stream) {
+  const int64_t nb = (m + kMsePerBlock - 1) / kMsePerBlock;
   if (nb > 0) {
     mse_partial_kernel<<<(unsigned)nb, kMseThreads, 0, stream>>>(m, channels, out, target, valid,
                                                                  psum, pcnt);
