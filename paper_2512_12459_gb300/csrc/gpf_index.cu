@@ -399,17 +399,34 @@ __global__ void emit_kernel(Grid grid, int64_t n, int64_t p_max, const float* __
     }
     if (bw.x != kNoBox) {
       const LevelBox b = unpack_box(bw);
-      const uint32_t mask = gmask[g];
-      uint32_t c = 0;
-      for (uint32_t iz = b.lz; iz <= b.hz; ++iz)
-        for (uint32_t iy = b.ly; iy <= b.hy; ++iy)
-          for (uint32_t ix = b.lx; ix <= b.hx; ++ix, ++c) {
-            if (mask != kMaskAll && !((mask >> c) & 1u)) continue;
-            const CellHash h = cell_hash(grid, b.level, ix, iy, iz);
-            if (mask == kMaskAll && !occupied(occ, h.bucket)) continue;
-            put(pos, h.bucket, (uint32_t)g | h.tag);
-            ++pos;
-          }
+      uint32_t mask = gmask[g];
+      if (mask != kMaskAll) {
+        // the set bits only, in increasing cell order (x fastest): cell c of
+        // the box is (c mod nx, (c / nx) mod ny, c / (nx ny)); c < 31, so the
+        // quotients computed as floor((c + 0.5) / d) in float32 are exact
+        const uint32_t nx = b.hx - b.lx + 1, nxy = nx * (b.hy - b.ly + 1);
+        const float inx = 1.0f / (float)nx, inxy = 1.0f / (float)nxy;
+        while (mask) {
+          const uint32_t c = (uint32_t)__ffs(mask) - 1u;
+          mask &= mask - 1u;
+          const uint32_t dz = (uint32_t)(((float)c + 0.5f) * inxy);
+          const uint32_t r = c - dz * nxy;
+          const uint32_t dy = (uint32_t)(((float)r + 0.5f) * inx);
+          const uint32_t dx = r - dy * nx;
+          const CellHash h = cell_hash(grid, b.level, b.lx + dx, b.ly + dy, b.lz + dz);
+          put(pos, h.bucket, (uint32_t)g | h.tag);
+          ++pos;
+        }
+      } else {
+        for (uint32_t iz = b.lz; iz <= b.hz; ++iz)
+          for (uint32_t iy = b.ly; iy <= b.hy; ++iy)
+            for (uint32_t ix = b.lx; ix <= b.hx; ++ix) {
+              const CellHash h = cell_hash(grid, b.level, ix, iy, iz);
+              if (!occupied(occ, h.bucket)) continue;
+              put(pos, h.bucket, (uint32_t)g | h.tag);
+              ++pos;
+            }
+      }
     }
   }
   __syncthreads();
