@@ -32,6 +32,7 @@ namespace {
 
 constexpr int kBwdWarps = 4;
 constexpr int64_t kGrab = 4;            // work units per atomic of the persistent loop
+constexpr int64_t kFineLarge = 4096;    // largest non-split Gaussians taken one per atomic
 constexpr int kBwdThreads = kBwdWarps * kWarp;
 
 struct BwdArgs {
@@ -362,16 +363,26 @@ bwd_grid_kernel(BwdArgs a) {
   const int64_t small_warps = (n_small + kWarp - 1) / kWarp;
   const int64_t n_split = min((int64_t)a.header->n_huge, kSplitMax);
   const int64_t units = small_warps + n_split * kSplitWays + (n_live - n_small - n_split);
-  // persistent: every warp takes the next kGrab work units (each 32 small
+  // persistent: every warp takes the next work units (each 32 small
   // Gaussians, one of the kSplitWays parts of a huge Gaussian, or one large
-  // Gaussian) until none is left; one atomic per kGrab units keeps the work
-  // counter, a single address, from queueing
+  // Gaussian) until none is left: kGrab at a time, so that one atomic on the
+  // work counter (a single address) serves several units, except over the
+  // split parts and the kFineLarge largest other Gaussians, which are taken
+  // one by one so that no warp holds several heavy units
+  const int64_t fine_begin = small_warps;
+  const int64_t fine_end =
+      small_warps + n_split * kSplitWays + min(n_live - n_small - n_split, kFineLarge);
   for (;;) {
-  unsigned long long w_u = 0;
-  if (lane == 0) w_u = atomicAdd(a.next_work, (unsigned long long)kGrab);
+  unsigned long long w_u = 0, g_u = 0;
+  if (lane == 0) {
+    const int64_t seen = (int64_t)*(volatile unsigned long long*)a.next_work;
+    g_u = (seen + kGrab > fine_begin && seen < fine_end) ? 1ull : (unsigned long long)kGrab;
+    w_u = atomicAdd(a.next_work, g_u);
+  }
   const int64_t w0 = (int64_t)__shfl_sync(kFullMask, w_u, 0);
+  const int64_t grab = (int64_t)__shfl_sync(kFullMask, g_u, 0);
   if (w0 >= units) break;
-  const int64_t w_end = min(w0 + kGrab, units);
+  const int64_t w_end = min(w0 + grab, units);
   for (int64_t w = w0; w < w_end; ++w) {
   if (w < small_warps) {
     const int64_t idx = w * kWarp + lane;
