@@ -28,7 +28,7 @@ struct DeviceHeader {
   uint32_t level_mask;   // bit L set when some Gaussian lives on level L
   uint32_t n_live;       // Gaussians whose level box holds a hit point
   uint32_t n_small;      // live Gaussians spanning <= 2 query-level cells per axis
-  uint32_t n_huge;       // live large Gaussians of the top size rank (split in the backward)
+  uint32_t n_huge;       // live large Gaussians of the two top size ranks (split in the backward)
   uint32_t stalled;      // 1 if a bounded wait of the build's sort gave up
   // work counters of the persistent pair loops (reset before each launch)
   unsigned long long next_tile;       // forward: next tile of 32 hit points
@@ -72,8 +72,8 @@ __device__ __forceinline__ uint16_t f32_to_bf16(float x) {
 // Bits of the backward's order key that rank the large Gaussians by size
 // (largest first), between the class and the coarse cell of the mean.
 constexpr int kOrderSizeBits = 3;
-// The backward splits each Gaussian of the top size rank (bounds over at
-// least 2^14 query-level cells), up to kSplitMax of them, into kSplitWays
+// The backward splits each Gaussian of the two top size ranks (bounds over
+// at least 2^12 query-level cells), up to kSplitMax of them, into kSplitWays
 // work units over its rows of cells, summing their partial sums in order.
 constexpr int kSplitWays = 16;
 constexpr int64_t kSplitMax = 16384;

@@ -259,7 +259,7 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
       gcount[g] = cnt;
       if (!live) cls = 2;
       small = live && cls == 0;
-      huge = live && cls == 1 && size_rank == 0;
+      huge = live && cls == 1 && size_rank <= 1;
     }
     okey[g] = mkey | (size_rank << size_shift) | (cls << cls_shift);
     glive[g] = (brute || live) ? 1 : 0;
