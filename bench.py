@@ -336,6 +336,72 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_train(args):
+    """The training run of the measurement plan's third configuration: the
+    1,000,000-Gaussian caustic field fitted, over 8 orbit views of 800 x 800
+    (radius 6, height 3, aimed at (0, 0, 1)), to targets rendered from a
+    perturbed copy (means + N(0, 0.01), spectra x U[0.8, 1.2]); Adam at lr
+    5e-4 for --train-steps steps, each a replay of one captured CUDA graph
+    (build, forward, MSE, backward, Adam). Reports time per step and the loss
+    curve (the loss of every step copied on the device, read once at the end)."""
+    import torch
+    import synth
+    import paper_2512_12459_gb300 as gpf
+    from paper_2512_12459_gb300.setup_index import autotune, make_index
+    from paper_2512_12459_gb300.train import TrainStep
+
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    pos, flux = synth.caustic_photons(N_PHOTONS, seed=0)
+    fnp = synth.field_from_photons(pos, flux, seed=0)
+    tgt_np = synth.perturbed_copy(fnp, seed=1)
+    qnp = synth.orbit_views(8, 800, 800)
+    gen_s = time.time() - t0
+    field = gpf.Field.from_numpy(fnp)
+    queries = gpf.Queries.from_numpy(qnp)
+    n_active = int(qnp.valid.sum())
+    tf = gpf.Field.from_numpy(tgt_np)
+    tidx = make_index(tf, queries, query_cell=CELL)
+    tidx.build(tf, queries)
+    target = gpf.gpf_radiance_fwd(tidx, tf, queries, gpf.GPF_SUM, r_max=R_MAX)[0].clone()
+    del tidx, tf
+    grid, _ = autotune(field, queries, r_max=R_MAX, repeats=2)
+    idx = make_index(field, queries, grid=grid, headroom=1.25)
+    step = TrainStep(field, queries, target, idx, r_max=R_MAX, lr=LR)
+    step.capture(warmup=1)                      # one real step, then the recording
+    n = args.train_steps
+    losses = torch.empty((n,), dtype=torch.float32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(n):
+        step()
+        losses[i].copy_(step.loss[0])
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    st = idx.stats()
+    if st["overflow"]:
+        raise RuntimeError(f"pair buffer overflow: {st}")
+    lh = losses.cpu().numpy().astype(float)
+    marks = sorted({0, n // 4, n // 2, 3 * n // 4, n - 1})
+    line = {
+        "metric": "training-step hit-point queries/s (8 views, 1M Gaussians)",
+        "value": n_active / (ms / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": n,
+        "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{N_PHOTONS:,} Gaussians, 8 orbit views of 800x800, "
+                               f"{n} Adam steps, CUDA graph",
+                   "hit_points": int(qnp.m), "active_hit_points": n_active,
+                   "l2": "inputs larger than L2",
+                   "grid": {"query_cell": grid.cell_size * (1 << grid.query_level),
+                            "max_span": grid.max_span, "coop_cells": grid.coop_cells}},
+        "loss": {str(i + 2): lh[i] for i in marks},   # step 1 ran before the capture
+        "loss_ratio_last_first": lh[-1] / lh[0],
+        "setup_s": {"generate": round(gen_s, 1)},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_bf16(args):
     """16-bit parameter storage: 4M Gaussians with an 8-bin spectrum in
     Morton order, 16 views of 1920x1080; the captured training step with
@@ -605,10 +671,12 @@ def main():
                     help="Gaussians (smaller cases are for profiling only)")
     ap.add_argument("--view", type=int, default=VIEW, help="view side in pixels")
     ap.add_argument("--workload", default="single",
-                    choices=["single", "batched", "bf16", "kde", "scaling"],
+                    choices=["single", "batched", "bf16", "kde", "scaling", "train"],
                     help="single: the 1M-Gaussian 1024x1024 step (default line); batched: "
                          "64 uneven views over 2M Gaussians, graph replay vs per-view launches")
     ap.add_argument("--batched-views", type=int, default=64)
+    ap.add_argument("--train-steps", type=int, default=200,
+                    help="train workload: Adam steps timed")
     ap.add_argument("--batched-photons", type=int, default=2_000_000)
     ap.add_argument("--bf16-photons", type=int, default=4_000_000)
     ap.add_argument("--bf16-views", type=int, default=16)
@@ -640,6 +708,9 @@ def main():
         return
     if args.workload == "scaling":
         run_scaling(args)
+        return
+    if args.workload == "train":
+        run_train(args)
         return
 
     import torch
