@@ -329,8 +329,9 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
   }
   if (mark) {
     // occupancy bits of every level: all levels' words are read at once,
-    // then the lanes in the same cell of a level (all of a warp's on the
-    // coarse ones) set its bit once, where it is not set yet
+    // then on each level the first lane of every run of lanes in the same
+    // cell (all of a warp's on the coarse ones) sets its bit where it is not
+    // set yet
     uint32_t bkt[kMaxLevels], word[kMaxLevels];
 #pragma unroll
     for (int L = 0; L < kMaxLevels; ++L) {
@@ -343,9 +344,11 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
     for (int L = 0; L < kMaxLevels; ++L) {
       if (L >= grid.levels) break;
       const uint32_t b = bkt[L];
-      const uint32_t same = __match_any_sync(kFullMask, b);
+      // setting a bit twice is harmless: skipping a lane whose left
+      // neighbour has the same cell removes nearly all repeats cheaply
+      const uint32_t left = __shfl_up_sync(kFullMask, b, 1);
       const uint32_t bit = 1u << (b & 31u);
-      if (b != 0xffffffffu && (same & lanemask_lt()) == 0 && !(word[L] & bit))
+      if (b != 0xffffffffu && ((threadIdx.x & 31) == 0 || left != b) && !(word[L] & bit))
         atomicOr(&occ[b >> 5], bit);
     }
   }
