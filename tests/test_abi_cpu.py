@@ -207,3 +207,23 @@ def test_generators_are_seeded():
     assert np.all(np.sum(q.n[:, v] * q.wo[:, v], axis=0) > 0)
     mp, mf = synth.merge_photon_pairs(pos, flux)
     assert mp.shape[0] == 1000 and np.allclose(mf.sum(), flux.sum())
+
+
+def test_box_cell_quotients_are_exact_in_float32():
+    """emit_kernel recovers the cell of bit c of a box's occupied-cell mask
+    (x fastest, boxes of at most 31 cells) as dz = floor((c + 0.5) / (nx ny)),
+    dy = floor((r + 0.5) / nx) in float32 with correctly rounded reciprocals:
+    exact for every box shape and bit index it can meet."""
+    f = np.float32
+    for nx in range(1, 32):
+        for ny in range(1, 32):
+            for nz in range(1, 32):
+                if nx * ny * nz > 31:
+                    continue
+                nxy = nx * ny
+                inx, inxy = f(1) / f(nx), f(1) / f(nxy)
+                for c in range(nx * ny * nz):
+                    dz = int(f(f(c) + f(0.5)) * inxy)
+                    r = c - dz * nxy
+                    dy = int(f(f(r) + f(0.5)) * inx)
+                    assert (dz, dy, r - dy * nx) == (c // nxy, (c % nxy) // nx, c % nx)
