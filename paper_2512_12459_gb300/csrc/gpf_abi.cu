@@ -94,6 +94,7 @@ size_t layout(const gpf_index* ix, char* base, IndexBuffers* b) {
   t.gcount = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * N));
   t.glive = reinterpret_cast<uint8_t*>(take(sizeof(uint8_t) * N));
   t.gmask = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * N));
+  t.qbox = reinterpret_cast<uint2*>(take(sizeof(uint2) * N));
   t.goffset = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * N));
   for (int k = 0; k < 2; ++k) {
     t.okey[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * N));

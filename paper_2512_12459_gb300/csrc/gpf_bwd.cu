@@ -49,6 +49,7 @@ struct BwdArgs {
   float* qrec;
   float* gacc;            // [N * NS] per-Gaussian sums, by Gaussian id
   const uint8_t* glive;   // [N] 1 if the pair loop visits the Gaussian
+  const uint2* qbox;      // [N] query-level cell bounds (pack_qbox), from the build
   float* bpart;           // [kSplitMax * kSplitWays * NS] split Gaussians' partials
   const float* rec;
   const uint4* box;
@@ -321,13 +322,9 @@ __device__ void bwd_lane_gaussian(const BwdArgs& a, int64_t gi) {
   GaussianRegs G;
   float phi[C];
   load_gaussian<C>(a, gi, G, phi);
-  const Frame fr = gaussian_frame(a.quat, a.logscale, a.n, gi);
-  const float mu[3] = {G.mx, G.my, G.mz};
   uint32_t lo[3], hi[3];
-  gaussian_cells0(Gd, fr, mu, a.cut, lo, hi);
-  const int K = Gd.qlevel;
-  const uint32_t lx = lo[0] >> K, hx = hi[0] >> K, ly = lo[1] >> K, hy = hi[1] >> K,
-                 lz = lo[2] >> K, hz = hi[2] >> K;
+  unpack_qbox(a.qbox[gi], lo, hi);
+  const uint32_t lx = lo[0], hx = hi[0], ly = lo[1], hy = hi[1], lz = lo[2], hz = hi[2];
   Acc<C> acc;
   acc.zero();
   for (uint32_t iz = lz; iz <= hz; ++iz)
@@ -400,14 +397,11 @@ bwd_grid_kernel(BwdArgs a) {
   GaussianRegs G;
   float phi[C];
   load_gaussian<C>(a, gi, G, phi);
-  const Frame fr = gaussian_frame(a.quat, a.logscale, a.n, gi);
-  const float mu[3] = {G.mx, G.my, G.mz};
   uint32_t lo[3], hi[3];
-  gaussian_cells0(Gd, fr, mu, a.cut, lo, hi);
+  unpack_qbox(a.qbox[gi], lo, hi);
   const int K = Gd.qlevel;
-  const int lx = (int)(lo[0] >> K), ly = (int)(lo[1] >> K), lz = (int)(lo[2] >> K);
-  const int nx = (int)(hi[0] >> K) - lx + 1, ny = (int)(hi[1] >> K) - ly + 1,
-            nz = (int)(hi[2] >> K) - lz + 1;
+  const int lx = (int)lo[0], ly = (int)lo[1], lz = (int)lo[2];
+  const int nx = (int)hi[0] - lx + 1, ny = (int)hi[1] - ly + 1, nz = (int)hi[2] - lz + 1;
   const float cut_keep = a.cut * 1.0001f;
   const float cellK = Gd.cell0 * (float)(1u << K);
   const float half = 0.5f * cellK * 1.001f;
@@ -468,7 +462,6 @@ bwd_grid_kernel(BwdArgs a) {
   float* dst = split ? a.bpart + ((j - n_small) * kSplitWays + part) * Acc<C>::NS
                      : a.gacc + gi * Acc<C>::NS;
   if (Acc<C>::NS == 32 || (lane & 1) == 0) dst[slot] = sum;
-  (void)fr;
   }
   }  // work loop
 }
@@ -609,6 +602,7 @@ cudaError_t launch_backward(const IndexDims& d, const IndexBuffers& b, const gpf
   a.qrec = b.qrec;
   a.gacc = b.gacc;
   a.glive = b.glive;
+  a.qbox = b.qbox;
   a.bpart = b.bpart;
   a.rec = b.rec;
   a.box = b.box;

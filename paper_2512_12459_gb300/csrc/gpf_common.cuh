@@ -251,6 +251,19 @@ __device__ __forceinline__ void gaussian_cells0(const Grid& g, const Frame& f, c
   }
 }
 
+// Query-level cell bounds of a Gaussian's k-sigma box (gaussian_cells0's
+// level-0 bounds >> K), packed 10 bits per axis (query-level cells per axis
+// are at most GPF_MAX_DIM = 1024): x = lo, y = hi, each ix | iy << 10 | iz << 20.
+__device__ __forceinline__ uint2 pack_qbox(const uint32_t lo[3], const uint32_t hi[3], int K) {
+  return make_uint2((lo[0] >> K) | ((lo[1] >> K) << 10) | ((lo[2] >> K) << 20),
+                    (hi[0] >> K) | ((hi[1] >> K) << 10) | ((hi[2] >> K) << 20));
+}
+__device__ __forceinline__ void unpack_qbox(uint2 b, uint32_t lo[3], uint32_t hi[3]) {
+  lo[0] = b.x & 1023u; lo[1] = (b.x >> 10) & 1023u; lo[2] = (b.x >> 20) & 1023u;
+  hi[0] = b.y & 1023u; hi[1] = (b.y >> 10) & 1023u; hi[2] = (b.y >> 20) & 1023u;
+}
+static_assert(GPF_MAX_DIM <= 1024, "query-level cell coordinates fit 10 bits");
+
 // 2^x on the special-function unit (ex2.approx.ftz.f32, relative error
 // ~2^-22 over the range used here).
 __device__ __forceinline__ float ex2_approx(float x) {

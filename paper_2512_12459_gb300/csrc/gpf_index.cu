@@ -153,7 +153,7 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
                                   float* __restrict__ rec, int rs, uint4* __restrict__ box,
                                   const uint32_t* __restrict__ occ,
                                   uint32_t* __restrict__ gcount, uint8_t* __restrict__ glive,
-                                  uint32_t* __restrict__ gmask,
+                                  uint32_t* __restrict__ gmask, uint2* __restrict__ qbox,
                                   uint32_t* __restrict__ okey, uint32_t* __restrict__ oval,
                                   DeviceHeader* header) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -198,6 +198,7 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
     if (!brute) {
       uint32_t lo[3], hi[3];
       gaussian_cells0(grid, fr, mu, cutoff, lo, hi);
+      qbox[g] = pack_qbox(lo, hi, grid.qlevel);    // the backward's cell range
       if ((hi[0] >> K) - (lo[0] >> K) <= 1 && (hi[1] >> K) - (lo[1] >> K) <= 1 &&
           (hi[2] >> K) - (lo[2] >> K) <= 1) {
         cls = 0;
@@ -500,7 +501,7 @@ cudaError_t launch_build(const IndexDims& d, const IndexBuffers& b, const gpf_fi
   if (f.n > 0) {
     preprocess_kernel<<<blocks_for(f.n), kThreads, 0, stream>>>(
         f, grid, d.cutoff, d.brute ? 1 : 0, b.rec, rec_stride(d.channels), b.box, b.occ,
-        b.gcount, b.glive, b.gmask, b.okey[0], b.oval[0], b.header);
+        b.gcount, b.glive, b.gmask, b.qbox, b.okey[0], b.oval[0], b.header);
     note_launches(1);
   }
   // 3. hit points sorted by query-level cell (inactive ones last), cell starts

@@ -58,6 +58,7 @@ struct IndexBuffers {
   uint32_t* gcount;     // [N_max] entries per Gaussian
   uint8_t* glive;       // [N_max] 1 if the backward visits the Gaussian (a hit point in reach)
   uint32_t* gmask;      // [N_max] occupied cells of the level box (boxes of <= 31 cells)
+  uint2* qbox;          // [N_max] query-level cell bounds of each Gaussian (pack_qbox)
   uint32_t* goffset;    // [N_max] exclusive scan of gcount
   uint32_t* okey[2];    // [N_max] query-level key of each mean (sort ping-pong)
   uint32_t* oval[2];    // [N_max] Gaussian ids in that order
