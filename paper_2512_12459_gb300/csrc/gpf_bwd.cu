@@ -351,7 +351,7 @@ __device__ void bwd_lane_gaussian(const BwdArgs& a, int64_t gi) {
 // query-level cell its k-sigma bounds overlap. Gaussians whose level box
 // holds no hit point come last and are skipped (zero gradient).
 template <int C, bool PSI>
-__global__ void __launch_bounds__(kBwdThreads, 8)
+__global__ void __launch_bounds__(kBwdThreads, 9)
 bwd_grid_kernel(BwdArgs a) {
   constexpr int QS = qrec_stride(C);
   const int lane = threadIdx.x & 31;
