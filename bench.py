@@ -175,41 +175,128 @@ def fp32_peak_tflops(sm_mhz_max: float, sms: int = 152) -> float:
     return sms * 128 * 2 * sm_mhz_max * 1e6 / 1e12
 
 
-def cpu_baseline(fnp, tgt_out_fn, qnp, budget_s: float = 15.0):
-    """The FP64 oracle (as it stands) on a bounded sample of the same workload:
-    forward + backward of single hit points over all Gaussians, repeated until
-    the time budget is spent. Returns queries/s and the sample description."""
+# ---- the FP64 oracle on all host cores (the CPU baseline and --impl reference)
+_W = {}
+
+
+def _oracle_worker_init(mean, quat, logscale, spectrum):
+    _W["f"] = (mean, quat, logscale, spectrum)
+
+
+def _oracle_task(x, n, wo, valid, target):
+    """Forward + backward of a few hit points over every Gaussian (the oracle
+    as it stands), in a worker process; returns the forward's per-point
+    results for the error check."""
     import oracle
-    rng = np.random.default_rng(123)
-    act = np.flatnonzero(qnp.valid.astype(bool))
-    done, t0 = 0, time.perf_counter()
-    chunk = 4
-    while time.perf_counter() - t0 < budget_s:
-        sel = rng.choice(act, size=chunk, replace=False)
-        x, n, wo = qnp.x[:, sel], qnp.n[:, sel], qnp.wo[:, sel]
-        fo = oracle.radiance_fwd(fnp.mean, fnp.quat, fnp.logscale, fnp.spectrum, x, n, wo, None,
-                                 qnp.valid[sel], r_max=R_MAX, cutoff_sigma=CUTOFF)
-        target = tgt_out_fn(sel)
-        g = oracle.mse_loss_grad(fo["out"], target, qnp.valid[sel])
-        oracle.radiance_bwd(fnp.mean, fnp.quat, fnp.logscale, fnp.spectrum, x, n, wo, g, None,
-                            qnp.valid[sel], r_max=R_MAX, cutoff_sigma=CUTOFF)
-        done += chunk
-    dt = time.perf_counter() - t0
-    return done / dt, done, dt
+    mean, quat, logscale, spectrum = _W["f"]
+    fo = oracle.radiance_fwd(mean, quat, logscale, spectrum, x, n, wo, None, valid,
+                             r_max=R_MAX, cutoff_sigma=CUTOFF)
+    g = oracle.mse_loss_grad(fo["out"], target, valid)
+    oracle.radiance_bwd(mean, quat, logscale, spectrum, x, n, wo, g, None, valid,
+                        r_max=R_MAX, cutoff_sigma=CUTOFF)
+    return {k: fo[k] for k in ("out", "denom", "logw_max", "near_cutoff")}
+
+
+class OraclePool:
+    """A spawn-started pool of one process per host core (os.sched_getaffinity),
+    each with one BLAS/OpenMP thread, holding the field. Spawned workers share
+    no CUDA state with this process."""
+
+    def __init__(self, fnp):
+        import concurrent.futures
+        import multiprocessing as mp
+        self.cores = len(os.sched_getaffinity(0))
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                                 "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"        # inherited by the spawned workers only
+        try:
+            self.ex = concurrent.futures.ProcessPoolExecutor(
+                max_workers=self.cores, mp_context=mp.get_context("spawn"),
+                initializer=_oracle_worker_init,
+                initargs=(fnp.mean, fnp.quat, fnp.logscale, fnp.spectrum))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def run(self, qnp, tgt_out_fn, budget_s: float, chunk: int = 4, seed: int = 123):
+        """Keeps every core busy with `chunk`-point tasks until budget_s has
+        passed, then waits for the tasks in flight. Returns (queries/s, points,
+        seconds, {point index: forward result})."""
+        import concurrent.futures
+        rng = np.random.default_rng(seed)
+        act = np.flatnonzero(qnp.valid.astype(bool))
+        t0 = time.perf_counter()
+        pending, results = {}, {}
+
+        def submit():
+            sel = rng.choice(act, size=chunk, replace=False)
+            fut = self.ex.submit(_oracle_task, qnp.x[:, sel], qnp.n[:, sel], qnp.wo[:, sel],
+                                 qnp.valid[sel], tgt_out_fn(sel))
+            pending[fut] = sel
+
+        for _ in range(self.cores):
+            submit()
+        done = 0
+        while pending:
+            fin, _ = concurrent.futures.wait(list(pending),
+                                             return_when=concurrent.futures.FIRST_COMPLETED)
+            for fut in fin:
+                sel = pending.pop(fut)
+                res = fut.result()
+                done += len(sel)
+                for j, i in enumerate(sel):
+                    results[int(i)] = {k: (v[..., j] if np.ndim(v) > 1 else v[j])
+                                       for k, v in res.items()}
+                if time.perf_counter() - t0 < budget_s:
+                    submit()
+        dt = time.perf_counter() - t0
+        return done / dt, done, dt, results
+
+    def close(self):
+        self.ex.shutdown(wait=True)
+
+
+def error_vs_oracle(out_gpu, results):
+    """Relative error |O_gpu - O_ref| / (rho sum w |Phi|) at the oracle's sample
+    points (hit points with a pair within 1e-4 of the cutoff excluded, as in
+    the parity tests): max, 99th percentile and median over points."""
+    errs = []
+    for i, r in results.items():
+        if r["near_cutoff"]:
+            continue
+        den = np.maximum(r["denom"], 1e-20)
+        errs.append(float(np.max(np.abs(out_gpu[:, i] - r["out"]) / den)))
+    if not errs:
+        return None
+    e = np.asarray(errs)
+    return {"max": float(e.max()), "p99": float(np.quantile(e, 0.99)),
+            "median": float(np.median(e)), "points": int(e.size),
+            "excluded_near_cutoff": int(len(results) - e.size),
+            "metric": "per hit point max over channels of |O_gpu - O_oracle| / (rho sum_i w_i "
+                      "|Phi_i|), oracle in float64 over all Gaussians"}
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the FP64 oracle timed on the host cores."""
+    """--impl reference: the FP64 oracle timed on all host cores, each step a
+    bounded random sample of the workload's hit points (fwd + bwd of each over
+    all Gaussians), sized so that the whole run ends within a few minutes."""
     if rank != 0:
         return
     fnp, tgt, qnp = make_inputs(0)
     tgt_fn = lambda sel: np.zeros((3, len(sel)))  # noqa: E731  (target values do not change the work)
+    per_step = min(args.ref_budget, 150.0 / max(1, args.steps + args.warmup))
+    pool = OraclePool(fnp)
     steps = []
     for _ in range(args.warmup):
-        cpu_baseline(fnp, tgt_fn, qnp, budget_s=2.0)
-    for _ in range(args.steps):
-        rate, done, dt = cpu_baseline(fnp, tgt_fn, qnp, budget_s=args.ref_budget)
+        pool.run(qnp, tgt_fn, budget_s=per_step / 2)
+    for k in range(args.steps):
+        rate, done, dt, _ = pool.run(qnp, tgt_fn, budget_s=per_step, seed=1000 + k)
         steps.append((rate, done, dt))
+    pool.close()
     rate = sum(s[1] for s in steps) / sum(s[2] for s in steps)
     n_active = int(qnp.valid.sum())
     line = {
@@ -219,10 +306,12 @@ def run_reference(args, rank, world):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "global_batch": n_active, "seq_len": None,
                    "parallelism": "cpu", "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": rate, "unit": "queries/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{sum(s[1] for s in steps)} random valid hit points, fwd+bwd "
-                                   "each over all 1,000,000 Gaussians (numpy float64, one thread); "
-                                   "ms_per_step extrapolates to the full view"},
+        "cpu_baseline": {"value": rate, "unit": "queries/s", "cores": pool.cores,
+                         "kind": "oracle",
+                         "sample": f"{sum(s[1] for s in steps)} random valid hit points in "
+                                   f"{args.steps} steps of about {per_step:.1f} s, fwd+bwd each "
+                                   "over all 1,000,000 Gaussians (numpy float64, one process "
+                                   "per core); ms_per_step extrapolates to the full view"},
         "e2e": {"value": rate, "unit": "queries/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -724,7 +813,11 @@ def main():
     from paper_2512_12459_gb300.setup_index import autotune, make_index
 
     fnp, tgt_np, qnp = make_inputs(rank)
+    # the oracle's process pool starts now (spawned: it shares nothing with
+    # this process's CUDA context) and is used after the timed region
+    pool = OraclePool(fnp) if rank == 0 and world == 1 and not args.no_cpu_baseline else None
     field = gpf.Field.from_numpy(fnp)
+    field0 = gpf.Field(*(t.clone() for t in field.tensors()))   # before any Adam step
     queries = gpf.Queries.from_numpy(qnp)
     tgt_field = gpf.Field.from_numpy(tgt_np)
     n_active = int(qnp.valid.sum())
@@ -884,7 +977,16 @@ def main():
 
     peaks, peaks_src = measured_peaks()
     smax = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = fp32_peak_tflops(smax)
+    nominal_fp32 = fp32_peak_tflops(smax)
+    # the pipes the pair loops use, measured on this GPU (after the timed region)
+    fma = gpf.gpf_measure_alu_peak(gpf.GPF_PEAK_FP32_FMA)
+    ex2 = gpf.gpf_measure_alu_peak(gpf.GPF_PEAK_EX2)
+    fp32_peak = fma["per_second"] / 1e12
+    ex2_peak = ex2["per_second"] / 1e12
+    alu_peaks = {"fp32_fma_tflops": fp32_peak, "ex2_tops": ex2_peak,
+                 "fp32_nominal_tflops": nominal_fp32,
+                 "how": "gpf_measure_alu_peak: 8 x 256 threads per SM, 8 independent chains "
+                        "per thread, CUDA events"}
     C = fnp.channels
     roof = None
     extra = {}
@@ -899,21 +1001,31 @@ def main():
         ach = bwd_ach if dom == "bwd_grid_kernel" else fwd_ach
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": profiled_traffic(dom),
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {smax:.0f} MHz ({peaks_src} max clock)",
+                "peak_source": "measured FP32 FMA rate of this GPU (gpf_measure_alu_peak); "
+                               f"nominal 152 SMs x 128 lanes x 2 x {smax:.0f} MHz = "
+                               f"{nominal_fp32:.1f}",
                 "duration_ms": kernel_ms[dom]}
+        # one ex2 per included pair in either pair loop
         extra = {"included_pairs": inc, "candidate_pairs": pairs["candidates"],
-                 "fwd_alu_frac": fwd_ach / fp32_peak, "bwd_alu_frac": bwd_ach / fp32_peak}
+                 "fwd_alu_frac": fwd_ach / fp32_peak, "bwd_alu_frac": bwd_ach / fp32_peak,
+                 "fwd_sfu_frac": inc / (kernel_ms["fwd_kernel"] / 1e3) / 1e12 / ex2_peak,
+                 "bwd_sfu_frac": inc / (kernel_ms["bwd_grid_kernel"] / 1e3) / 1e12 / ex2_peak}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
+    cpu, err = None, None
+    if pool is not None:
         tgt_out = target.cpu().numpy().astype(np.float64)
-        rate, done, dt = cpu_baseline(fnp, lambda sel: tgt_out[:, sel], qnp,
-                                      budget_s=args.cpu_budget)
-        cpu = {"value": rate, "unit": "queries/s", "cores": 1, "kind": "oracle",
+        rate, done, dt, results = pool.run(qnp, lambda sel: tgt_out[:, sel],
+                                           budget_s=args.cpu_budget)
+        pool.close()
+        cpu = {"value": rate, "unit": "queries/s", "cores": pool.cores, "kind": "oracle",
                "sample": f"{done} random valid hit points of the same view, fwd+bwd each over all "
-                         f"1,000,000 Gaussians, {dt:.1f} s (numpy float64, one thread)"}
-        del oracle
+                         f"1,000,000 Gaussians, {dt:.1f} s (numpy float64, one process per "
+                         "core)"}
+        # the error of the GPU forward at the same points (the field before
+        # the steps above, through a fresh build of the same index)
+        idx.build(field0, queries)
+        out0, _ = gpf.gpf_radiance_fwd(idx, field0, queries, gpf.GPF_SUM, r_max=R_MAX)
+        err = error_vs_oracle(out0.cpu().numpy().astype(np.float64), results)
 
     if rank == 0:
         line = {
@@ -934,7 +1046,9 @@ def main():
             "ms_breakdown": {k: v for k, v in ms.items() if k != "step"},
             "kernel_ms": kernel_ms,
             "roofline": roof,
+            "alu_peaks": alu_peaks,
             "cpu_baseline": cpu,
+            "error_vs_oracle": err,
             "e2e": {"value": total_q / (e2e_ms / 1e3), "unit": "queries/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms,

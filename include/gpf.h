@@ -46,10 +46,14 @@
  *     before anything is enqueued; on an error nothing is enqueued and
  *     gpf_last_error() describes it. No call aborts or throws.
  *   - Problems found on the device (a full pair buffer; a wait of the index
- *     build's single-pass sort that ran out of its poll limit) set a flag in
- *     the index workspace. Kernels that see it leave their outputs untouched;
- *     gpf_index_stats() reads it back and reports GPF_ERR_CAPACITY or
- *     GPF_ERR_TIMEOUT.
+ *     build's single-pass sort that ran out of its poll limit; a non-finite
+ *     Gaussian parameter or active hit point) set a flag in the index
+ *     workspace. Every later kernel that reads the index (forward, backward,
+ *     and an Adam step given the index as its guard) sees it and leaves its
+ *     outputs untouched. gpf_index_stats() reads the flags back and reports
+ *     GPF_ERR_CAPACITY, GPF_ERR_TIMEOUT or GPF_ERR_NONFINITE;
+ *     gpf_index_flags_async() copies them to device memory without a
+ *     synchronisation (for a step replayed as a CUDA graph).
  */
 #ifndef GPF_H
 #define GPF_H
@@ -72,8 +76,16 @@ typedef enum gpf_status {
   GPF_ERR_CAPACITY = 4,           /* the (cell, Gaussian) pair buffer was full */
   GPF_ERR_NOT_BUILT = 5,          /* index used before gpf_build_index         */
   GPF_ERR_MISMATCH = 6,           /* field/queries differ from those indexed   */
-  GPF_ERR_TIMEOUT = 7             /* a bounded device-side wait gave up        */
+  GPF_ERR_TIMEOUT = 7,            /* a bounded device-side wait gave up        */
+  GPF_ERR_NONFINITE = 8           /* a non-finite parameter or hit point       */
 } gpf_status;
+
+/* Bits of the device flags word (gpf_index_flags_async); 0 = usable. */
+#define GPF_FLAG_CAPACITY 1u      /* the pair buffer was full                   */
+#define GPF_FLAG_TIMEOUT 2u       /* a bounded wait of the build's sort gave up */
+#define GPF_FLAG_NONFINITE 4u     /* a Gaussian parameter (mean, quat, logscale,
+                                     spectrum) or the position of an active hit
+                                     point was NaN or infinite                 */
 
 typedef enum gpf_mode { GPF_SUM = 0, GPF_NORMALIZED = 1, GPF_DISK_KDE = 2 } gpf_mode;
 
@@ -156,6 +168,13 @@ typedef struct gpf_query_params {
   float ball_r;          /* GPF_NB_BALL_KNN: ball radius (paper: 0.02), at
                             most the index's ball_radius                     */
   int32_t k_min;         /* GPF_NB_BALL_KNN: 0..GPF_MAX_KMIN (paper: 3)      */
+  int32_t f64_sums;      /* gpf_radiance_bwd only. 0: the per-Gaussian sums
+                            and their reduction run in float32 (the product
+                            path). 1: the gradient-check build: the same
+                            float32 pair terms are summed, reduced and turned
+                            into gradients in float64, so that summation
+                            order no longer hides a wrong term (slow: GB300's
+                            float64 rate is low). Must be 0 in the forward. */
 } gpf_query_params;
 
 /* Multi-level uniform grid and capacities of an index.
@@ -202,11 +221,24 @@ typedef struct gpf_grid_config {
  * the device data live in the caller's workspace. */
 typedef struct gpf_index gpf_index;
 
-/* Counters read back by gpf_index_stats. */
+/* Counters read back by gpf_index_stats. The Gaussian classes are those of
+ * the backward's work split: a live Gaussian has a hit point in a cell of its
+ * k-sigma box; a small one's bounds span at most 2 query-level cells per
+ * axis (one lane of a warp takes it); a large one is spread over a warp; the
+ * large ones whose bounds cover at least 2^12 query-level cells ("huge") are
+ * split, up to GPF_BWD_SPLIT_MAX of them, into GPF_BWD_SPLIT_WAYS work units
+ * whose partial sums are added in a fixed order. */
+#define GPF_BWD_SPLIT_WAYS 16
+#define GPF_BWD_SPLIT_MAX 16384
 typedef struct gpf_index_stats_t {
   int64_t n_pairs;       /* (cell, Gaussian) entries the last build needed   */
   int64_t n_active;      /* hit points that are valid and face the viewer    */
-  int64_t n_occupied;    /* reserved (0)                                     */
+  int64_t n_live;        /* live Gaussians                                   */
+  int64_t n_small;       /* live small Gaussians                             */
+  int64_t n_huge;        /* live huge Gaussians                              */
+  int64_t n_split;       /* huge Gaussians split: min(n_huge, GPF_BWD_SPLIT_MAX) */
+  uint32_t level_mask;   /* bit L set when some Gaussian lives on level L    */
+  uint32_t flags;        /* GPF_FLAG_* bits (0 = usable)                     */
   int32_t overflow;      /* 1 if n_pairs exceeded max_pairs                  */
   int32_t reserved;
 } gpf_index_stats_t;
@@ -232,6 +264,12 @@ typedef struct gpf_adam_hparams {
                             updates applied so far: the update uses
                             t = *step_counter + 1 and then increments it, so
                             a captured CUDA graph replays correct steps       */
+  const gpf_index *guard;/* NULL, or a built index (the one whose backward
+                            produced the gradients): when its last build set
+                            a device flag (GPF_FLAG_*), the update is skipped
+                            on the device: parameters, moments and the step
+                            counter stay untouched. The check happens when
+                            the kernels run, so a captured graph keeps it.   */
 } gpf_adam_hparams;
 
 /* ------------------------------------------------------------------------ */
@@ -298,10 +336,24 @@ gpf_status gpf_build_index(gpf_index *index, const gpf_field *field,
 
 /*
  * gpf_index_stats - synchronise the stream and read the device counters of
- * the last build. Returns GPF_ERR_CAPACITY if the pair buffer overflowed.
+ * the last build. The counters are filled in either way; the status is
+ * GPF_ERR_TIMEOUT, GPF_ERR_NONFINITE or GPF_ERR_CAPACITY (in that order of
+ * precedence) when the matching flag is set, else GPF_OK.
  */
 gpf_status gpf_index_stats(const gpf_index *index, gpf_index_stats_t *stats,
                            gpf_stream stream);
+
+/*
+ * gpf_index_flags_async - enqueue on the stream a one-thread kernel that
+ * writes the device flags of the index's last build (GPF_FLAG_* bits, 0 =
+ * usable) to *flags, without synchronising: a step captured in a CUDA graph
+ * can report an unusable build through it (copy the word to pinned host
+ * memory in the same graph and read it once the replay has finished).
+ *   flags  device uint32, 4-byte aligned, owned by the caller.
+ * The paper has no counterpart: it is error reporting for graph replays.
+ * Errors: GPF_ERR_INVALID_ARG, GPF_ERR_NOT_BUILT, GPF_ERR_CUDA.
+ */
+gpf_status gpf_index_flags_async(const gpf_index *index, uint32_t *flags, gpf_stream stream);
 
 /*
  * gpf_radiance_fwd - radiance O at every hit point (Sec. 4.2, aggregation
@@ -375,7 +427,10 @@ uint64_t gpf_launch_count(void);
  *   out, z    [C,M] and [M] device: the outputs of the matching forward
  *             (read only in GPF_NORMALIZED mode; may be NULL in GPF_SUM).
  *   grads     host struct of device pointers [3,N], [4,N], [3,N], [C,N];
- *             accumulate = 0 overwrites, 1 adds.
+ *             accumulate = 0 overwrites, 1 adds. Left untouched when the
+ *             index's last build set a device flag.
+ *   params    as gpf_radiance_fwd; f64_sums = 1 selects the float64
+ *             gradient-check build of the sums.
  * Errors: as gpf_radiance_fwd.
  */
 gpf_status gpf_radiance_bwd(const gpf_index *index, const gpf_field *field,
@@ -413,9 +468,11 @@ gpf_status gpf_mse_loss_grad(int64_t m, int32_t channels, const float *out,
  * every GPU that loads the library, held until the process exits).
  *   Arguments, outputs and results as gpf_mse_loss_grad (bitwise equal).
  *   m <= GPF_NOALLOC_MAX_POINTS, else GPF_ERR_INVALID_ARG and nothing runs.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture. Allocates no memory. All calls share the one array, which keeps the
+ * Every call looks up the array's device address on the current device (a
+ * host-side lookup, no allocation), so the address stays right after a
+ * cudaDeviceReset reloads the library's device code; the first call on a
+ * device (or after such a reset) also loads that code, so make it before any
+ * stream capture. Allocates no memory. All calls share the one array, which keeps the
  * last call's partial sums; every call overwrites what it reads, but calls
  * whose kernels may overlap on the GPU race on it: order them.
  */
@@ -489,6 +546,23 @@ gpf_status gpf_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
                           uint32_t *vals_alt, int64_t n, int32_t bits, void *workspace,
                           size_t workspace_bytes, int32_t *result_in_alt, gpf_stream stream);
 gpf_status gpf_sort_pairs_check(const void *workspace, gpf_stream stream);
+
+/*
+ * gpf_measure_alu_peak - measured throughput of the two pipes the pair loops
+ * are bound by, for the roofline denominators: GPF_PEAK_FP32_FMA (float32
+ * fused multiply-adds, reported in flop/s, one FMA = 2 flops) or GPF_PEAK_EX2
+ * (the special-function unit's ex2.approx.ftz.f32, every included pair's
+ * exponential, in results/s). Launches 8 blocks of 256 threads per SM, each
+ * thread running 8 independent chains of iters x 16 operations, once untimed
+ * and once timed with CUDA events, on a stream of its own; synchronous.
+ *   per_second  host, receives the rate; seconds: host, the timed launch.
+ * The paper has no counterpart: it is a measurement aid.
+ * Errors: GPF_ERR_INVALID_ARG (which, iters outside 1 .. 2^20, NULL), GPF_ERR_CUDA.
+ */
+#define GPF_PEAK_FP32_FMA 0
+#define GPF_PEAK_EX2 1
+gpf_status gpf_measure_alu_peak(int32_t which, int32_t iters, double *per_second,
+                                double *seconds);
 
 /*
  * gpf_test_sort_wait_timeout - failure-detection test of the sort's bounded

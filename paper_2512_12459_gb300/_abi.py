@@ -17,6 +17,14 @@ GPF_ERR_CAPACITY = 4
 GPF_ERR_NOT_BUILT = 5
 GPF_ERR_MISMATCH = 6
 GPF_ERR_TIMEOUT = 7
+GPF_ERR_NONFINITE = 8
+GPF_FLAG_CAPACITY = 1
+GPF_FLAG_TIMEOUT = 2
+GPF_FLAG_NONFINITE = 4
+GPF_BWD_SPLIT_WAYS = 16
+GPF_BWD_SPLIT_MAX = 16384
+GPF_PEAK_FP32_FMA = 0
+GPF_PEAK_EX2 = 1
 
 GPF_SUM = 0
 GPF_NORMALIZED = 1
@@ -48,7 +56,7 @@ class gpf_queries(ctypes.Structure):
 
 class gpf_query_params(ctypes.Structure):
     _fields_ = [("mode", c_i32), ("r_max", c_f32), ("eps", c_f32), ("neighbourhood", c_i32),
-                ("ball_r", c_f32), ("k_min", c_i32)]
+                ("ball_r", c_f32), ("k_min", c_i32), ("f64_sums", c_i32)]
 
 
 class gpf_grid_config(ctypes.Structure):
@@ -60,8 +68,9 @@ class gpf_grid_config(ctypes.Structure):
 
 
 class gpf_index_stats_t(ctypes.Structure):
-    _fields_ = [("n_pairs", c_i64), ("n_active", c_i64), ("n_occupied", c_i64),
-                ("overflow", c_i32), ("reserved", c_i32)]
+    _fields_ = [("n_pairs", c_i64), ("n_active", c_i64), ("n_live", c_i64), ("n_small", c_i64),
+                ("n_huge", c_i64), ("n_split", c_i64), ("level_mask", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("overflow", c_i32), ("reserved", c_i32)]
 
 
 class gpf_field_grad(ctypes.Structure):
@@ -71,7 +80,7 @@ class gpf_field_grad(ctypes.Structure):
 
 class gpf_adam_hparams(ctypes.Structure):
     _fields_ = [("lr", c_f32 * 4), ("beta1", c_f32), ("beta2", c_f32), ("eps", c_f32),
-                ("step", c_i32), ("step_counter", c_vp)]
+                ("step", c_i32), ("step_counter", c_vp), ("guard", c_vp)]
 
 
 # name -> (restype, argtypes); every symbol include/gpf.h declares
@@ -85,6 +94,7 @@ SIGNATURES = {
     "gpf_build_index": (c_i32, [c_vp, ctypes.POINTER(gpf_field), ctypes.POINTER(gpf_queries),
                                 c_vp, ctypes.c_size_t, c_vp]),
     "gpf_index_stats": (c_i32, [c_vp, ctypes.POINTER(gpf_index_stats_t), c_vp]),
+    "gpf_index_flags_async": (c_i32, [c_vp, c_vp, c_vp]),
     "gpf_radiance_fwd": (c_i32, [c_vp, ctypes.POINTER(gpf_field), ctypes.POINTER(gpf_queries),
                                  ctypes.POINTER(gpf_query_params), c_vp, c_vp, c_vp]),
     "gpf_count_pairs": (c_i32, [c_vp, ctypes.POINTER(gpf_field), ctypes.POINTER(gpf_queries),
@@ -107,6 +117,8 @@ SIGNATURES = {
                                ctypes.POINTER(c_i32), c_vp]),
     "gpf_sort_pairs_check": (c_i32, [c_vp, c_vp]),
     "gpf_test_sort_wait_timeout": (c_i32, [ctypes.c_uint32, c_vp]),
+    "gpf_measure_alu_peak": (c_i32, [c_i32, c_i32, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None

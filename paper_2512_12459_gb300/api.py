@@ -20,6 +20,7 @@ from ._abi import (GPF_DISK_KDE, GPF_NB_BALL_KNN, GPF_NB_KSIGMA, GPF_NORMALIZED,
 __all__ = [
     "GPF_SUM", "GPF_NORMALIZED", "GPF_DISK_KDE", "GPFError", "GridConfig", "Field", "Queries", "Index",
     "grid_for_bounds", "gpf_radiance_fwd", "gpf_radiance_bwd", "gpf_mse_loss_grad",
+    "gpf_mse_workspace",
     "gpf_adam_step", "AdamState", "PAPER_R", "PAPER_EPS", "PAPER_LR",
 ]
 
@@ -287,14 +288,29 @@ class Index:
         self._timing = (fwd, bwd)   # keep the events alive while they are set
         check(self._lib.gpf_index_set_timing_events(self._h, *hs), "gpf_index_set_timing_events")
 
-    def stats(self, stream=None) -> dict:
-        """gpf_index_stats (synchronises the stream)."""
+    def stats(self, stream=None, raise_on_flags: bool = False) -> dict:
+        """gpf_index_stats (synchronises the stream): the counters of the last
+        build and its device flags (GPF_FLAG_* bits in "flags"; "overflow"
+        is the capacity bit). A set flag raises GPFError only with
+        raise_on_flags; other failures always raise."""
         st = _abi.gpf_index_stats_t()
         status = self._lib.gpf_index_stats(self._h, ctypes.byref(st), _stream(stream))
-        out = {"n_pairs": st.n_pairs, "n_active": st.n_active, "overflow": bool(st.overflow)}
-        if status not in (_abi.GPF_OK, _abi.GPF_ERR_CAPACITY):
+        out = {"n_pairs": st.n_pairs, "n_active": st.n_active, "n_live": st.n_live,
+               "n_small": st.n_small, "n_huge": st.n_huge, "n_split": st.n_split,
+               "level_mask": st.level_mask, "flags": st.flags, "overflow": bool(st.overflow)}
+        flag_status = (_abi.GPF_ERR_CAPACITY, _abi.GPF_ERR_TIMEOUT, _abi.GPF_ERR_NONFINITE)
+        if status != _abi.GPF_OK and (raise_on_flags or status not in flag_status):
             check(status, "gpf_index_stats")
         return out
+
+    def flags_async(self, flags: torch.Tensor, stream=None) -> None:
+        """gpf_index_flags_async: enqueue a write of the last build's device
+        flags (GPF_FLAG_* bits, 0 = usable) into `flags`, a 1-element int32
+        CUDA tensor, without synchronising."""
+        if flags.dtype != torch.int32 or not flags.is_cuda or flags.numel() < 1:
+            raise ValueError("flags must be an int32 CUDA tensor with at least one element")
+        check(self._lib.gpf_index_flags_async(self._h, flags.data_ptr(), _stream(stream)),
+              "gpf_index_flags_async")
 
 
 def _event_handle(ev):
@@ -308,9 +324,10 @@ def _event_handle(ev):
     return h
 
 
-def _params(mode, r_max, eps, neighbourhood=0, ball_r=0.0, k_min=0) -> _abi.gpf_query_params:
+def _params(mode, r_max, eps, neighbourhood=0, ball_r=0.0, k_min=0,
+            f64_sums=False) -> _abi.gpf_query_params:
     return _abi.gpf_query_params(int(mode), float(r_max), float(eps), int(neighbourhood),
-                                 float(ball_r), int(k_min))
+                                 float(ball_r), int(k_min), 1 if f64_sums else 0)
 
 
 def gpf_radiance_fwd(index: Index, field: Field, queries: Queries, mode: int = GPF_SUM,
@@ -350,6 +367,15 @@ def gpf_count_pairs(index: Index, field: Field, queries: Queries, stream=None) -
     return {"candidates": int(c[0]), "included": int(c[1])}
 
 
+def gpf_measure_alu_peak(which: int = _abi.GPF_PEAK_FP32_FMA, iters: int = 4096) -> dict:
+    """gpf_measure_alu_peak: measured FP32 FMA flop/s (which=GPF_PEAK_FP32_FMA)
+    or ex2 results/s (GPF_PEAK_EX2) of the current device (synchronous)."""
+    rate, sec = ctypes.c_double(), ctypes.c_double()
+    check(load().gpf_measure_alu_peak(int(which), int(iters), ctypes.byref(rate),
+                                      ctypes.byref(sec)), "gpf_measure_alu_peak")
+    return {"per_second": float(rate.value), "seconds": float(sec.value)}
+
+
 def gpf_launch_count() -> int:
     """Kernels libgpf has launched in this process."""
     return int(load().gpf_launch_count())
@@ -359,10 +385,11 @@ def gpf_radiance_bwd(index: Index, field: Field, queries: Queries, grad_out: tor
                      out: Optional[torch.Tensor] = None, z: Optional[torch.Tensor] = None,
                      mode: int = GPF_SUM, r_max: float = math.inf, eps: float = PAPER_EPS,
                      grads: Optional[Field] = None, accumulate: bool = False,
-                     stream=None, neighbourhood: int = 0) -> Field:
+                     stream=None, neighbourhood: int = 0, f64_sums: bool = False) -> Field:
     """Gradients (a Field of tensors) of sum(grad_out * O) w.r.t. mean, quat,
     logscale and spectrum (the k-sigma neighbourhood; the library refuses
-    others)."""
+    others). f64_sums=True runs the float64 gradient-check build of the
+    per-Gaussian sums (gpf_query_params.f64_sums)."""
     m, c = queries.m, field.channels
     _need(grad_out, "grad_out", c, m)
     if grads is None:       # float32 gradients for either storage
@@ -377,7 +404,8 @@ def gpf_radiance_bwd(index: Index, field: Field, queries: Queries, grad_out: tor
             raise ValueError("GPF_NORMALIZED backward needs the forward's out and z")
         _need(out, "out", c, m)
         _need(z, "z", 0, m)
-    fs, qs, ps = field.c_struct(), queries.c_struct(c), _params(mode, r_max, eps, neighbourhood)
+    fs, qs = field.c_struct(), queries.c_struct(c)
+    ps = _params(mode, r_max, eps, neighbourhood, f64_sums=f64_sums)
     gs = _abi.gpf_field_grad(_ptr(grads.mean), _ptr(grads.quat), _ptr(grads.logscale),
                              _ptr(grads.spectrum), 1 if accumulate else 0, 0)
     check(index._lib.gpf_radiance_bwd(index.handle, ctypes.byref(fs), ctypes.byref(qs),
@@ -413,24 +441,43 @@ def gpf_sort_pairs(keys: torch.Tensor, vals: torch.Tensor, bits: int = 32, check
 
 
 class _MseWorkspace:
+    """Scratch of gpf_mse_loss_grad, one buffer per (size, device, stream).
+    Each buffer is allocated while its stream is current, so PyTorch's caching
+    allocator hands its memory to another tensor only after the work queued
+    on that stream has used it; calls on different streams never share one."""
     cache = {}
+    max_entries = 16
 
     @classmethod
-    def get(cls, m: int, device) -> torch.Tensor:
-        key = (m, str(device))
+    def get(cls, m: int, device, stream) -> torch.Tensor:
+        key = (m, str(device), stream.cuda_stream)
         ws = cls.cache.get(key)
         if ws is None:
             sz = ctypes.c_size_t()
             check(load().gpf_mse_workspace_size(m, ctypes.byref(sz)), "gpf_mse_workspace_size")
-            ws = torch.empty(max(int(sz.value), 256), dtype=torch.uint8, device=device)
-            cls.cache = {key: ws}
+            with torch.cuda.stream(stream):
+                ws = torch.empty(max(int(sz.value), 256), dtype=torch.uint8, device=device)
+            if len(cls.cache) >= cls.max_entries:
+                cls.cache.pop(next(iter(cls.cache)))
+            cls.cache[key] = ws
         return ws
+
+
+def gpf_mse_workspace(m: int, device="cuda") -> torch.Tensor:
+    """A device scratch buffer for gpf_mse_loss_grad over m hit points (for
+    callers that keep their own, e.g. a step captured as a CUDA graph)."""
+    sz = ctypes.c_size_t()
+    check(load().gpf_mse_workspace_size(m, ctypes.byref(sz)), "gpf_mse_workspace_size")
+    return torch.empty(max(int(sz.value), 256), dtype=torch.uint8, device=device)
 
 
 def gpf_mse_loss_grad(out: torch.Tensor, target: torch.Tensor,
                       valid: Optional[torch.Tensor] = None, loss: Optional[torch.Tensor] = None,
-                      grad: Optional[torch.Tensor] = None, stream=None):
-    """MSE loss (a 1-element CUDA tensor) and its gradient with respect to out."""
+                      grad: Optional[torch.Tensor] = None, stream=None,
+                      workspace: Optional[torch.Tensor] = None):
+    """MSE loss (a 1-element CUDA tensor) and its gradient with respect to out.
+    workspace: a buffer from gpf_mse_workspace(m), or None for one cached per
+    (size, device, stream)."""
     c, m = int(out.shape[0]), int(out.shape[1])
     _need(out, "out", c, m)
     _need(target, "target", c, m)
@@ -440,10 +487,11 @@ def gpf_mse_loss_grad(out: torch.Tensor, target: torch.Tensor,
         loss = torch.empty((1,), dtype=torch.float32, device=out.device)
     if grad is None:
         grad = torch.empty_like(out)
-    ws = _MseWorkspace.get(m, out.device)
+    st = stream if stream is not None else torch.cuda.current_stream(out.device)
+    ws = workspace if workspace is not None else _MseWorkspace.get(m, out.device, st)
     check(load().gpf_mse_loss_grad(m, c, out.data_ptr(), target.data_ptr(), _ptr(valid),
                                    loss.data_ptr(), grad.data_ptr(), ws.data_ptr(), ws.numel(),
-                                   _stream(stream)), "gpf_mse_loss_grad")
+                                   st.cuda_stream), "gpf_mse_loss_grad")
     return loss, grad
 
 
@@ -473,19 +521,24 @@ def _grad_struct(f: Field) -> _abi.gpf_field_grad:
 
 
 def gpf_adam_step(params: Field, grads: Field, state: AdamState, lr=PAPER_LR, beta1: float = 0.9,
-                  beta2: float = 0.999, eps: float = 1e-8, stream=None) -> None:
-    """One Adam update of params in place; state.step is incremented first."""
+                  beta2: float = 0.999, eps: float = 1e-8, stream=None,
+                  guard: Optional[Index] = None) -> None:
+    """One Adam update of params in place; state.step is incremented first
+    (host count). guard: an Index whose last build, if it set a device flag,
+    cancels the update on the device (parameters, moments and the device
+    step counter stay as they were)."""
     lrs = list(lr) if isinstance(lr, (list, tuple)) else [float(lr)] * 4
     for g, p in zip(grads.tensors() + state.m.tensors() + state.v.tensors(), params.tensors() * 3):
         _need(g, "adam tensor", p.shape[0], p.shape[1])
     fs = params.c_struct()
     if state.step_counter is not None:
         hp = _abi.gpf_adam_hparams((ctypes.c_float * 4)(*lrs), beta1, beta2, eps, 0,
-                                   state.step_counter.data_ptr())
+                                   state.step_counter.data_ptr(),
+                                   guard.handle if guard is not None else None)
     else:
         state.step += 1
         hp = _abi.gpf_adam_hparams((ctypes.c_float * 4)(*lrs), beta1, beta2, eps, state.step,
-                                   None)
+                                   None, guard.handle if guard is not None else None)
     g, m, v = _grad_struct(grads), _grad_struct(state.m), _grad_struct(state.v)
     check(load().gpf_adam_step(ctypes.byref(fs), ctypes.byref(g), ctypes.byref(m),
                                ctypes.byref(v), ctypes.byref(hp), _stream(stream)),

@@ -106,8 +106,9 @@ size_t layout(const gpf_index* ix, char* base, IndexBuffers* b) {
   }
   t.qstart = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * ncp));
   t.qrec = reinterpret_cast<float*>(take(sizeof(float) * M * qrec_stride(d.channels)));
-  t.gacc = reinterpret_cast<float*>(take(sizeof(float) * N * gacc_stride(d.channels)));
-  t.bpart = reinterpret_cast<float*>(take(sizeof(float) * std::min<int64_t>(N, kSplitMax) *
+  // room for float64 sums (the gradient-check build of the backward)
+  t.gacc = reinterpret_cast<float*>(take(sizeof(double) * N * gacc_stride(d.channels)));
+  t.bpart = reinterpret_cast<float*>(take(sizeof(double) * std::min<int64_t>(N, kSplitMax) *
                                           kSplitWays * gacc_stride(d.channels)));
   for (int k = 0; k < 2; ++k) {
     t.gkey[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (P > 0 ? P : 1)));
@@ -182,6 +183,8 @@ gpf_status check_params(const gpf_query_params* p) {
     if (p->k_min < 0 || p->k_min > GPF_MAX_KMIN)
       return fail(GPF_ERR_INVALID_ARG, "params.k_min = %d outside 0..%d", p->k_min, GPF_MAX_KMIN);
   }
+  if (p->f64_sums != 0 && p->f64_sums != 1)
+    return fail(GPF_ERR_INVALID_ARG, "params.f64_sums must be 0 or 1");
   return GPF_OK;
 }
 
@@ -229,6 +232,7 @@ const char* gpf_status_string(gpf_status s) {
     case GPF_ERR_NOT_BUILT: return "GPF_ERR_NOT_BUILT";
     case GPF_ERR_MISMATCH: return "GPF_ERR_MISMATCH";
     case GPF_ERR_TIMEOUT: return "GPF_ERR_TIMEOUT";
+    case GPF_ERR_NONFINITE: return "GPF_ERR_NONFINITE";
   }
   return "GPF_ERR_UNKNOWN";
 }
@@ -387,12 +391,32 @@ gpf_status gpf_index_stats(const gpf_index* index, gpf_index_stats_t* stats, gpf
   memset(stats, 0, sizeof(*stats));
   stats->n_pairs = h.n_pairs;
   stats->n_active = h.n_active;
+  stats->n_live = h.n_live;
+  stats->n_small = h.n_small;
+  stats->n_huge = h.n_huge;
+  stats->n_split = std::min<int64_t>(h.n_huge, kSplitMax);
+  stats->level_mask = h.level_mask;
+  stats->flags = (h.overflow ? GPF_FLAG_CAPACITY : 0u) | (h.stalled ? GPF_FLAG_TIMEOUT : 0u) |
+                 (h.nonfinite ? GPF_FLAG_NONFINITE : 0u);
   stats->overflow = (int32_t)h.overflow;
   if (h.stalled)
     return fail(GPF_ERR_TIMEOUT, "a bounded wait of the index build's sort gave up");
+  if (h.nonfinite)
+    return fail(GPF_ERR_NONFINITE,
+                "a Gaussian parameter or an active hit point of the last build is not finite");
   if (h.overflow)
     return fail(GPF_ERR_CAPACITY, "pair buffer overflow: %u entries needed, capacity %lld",
                 h.n_pairs, (long long)index->dims.p_max);
+  return GPF_OK;
+}
+
+gpf_status gpf_index_flags_async(const gpf_index* index, uint32_t* flags, gpf_stream stream) {
+  if (!index) return fail(GPF_ERR_INVALID_ARG, "index is NULL");
+  GPF_CHECK_PTR(flags, "flags");
+  if (!index->built) return fail(GPF_ERR_NOT_BUILT, "gpf_build_index has not run on this index");
+  const cudaError_t e = launch_index_flags(index->buf.header, flags,
+                                           reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "gpf_index_flags_async");
   return GPF_OK;
 }
 
@@ -404,6 +428,8 @@ gpf_status gpf_radiance_fwd(const gpf_index* index, const gpf_field* field,
   if ((s = check_field(index, field)) != GPF_OK) return s;
   if ((s = check_queries(index, queries)) != GPF_OK) return s;
   if ((s = check_params(params)) != GPF_OK) return s;
+  if (params->f64_sums != 0)
+    return fail(GPF_ERR_INVALID_ARG, "params.f64_sums applies to gpf_radiance_bwd only");
   if ((s = check_same(index, field, queries)) != GPF_OK) return s;
   if (params->neighbourhood == GPF_NB_BALL_KNN) {
     if (index->dims.grid.blevel < 0)
@@ -435,7 +461,7 @@ gpf_status gpf_count_pairs(const gpf_index* index, const gpf_field* field,
   if ((s = check_same(index, field, queries)) != GPF_OK) return s;
   if (!counts || !aligned(counts, 8))
     return fail(GPF_ERR_INVALID_ARG, "counts is NULL or not 8-byte aligned");
-  gpf_query_params p{GPF_SUM, INFINITY, 1e-6f, 0};
+  gpf_query_params p{GPF_SUM, INFINITY, 1e-6f, 0, 0.0f, 0, 0};
   cudaError_t e = launch_forward(index->dims, index->buf, *queries, p, field->n, nullptr, nullptr,
                                  reinterpret_cast<unsigned long long*>(counts), KernelEvents{},
                                  reinterpret_cast<cudaStream_t>(stream));
@@ -563,6 +589,12 @@ gpf_status gpf_adam_step(const gpf_field* params, const gpf_field_grad* grads,
   if (!(hp->beta1 >= 0.0f && hp->beta1 < 1.0f) || !(hp->beta2 >= 0.0f && hp->beta2 < 1.0f))
     return fail(GPF_ERR_INVALID_ARG, "betas must lie in [0, 1)");
   if (!(hp->eps >= 0.0f)) return fail(GPF_ERR_INVALID_ARG, "eps must be >= 0");
+  const DeviceHeader* guard = nullptr;
+  if (hp->guard) {
+    if (!hp->guard->built)
+      return fail(GPF_ERR_NOT_BUILT, "hp.guard: gpf_build_index has not run on that index");
+    guard = hp->guard->buf.header;
+  }
   for (int k = 0; k < 4; ++k)
     if (!isfinite(hp->lr[k]) || hp->lr[k] < 0.0f)
       return fail(GPF_ERR_INVALID_ARG, "lr[%d] must be finite and >= 0", k);
@@ -578,7 +610,8 @@ gpf_status gpf_adam_step(const gpf_field* params, const gpf_field_grad* grads,
         return fail(GPF_ERR_INVALID_ARG, "%s has a NULL array", names[k]);
     }
   }
-  cudaError_t e = launch_adam(*params, *grads, *m, *v, *hp, reinterpret_cast<cudaStream_t>(stream));
+  cudaError_t e =
+      launch_adam(*params, *grads, *m, *v, *hp, guard, reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "gpf_adam_step");
   return GPF_OK;
 }
@@ -646,6 +679,18 @@ gpf_status gpf_sort_pairs_check(const void* workspace, gpf_stream stream) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "gpf_sort_pairs_check");
   if (flag) return fail(GPF_ERR_TIMEOUT, "a bounded wait of the sort gave up");
+  return GPF_OK;
+}
+
+gpf_status gpf_measure_alu_peak(int32_t which, int32_t iters, double* per_second,
+                                double* seconds) {
+  if (which != GPF_PEAK_FP32_FMA && which != GPF_PEAK_EX2)
+    return fail(GPF_ERR_INVALID_ARG, "which = %d is not GPF_PEAK_FP32_FMA or GPF_PEAK_EX2", which);
+  if (iters < 1 || iters > (1 << 20))
+    return fail(GPF_ERR_INVALID_ARG, "iters = %d outside 1 .. 2^20", iters);
+  if (!per_second || !seconds) return fail(GPF_ERR_INVALID_ARG, "per_second or seconds is NULL");
+  const cudaError_t e = measure_alu_peak(which, iters, per_second, seconds);
+  if (e != cudaSuccess) return cuda_fail(e, "gpf_measure_alu_peak");
   return GPF_OK;
 }
 

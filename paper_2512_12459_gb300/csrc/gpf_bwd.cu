@@ -18,6 +18,9 @@
 // the Gaussian's k-sigma bounds overlap, so each pair is seen exactly once,
 // and the sums are reduced inside the warp: no global atomics, bitwise
 // reproducible.
+// The sums have a type T: float in the product path; double in the
+// gradient-check build (gpf_query_params.f64_sums), where the same float32
+// pair terms are accumulated, reduced and turned into gradients in float64.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -47,10 +50,10 @@ struct BwdArgs {
   const float* z;
   int64_t m;
   float* qrec;
-  float* gacc;            // [N * NS] per-Gaussian sums, by Gaussian id
+  void* gacc;             // [N * NS] per-Gaussian sums (type T), by Gaussian id
   const uint8_t* glive;   // [N] 1 if the pair loop visits the Gaussian
   const uint2* qbox;      // [N] query-level cell bounds (pack_qbox), from the build
-  float* bpart;           // [kSplitMax * kSplitWays * NS] split Gaussians' partials
+  void* bpart;            // [kSplitMax * kSplitWays * NS] split Gaussians' partials (T)
   const float* rec;
   const uint4* box;
   const uint32_t* order;  // Gaussian ids in mean-cell order
@@ -59,6 +62,8 @@ struct BwdArgs {
   const float* logscale;
   int mode;
   float r, r2, inv_rr, eps, cut, cut2;
+  double rd, r2d, inv_rrd;  // the falloff parameters in float64 (gradient-check build)
+  int f64;                  // 1: the gradient-check build (float64 pair arithmetic)
   gpf_field_grad g;
   unsigned long long* next_work;  // work counter, zero at launch
 };
@@ -79,9 +84,19 @@ __global__ void pack_qrec_kernel(BwdArgs a) {
   if (a.mode == GPF_NORMALIZED) {
     const float Z = a.z[q];
     if (Z > a.eps) {
-      zeta = 1.0f / Z;
+      if (a.f64) {
+        // the check build rounds each to float32 once
+        double k = 0.0;
 #pragma unroll
-      for (int c = 0; c < C; ++c) kappa = fmaf(a.grad_out[(int64_t)c * a.m + q], a.out[(int64_t)c * a.m + q], kappa);
+        for (int c = 0; c < C; ++c)
+          k = fma((double)a.grad_out[(int64_t)c * a.m + q], (double)a.out[(int64_t)c * a.m + q], k);
+        kappa = (float)k;
+        zeta = (float)(1.0 / (double)Z);
+      } else {
+        zeta = 1.0f / Z;
+#pragma unroll
+        for (int c = 0; c < C; ++c) kappa = fmaf(a.grad_out[(int64_t)c * a.m + q], a.out[(int64_t)c * a.m + q], kappa);
+      }
     } else {
       zeta = 1.0f / a.eps;
     }
@@ -98,31 +113,44 @@ __global__ void pack_qrec_kernel(BwdArgs a) {
   for (int c = 5 + C; c < QS; ++c) r[c] = 0.0f;
 }
 
-template <int C>
+// acc += a * b and acc += a for float32 terms a, b into sums of type T:
+// one fused multiply-add in float32, or the exact float64 product and sum.
+template <typename T>
+__device__ __forceinline__ void mac(T& acc, float a, float b) {
+  if constexpr (sizeof(T) == 4) acc = fmaf(a, b, acc);
+  else acc = fma((double)a, (double)b, acc);
+}
+template <typename T>
+__device__ __forceinline__ T fmaT(T a, T b, T c) {
+  if constexpr (sizeof(T) == 4) return fmaf(a, b, c);
+  else return fma(a, b, c);
+}
+
+template <int C, typename T>
 struct Acc {
-  float A00, A01, A02, A11, A12, A22;
-  float B0, B1, B2;
-  float D0, D1, D2;
-  float P[C];
+  T A00, A01, A02, A11, A12, A22;
+  T B0, B1, B2;
+  T D0, D1, D2;
+  T P[C];
   __device__ void zero() {
-    A00 = A01 = A02 = A11 = A12 = A22 = 0.f;
-    B0 = B1 = B2 = 0.f;
-    D0 = D1 = D2 = 0.f;
+    A00 = A01 = A02 = A11 = A12 = A22 = T(0);
+    B0 = B1 = B2 = T(0);
+    D0 = D1 = D2 = T(0);
 #pragma unroll
-    for (int c = 0; c < C; ++c) P[c] = 0.f;
+    for (int c = 0; c < C; ++c) P[c] = T(0);
   }
   // The sums as an array of NS slots (zero padded): 16 for C <= 4, else 32.
   static constexpr int NV = 12 + C;
   static constexpr int NS = NV <= 16 ? 16 : 32;
-  __device__ void to_array(float (&v)[NS]) const {
+  __device__ void to_array(T (&v)[NS]) const {
     v[0] = A00; v[1] = A01; v[2] = A02; v[3] = A11; v[4] = A12; v[5] = A22;
     v[6] = B0; v[7] = B1; v[8] = B2; v[9] = D0; v[10] = D1; v[11] = D2;
 #pragma unroll
     for (int c = 0; c < C; ++c) v[12 + c] = P[c];
 #pragma unroll
-    for (int i = NV; i < NS; ++i) v[i] = 0.f;
+    for (int i = NV; i < NS; ++i) v[i] = T(0);
   }
-  __device__ void from_array(const float* v) {
+  __device__ void from_array(const T* v) {
     A00 = v[0]; A01 = v[1]; A02 = v[2]; A11 = v[3]; A12 = v[4]; A22 = v[5];
     B0 = v[6]; B1 = v[7]; B2 = v[8]; D0 = v[9]; D1 = v[10]; D2 = v[11];
 #pragma unroll
@@ -135,8 +163,8 @@ struct Acc {
 // holds and keeps the other half, so NS - 1 shuffles leave every lane with
 // one complete sum (for NS = 16 lanes l and l ^ 1 hold the same one). The
 // slot a lane ends with is returned in *slot.
-template <int NS>
-__device__ __forceinline__ float reduce_scatter(float (&v)[NS], int lane, int* slot) {
+template <int NS, typename T>
+__device__ __forceinline__ T reduce_scatter(T (&v)[NS], int lane, int* slot) {
   constexpr int kStages = NS == 16 ? 4 : 5;
   int idx = 0;
 #pragma unroll
@@ -146,8 +174,8 @@ __device__ __forceinline__ float reduce_scatter(float (&v)[NS], int lane, int* s
     if (up) idx += h;
 #pragma unroll
     for (int i = 0; i < h; ++i) {
-      const float send = up ? v[i] : v[i + h];
-      const float keep = up ? v[i + h] : v[i];
+      const T send = up ? v[i] : v[i + h];
+      const T keep = up ? v[i + h] : v[i];
       v[i] = keep + __shfl_xor_sync(kFullMask, send, o);
     }
   }
@@ -159,6 +187,22 @@ __device__ __forceinline__ float reduce_scatter(float (&v)[NS], int lane, int* s
 struct GaussianRegs {
   float mx, my, mz;
   float M[9];
+};
+
+// A Gaussian as a pair loop holds it: its float32 record (mean, M = S^-1 R^T,
+// Phi; the cull reads it too) and, for float64 sums, the same quantities in
+// float64 computed from the raw parameters (R(q / |q|) and s = exp(l) in
+// float64), so that the gradient-check build rounds nothing below float64.
+template <int C, typename T>
+struct PairG {
+  GaussianRegs G;
+  float phi[C];
+};
+template <int C>
+struct PairG<C, double> {
+  GaussianRegs G;
+  float phi[C];
+  double mx, my, mz, M[9], phid[C];
 };
 
 // A packed hit point, all of it (one 32-byte sector for C <= 3): the loads
@@ -173,11 +217,68 @@ __device__ __forceinline__ void load_qrec(const float* __restrict__ qr,
   }
 }
 
-// One (Gaussian, hit point) pair of the backward, the hit point in q.
+// One (Gaussian, hit point) pair of the backward in float64 (the
+// gradient-check build): the steps of the float32 pair below, in float64.
 template <int C, bool PSI>
-__device__ __forceinline__ void bwd_pair_q(const GaussianRegs& G, const float (&phi)[C],
+__device__ __forceinline__ void bwd_pair_q64(const PairG<C, double>& P,
+                                             const float (&q)[qrec_stride(C)], const BwdArgs& a,
+                                             Acc<C, double>& acc) {
+  const double dx = (double)q[0] - P.mx, dy = (double)q[1] - P.my, dz = (double)q[2] - P.mz;
+  const double u0 = fma(P.M[0], dx, fma(P.M[1], dy, P.M[2] * dz));
+  const double u1 = fma(P.M[3], dx, fma(P.M[4], dy, P.M[5] * dz));
+  const double u2 = fma(P.M[6], dx, fma(P.M[7], dy, P.M[8] * dz));
+  const double Q = fma(u0, u0, fma(u1, u1, u2 * u2));
+  if (!(Q <= (double)a.cut2)) return;
+  const float* qv = q + 4;
+  double e = -0.5 * Q;
+  double pcoef = 0.0;
+  if (PSI) {
+    const double d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    if (d2 > a.r2d) {
+      const double dist = sqrt(d2);
+      const double t = (dist - a.rd) * a.inv_rrd;
+      e = fma(-3.0 * t, t, e);
+      pcoef = 6.0 * t * a.inv_rrd / dist;
+    }
+  }
+  const double w = exp(e);
+  const double zeta = q[3], kappa = qv[0];
+  double gp = 0.0;
+#pragma unroll
+  for (int c = 0; c < C; ++c) gp = fma((double)qv[1 + c], P.phid[c], gp);
+  const double bw = zeta * (gp - kappa) * w;
+  const double b0 = bw * u0, b1 = bw * u1, b2 = bw * u2;
+  acc.A00 = fma(b0, u0, acc.A00);
+  acc.A01 = fma(b0, u1, acc.A01);
+  acc.A02 = fma(b0, u2, acc.A02);
+  acc.A11 = fma(b1, u1, acc.A11);
+  acc.A12 = fma(b1, u2, acc.A12);
+  acc.A22 = fma(b2, u2, acc.A22);
+  acc.B0 += b0;
+  acc.B1 += b1;
+  acc.B2 += b2;
+  if (PSI) {
+    const double pc = bw * pcoef;
+    acc.D0 = fma(pc, dx, acc.D0);
+    acc.D1 = fma(pc, dy, acc.D1);
+    acc.D2 = fma(pc, dz, acc.D2);
+  }
+  const double wz = w * zeta;
+#pragma unroll
+  for (int c = 0; c < C; ++c) acc.P[c] = fma((double)qv[1 + c], wz, acc.P[c]);
+}
+
+// One (Gaussian, hit point) pair of the backward, the hit point in q.
+template <int C, bool PSI, typename T>
+__device__ __forceinline__ void bwd_pair_q(const PairG<C, T>& P,
                                            const float (&q)[qrec_stride(C)], const BwdArgs& a,
-                                           Acc<C>& acc) {
+                                           Acc<C, T>& acc) {
+  if constexpr (sizeof(T) == 8) {
+    bwd_pair_q64<C, PSI>(P, q, a, acc);
+    return;
+  } else {
+  const GaussianRegs& G = P.G;
+  const float (&phi)[C] = P.phi;
   const float dx = q[0] - G.mx, dy = q[1] - G.my, dz = q[2] - G.mz;
   const float u0 = fmaf(G.M[0], dx, fmaf(G.M[1], dy, G.M[2] * dz));
   const float u1 = fmaf(G.M[3], dx, fmaf(G.M[4], dy, G.M[5] * dz));
@@ -205,53 +306,59 @@ __device__ __forceinline__ void bwd_pair_q(const GaussianRegs& G, const float (&
   for (int c = 0; c < C; ++c) gp = fmaf(qv[1 + c], phi[c], gp);
   const float bw = zeta * (gp - kappa) * w;
   const float b0 = bw * u0, b1 = bw * u1, b2 = bw * u2;
-  acc.A00 = fmaf(b0, u0, acc.A00);
-  acc.A01 = fmaf(b0, u1, acc.A01);
-  acc.A02 = fmaf(b0, u2, acc.A02);
-  acc.A11 = fmaf(b1, u1, acc.A11);
-  acc.A12 = fmaf(b1, u2, acc.A12);
-  acc.A22 = fmaf(b2, u2, acc.A22);
-  acc.B0 += b0;
-  acc.B1 += b1;
-  acc.B2 += b2;
+  mac(acc.A00, b0, u0);
+  mac(acc.A01, b0, u1);
+  mac(acc.A02, b0, u2);
+  mac(acc.A11, b1, u1);
+  mac(acc.A12, b1, u2);
+  mac(acc.A22, b2, u2);
+  acc.B0 += (T)b0;
+  acc.B1 += (T)b1;
+  acc.B2 += (T)b2;
   if (PSI) {
     const float pc = bw * pcoef;
-    acc.D0 = fmaf(pc, dx, acc.D0);
-    acc.D1 = fmaf(pc, dy, acc.D1);
-    acc.D2 = fmaf(pc, dz, acc.D2);
+    mac(acc.D0, pc, dx);
+    mac(acc.D1, pc, dy);
+    mac(acc.D2, pc, dz);
   }
   const float wz = w * zeta;
 #pragma unroll
-  for (int c = 0; c < C; ++c) acc.P[c] = fmaf(qv[1 + c], wz, acc.P[c]);
+  for (int c = 0; c < C; ++c) mac(acc.P[c], qv[1 + c], wz);
+  }
 }
 
-template <int C, bool PSI>
-__device__ __forceinline__ void bwd_pair(const GaussianRegs& G, const float (&phi)[C],
-                                         const float* __restrict__ qr, const BwdArgs& a,
-                                         Acc<C>& acc) {
+template <int C, bool PSI, typename T>
+__device__ __forceinline__ void bwd_pair(const PairG<C, T>& P, const float* __restrict__ qr,
+                                         const BwdArgs& a, Acc<C, T>& acc) {
   float q[qrec_stride(C)];
   load_qrec<C>(qr, q);
-  bwd_pair_q<C, PSI>(G, phi, q, a, acc);
+  bwd_pair_q<C, PSI, T>(P, q, a, acc);
 }
 
-// Gradients of one Gaussian from its reduced sums (runs on one lane).
-template <int C>
-__device__ void bwd_epilogue(const BwdArgs& a, int64_t gi, const Frame& fr, const Acc<C>& acc) {
+// Gradients of one Gaussian from its reduced sums (runs on one lane), in
+// the sums' type T.
+template <int C, typename T>
+__device__ void bwd_epilogue(const BwdArgs& a, int64_t gi, const Frame& fr, const Acc<C, T>& acc) {
   const int64_t n = a.n;
-  const float (&R)[3][3] = fr.R;
-  const float (&s)[3] = fr.s;
-  const float qw = fr.qhat[0], qx = fr.qhat[1], qy = fr.qhat[2], qz = fr.qhat[3];
-  const float iq = fr.inv_qn;
-  const float A[3][3] = {{acc.A00, acc.A01, acc.A02}, {acc.A01, acc.A11, acc.A12},
-                         {acc.A02, acc.A12, acc.A22}};
-  const float B[3] = {acc.B0, acc.B1, acc.B2};
-  const float D[3] = {acc.D0, acc.D1, acc.D2};
-  float dmu[3], dl[3], dR[3][3];
+  T R[3][3], s[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    s[k] = (T)fr.s[k];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) R[k][j] = (T)fr.R[k][j];
+  }
+  const T qw = fr.qhat[0], qx = fr.qhat[1], qy = fr.qhat[2], qz = fr.qhat[3];
+  const T iq = fr.inv_qn;
+  const T A[3][3] = {{acc.A00, acc.A01, acc.A02}, {acc.A01, acc.A11, acc.A12},
+                     {acc.A02, acc.A12, acc.A22}};
+  const T B[3] = {acc.B0, acc.B1, acc.B2};
+  const T D[3] = {acc.D0, acc.D1, acc.D2};
+  T dmu[3], dl[3], dR[3][3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     dmu[k] = D[k];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) dmu[k] = fmaf(R[k][j] / s[j], B[j], dmu[k]);
+    for (int j = 0; j < 3; ++j) dmu[k] = fmaT<T>(R[k][j] / s[j], B[j], dmu[k]);
   }
 #pragma unroll
   for (int j = 0; j < 3; ++j) dl[j] = A[j][j];
@@ -259,41 +366,41 @@ __device__ void bwd_epilogue(const BwdArgs& a, int64_t gi, const Frame& fr, cons
   for (int k = 0; k < 3; ++k)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      float t = 0.0f;
+      T t = T(0);
 #pragma unroll
-      for (int mm = 0; mm < 3; ++mm) t = fmaf(R[k][mm] * s[mm], A[j][mm], t);
+      for (int mm = 0; mm < 3; ++mm) t = fmaT<T>(R[k][mm] * s[mm], A[j][mm], t);
       dR[k][j] = -t / s[j];
     }
   // d loss / d qhat through the entries of R(qhat)
-  const float gw = 2.0f * (-qz * dR[0][1] + qy * dR[0][2] + qz * dR[1][0] - qx * dR[1][2] -
-                           qy * dR[2][0] + qx * dR[2][1]);
-  const float gx = 2.0f * (qy * dR[0][1] + qz * dR[0][2] + qy * dR[1][0] - 2.0f * qx * dR[1][1] -
-                           qw * dR[1][2] + qz * dR[2][0] + qw * dR[2][1] - 2.0f * qx * dR[2][2]);
-  const float gy = 2.0f * (-2.0f * qy * dR[0][0] + qx * dR[0][1] + qw * dR[0][2] + qx * dR[1][0] +
-                           qz * dR[1][2] - qw * dR[2][0] + qz * dR[2][1] - 2.0f * qy * dR[2][2]);
-  const float gz = 2.0f * (-2.0f * qz * dR[0][0] - qw * dR[0][1] + qx * dR[0][2] + qw * dR[1][0] -
-                           2.0f * qz * dR[1][1] + qy * dR[1][2] + qx * dR[2][0] + qy * dR[2][1]);
+  const T gw = T(2) * (-qz * dR[0][1] + qy * dR[0][2] + qz * dR[1][0] - qx * dR[1][2] -
+                       qy * dR[2][0] + qx * dR[2][1]);
+  const T gx = T(2) * (qy * dR[0][1] + qz * dR[0][2] + qy * dR[1][0] - T(2) * qx * dR[1][1] -
+                       qw * dR[1][2] + qz * dR[2][0] + qw * dR[2][1] - T(2) * qx * dR[2][2]);
+  const T gy = T(2) * (-T(2) * qy * dR[0][0] + qx * dR[0][1] + qw * dR[0][2] + qx * dR[1][0] +
+                       qz * dR[1][2] - qw * dR[2][0] + qz * dR[2][1] - T(2) * qy * dR[2][2]);
+  const T gz = T(2) * (-T(2) * qz * dR[0][0] - qw * dR[0][1] + qx * dR[0][2] + qw * dR[1][0] -
+                       T(2) * qz * dR[1][1] + qy * dR[1][2] + qx * dR[2][0] + qy * dR[2][1]);
   // through qhat = q / |q|
-  const float dot = qw * gw + qx * gx + qy * gy + qz * gz;
-  const float dq[4] = {(gw - qw * dot) * iq, (gx - qx * dot) * iq, (gy - qy * dot) * iq,
-                       (gz - qz * dot) * iq};
+  const T dot = qw * gw + qx * gx + qy * gy + qz * gz;
+  const T dq[4] = {(gw - qw * dot) * iq, (gx - qx * dot) * iq, (gy - qy * dot) * iq,
+                   (gz - qz * dot) * iq};
   const bool accu = a.g.accumulate != 0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     float* p = a.g.mean + k * n + gi;
-    *p = accu ? *p + dmu[k] : dmu[k];
+    *p = accu ? (float)((T)*p + dmu[k]) : (float)dmu[k];
     float* pl = a.g.logscale + k * n + gi;
-    *pl = accu ? *pl + dl[k] : dl[k];
+    *pl = accu ? (float)((T)*pl + dl[k]) : (float)dl[k];
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     float* p = a.g.quat + k * n + gi;
-    *p = accu ? *p + dq[k] : dq[k];
+    *p = accu ? (float)((T)*p + dq[k]) : (float)dq[k];
   }
 #pragma unroll
   for (int c = 0; c < C; ++c) {
     float* p = a.g.spectrum + (int64_t)c * n + gi;
-    *p = accu ? *p + acc.P[c] : acc.P[c];
+    *p = accu ? (float)((T)*p + acc.P[c]) : (float)acc.P[c];
   }
 }
 
@@ -313,33 +420,70 @@ __device__ __forceinline__ void load_gaussian(const BwdArgs& a, int64_t gi, Gaus
   for (int c = 0; c < C; ++c) phi[c] = r[13 + c];
 }
 
+template <int C, typename T>
+__device__ __forceinline__ void load_pair_gaussian(const BwdArgs& a, int64_t gi, PairG<C, T>& P) {
+  load_gaussian<C>(a, gi, P.G, P.phi);
+  if constexpr (sizeof(T) == 8) {
+    const int64_t n = a.n;
+    double qw = a.quat[gi], qx = a.quat[n + gi], qy = a.quat[2 * n + gi], qz = a.quat[3 * n + gi];
+    const double qn = sqrt(qw * qw + qx * qx + qy * qy + qz * qz);
+    const double iq = qn > 0.0 ? 1.0 / qn : 0.0;
+    qw *= iq; qx *= iq; qy *= iq; qz *= iq;
+    const double R[3][3] = {
+        {1.0 - 2.0 * (qy * qy + qz * qz), 2.0 * (qx * qy - qw * qz), 2.0 * (qx * qz + qw * qy)},
+        {2.0 * (qx * qy + qw * qz), 1.0 - 2.0 * (qx * qx + qz * qz), 2.0 * (qy * qz - qw * qx)},
+        {2.0 * (qx * qz - qw * qy), 2.0 * (qy * qz + qw * qx), 1.0 - 2.0 * (qx * qx + qy * qy)}};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double inv_s = exp(-(double)a.logscale[j * n + gi]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) P.M[3 * j + k] = R[k][j] * inv_s;
+    }
+    P.mx = P.G.mx; P.my = P.G.my; P.mz = P.G.mz;
+#pragma unroll
+    for (int c = 0; c < C; ++c) P.phid[c] = P.phi[c];
+  }
+}
+
+// Stores NS sums of type T (16-byte vectors).
+template <int NS, typename T>
+__device__ __forceinline__ void store_sums(T* dst, const T (&v)[NS]) {
+  if constexpr (sizeof(T) == 4) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int i = 0; i < NS / 4; ++i)
+      d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  } else {
+    double2* d2 = reinterpret_cast<double2*>(dst);
+#pragma unroll
+    for (int i = 0; i < NS / 2; ++i) d2[i] = make_double2(v[2 * i], v[2 * i + 1]);
+  }
+}
+
 // One lane runs one small Gaussian (bounds within 2 x 2 x 2 query-level
 // cells) alone: no reduction across lanes, the epilogues run side by side.
-template <int C, bool PSI>
+template <int C, bool PSI, typename T>
 __device__ void bwd_lane_gaussian(const BwdArgs& a, int64_t gi) {
   constexpr int QS = qrec_stride(C);
+  constexpr int NS = Acc<C, T>::NS;
   const Grid& Gd = a.grid;
-  GaussianRegs G;
-  float phi[C];
-  load_gaussian<C>(a, gi, G, phi);
+  PairG<C, T> P;
+  load_pair_gaussian<C, T>(a, gi, P);
   uint32_t lo[3], hi[3];
   unpack_qbox(a.qbox[gi], lo, hi);
   const uint32_t lx = lo[0], hx = hi[0], ly = lo[1], hy = hi[1], lz = lo[2], hz = hi[2];
-  Acc<C> acc;
+  Acc<C, T> acc;
   acc.zero();
   for (uint32_t iz = lz; iz <= hz; ++iz)
     for (uint32_t iy = ly; iy <= hy; ++iy) {
       const uint32_t key = qkey_of(Gd, lx, iy, iz);
       const uint32_t e = a.qstart[key + (hx - lx) + 1];
       for (uint32_t k = a.qstart[key]; k < e; ++k)
-        bwd_pair<C, PSI>(G, phi, a.qrec + (int64_t)k * QS, a, acc);
+        bwd_pair<C, PSI, T>(P, a.qrec + (int64_t)k * QS, a, acc);
     }
-  float v[Acc<C>::NS];
+  T v[NS];
   acc.to_array(v);
-  float4* dst = reinterpret_cast<float4*>(a.gacc + gi * Acc<C>::NS);
-#pragma unroll
-  for (int i = 0; i < Acc<C>::NS / 4; ++i)
-    dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  store_sums<NS, T>(static_cast<T*>(a.gacc) + gi * NS, v);
 }
 
 // Grid path. The Gaussians come in (class, size, mean-cell) order, the small
@@ -350,10 +494,13 @@ __device__ void bwd_lane_gaussian(const BwdArgs& a, int64_t gi) {
 // later warp runs one large Gaussian over the hit points of every
 // query-level cell its k-sigma bounds overlap. Gaussians whose level box
 // holds no hit point come last and are skipped (zero gradient).
-template <int C, bool PSI>
-__global__ void __launch_bounds__(kBwdThreads, 9)
+// float32 sums: 9 resident blocks per SM (56 registers); the float64 sums
+// of the gradient-check build need more registers and run at fewer.
+template <int C, bool PSI, typename T>
+__global__ void __launch_bounds__(kBwdThreads, sizeof(T) == 4 ? 9 : 2)
 bwd_grid_kernel(BwdArgs a) {
   constexpr int QS = qrec_stride(C);
+  constexpr int NS = Acc<C, T>::NS;
   const int lane = threadIdx.x & 31;
   if (index_unusable(a.header)) return;
   const int64_t n_small = a.header->n_small, n_live = a.header->n_live;
@@ -383,7 +530,7 @@ bwd_grid_kernel(BwdArgs a) {
   for (int64_t w = w0; w < w_end; ++w) {
   if (w < small_warps) {
     const int64_t idx = w * kWarp + lane;
-    if (idx < n_small) bwd_lane_gaussian<C, PSI>(a, a.order[idx]);
+    if (idx < n_small) bwd_lane_gaussian<C, PSI, T>(a, a.order[idx]);
     __syncwarp();
     continue;
   }
@@ -394,9 +541,9 @@ bwd_grid_kernel(BwdArgs a) {
   const int row_step = split ? kSplitWays * kWarp : kWarp;
   const Grid& Gd = a.grid;
   const int64_t gi = a.order[j];
-  GaussianRegs G;
-  float phi[C];
-  load_gaussian<C>(a, gi, G, phi);
+  PairG<C, T> P;
+  load_pair_gaussian<C, T>(a, gi, P);
+  const GaussianRegs& G = P.G;
   uint32_t lo[3], hi[3];
   unpack_qbox(a.qbox[gi], lo, hi);
   const int K = Gd.qlevel;
@@ -410,7 +557,7 @@ bwd_grid_kernel(BwdArgs a) {
   const int rows = ny * nz;
   const bool xborder = lx == 0 || lx + nx - 1 == Gd.dx - 1;
   const float rcx = Gd.ox + (lx + 0.5f * nx) * cellK, rhx = 0.5f * nx * cellK * 1.001f;
-  Acc<C> acc;
+  Acc<C, T> acc;
   acc.zero();
   for (int rb = part * kWarp; rb < rows; rb += row_step) {
     const int ri = rb + lane;
@@ -451,96 +598,114 @@ bwd_grid_kernel(BwdArgs a) {
       const uint32_t ex_s = __shfl_sync(kFullMask, excl, src);
       if (f < tot) {
         const int64_t k = (int64_t)qs_s + (f - ex_s);
-        bwd_pair<C, PSI>(G, phi, a.qrec + k * QS, a, acc);
+        bwd_pair<C, PSI, T>(P, a.qrec + k * QS, a, acc);
       }
     }
   }
-  float v[Acc<C>::NS];
+  T v[NS];
   acc.to_array(v);
   int slot;
-  const float sum = reduce_scatter<Acc<C>::NS>(v, lane, &slot);
-  float* dst = split ? a.bpart + ((j - n_small) * kSplitWays + part) * Acc<C>::NS
-                     : a.gacc + gi * Acc<C>::NS;
-  if (Acc<C>::NS == 32 || (lane & 1) == 0) dst[slot] = sum;
+  const T sum = reduce_scatter<NS, T>(v, lane, &slot);
+  T* dst = split ? static_cast<T*>(a.bpart) + ((j - n_small) * kSplitWays + part) * NS
+                 : static_cast<T*>(a.gacc) + gi * NS;
+  if (NS == 32 || (lane & 1) == 0) dst[slot] = sum;
   }
   }  // work loop
 }
 
 // Brute-force path (no cell lists): one warp per Gaussian over all active hit points.
-template <int C, bool PSI>
+template <int C, bool PSI, typename T>
 __global__ void __launch_bounds__(kBwdThreads)
 bwd_brute_kernel(BwdArgs a) {
   constexpr int QS = qrec_stride(C);
+  constexpr int NS = Acc<C, T>::NS;
   const int lane = threadIdx.x & 31;
   const int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (gi >= a.n || index_unusable(a.header)) return;
   const int64_t n_act = a.header->n_active;
-  GaussianRegs G;
-  float phi[C];
-  load_gaussian<C>(a, gi, G, phi);
-  Acc<C> acc;
+  PairG<C, T> P;
+  load_pair_gaussian<C, T>(a, gi, P);
+  Acc<C, T> acc;
   acc.zero();
-  for (int64_t k = lane; k < n_act; k += kWarp) bwd_pair<C, PSI>(G, phi, a.qrec + k * QS, a, acc);
-  float v[Acc<C>::NS];
+  for (int64_t k = lane; k < n_act; k += kWarp) bwd_pair<C, PSI, T>(P, a.qrec + k * QS, a, acc);
+  T v[NS];
   acc.to_array(v);
   int slot;
-  const float sum = reduce_scatter<Acc<C>::NS>(v, lane, &slot);
-  if (Acc<C>::NS == 32 || (lane & 1) == 0) a.gacc[gi * Acc<C>::NS + slot] = sum;
+  const T sum = reduce_scatter<NS, T>(v, lane, &slot);
+  if (NS == 32 || (lane & 1) == 0) static_cast<T*>(a.gacc)[gi * NS + slot] = sum;
 }
 
 // The split Gaussians' sums: their kSplitWays parts added in part order,
 // into gacc at the Gaussian's id (one thread per split Gaussian).
-template <int C>
+template <int C, typename T>
 __global__ void bwd_split_combine_kernel(BwdArgs a) {
+  constexpr int NS = Acc<C, T>::NS;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (index_unusable(a.header)) return;
   const int64_t n_split = min((int64_t)a.header->n_huge, kSplitMax);
   if (s >= n_split) return;
   const int64_t gi = a.order[(int64_t)a.header->n_small + s];
-  float v[Acc<C>::NS];
-  const float* p = a.bpart + s * kSplitWays * Acc<C>::NS;
+  T v[NS];
+  const T* p = static_cast<const T*>(a.bpart) + s * kSplitWays * NS;
 #pragma unroll
-  for (int i = 0; i < Acc<C>::NS; ++i) v[i] = p[i];
+  for (int i = 0; i < NS; ++i) v[i] = p[i];
   for (int b = 1; b < kSplitWays; ++b)
 #pragma unroll
-    for (int i = 0; i < Acc<C>::NS; ++i) v[i] += p[b * Acc<C>::NS + i];
-  float4* dst = reinterpret_cast<float4*>(a.gacc + gi * Acc<C>::NS);
-#pragma unroll
-  for (int i = 0; i < Acc<C>::NS / 4; ++i)
-    dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    for (int i = 0; i < NS; ++i) v[i] += p[b * NS + i];
+  store_sums<NS, T>(static_cast<T*>(a.gacc) + gi * NS, v);
 }
 
 // Gradients of every Gaussian from its sums, one thread per Gaussian id (so
 // that every read and write is coalesced). Gaussians the pair loop did not
-// visit (no hit point in reach) get zero gradients.
-template <int C>
-__global__ void bwd_epilogue_kernel(BwdArgs a) {
+// visit (no hit point in reach) get zero gradients. With no hit points at
+// all (sums_ready = false) every Gaussian gets zero gradients.
+template <int C, typename T>
+__global__ void bwd_epilogue_kernel(BwdArgs a, bool sums_ready) {
+  constexpr int NS = Acc<C, T>::NS;
   const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= a.n || index_unusable(a.header)) return;
-  Acc<C> acc;
-  if (a.glive[gi]) {
-    const float4* src = reinterpret_cast<const float4*>(a.gacc + gi * Acc<C>::NS);
-    float v[Acc<C>::NS];
+  Acc<C, T> acc;
+  if (sums_ready && a.glive[gi]) {
+    T v[NS];
+    const T* src = static_cast<const T*>(a.gacc) + gi * NS;
+    if constexpr (sizeof(T) == 4) {
+      const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
-    for (int i = 0; i < Acc<C>::NS / 4; ++i) {
-      const float4 t = src[i];
-      v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+      for (int i = 0; i < NS / 4; ++i) {
+        const float4 t = s4[i];
+        v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+      }
+    } else {
+      const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+      for (int i = 0; i < NS / 2; ++i) {
+        const double2 t = s2[i];
+        v[2 * i] = t.x; v[2 * i + 1] = t.y;
+      }
     }
     acc.from_array(v);
   } else {
     acc.zero();
   }
   const Frame fr = gaussian_frame(a.quat, a.logscale, a.n, gi);
-  bwd_epilogue<C>(a, gi, fr, acc);
+  bwd_epilogue<C, T>(a, gi, fr, acc);
 }
 
-template <int C>
-cudaError_t launch_c(const BwdArgs& a, const IndexDims& d, bool psi, const KernelEvents& ev,
-                     cudaStream_t stream) {
+template <int C, typename T>
+cudaError_t launch_ct(const BwdArgs& a, const IndexDims& d, bool psi, const KernelEvents& ev,
+                      cudaStream_t stream) {
+  if (a.n == 0) return cudaSuccess;
+  const unsigned eblocks = (unsigned)((a.n + 255) / 256);
+  if (a.m == 0) {
+    // no hit points: every gradient is zero (written by the epilogue, which
+    // leaves them untouched when the build set a flag)
+    bwd_epilogue_kernel<C, T><<<eblocks, 256, 0, stream>>>(a, false);
+    note_launches(1);
+    return cudaGetLastError();
+  }
   const unsigned pblocks = (unsigned)((a.m + 255) / 256);
   pack_qrec_kernel<C><<<pblocks, 256, 0, stream>>>(a);
   note_launches(1);
-  if (a.n == 0) return cudaGetLastError();
   // brute force: a warp per Gaussian; grid: up to n / 32 lane warps + n warps
   const int64_t warps = d.brute ? a.n : a.n + (a.n + kWarp - 1) / kWarp;
   const unsigned blocks = (unsigned)((warps + kBwdWarps - 1) / kBwdWarps);
@@ -550,25 +715,32 @@ cudaError_t launch_c(const BwdArgs& a, const IndexDims& d, bool psi, const Kerne
     return e;
   if (ev.start && (e = cudaEventRecord(ev.start, stream)) != cudaSuccess) return e;
   if (d.brute) {
-    if (psi) bwd_brute_kernel<C, true><<<blocks, kBwdThreads, 0, stream>>>(a);
-    else bwd_brute_kernel<C, false><<<blocks, kBwdThreads, 0, stream>>>(a);
+    if (psi) bwd_brute_kernel<C, true, T><<<blocks, kBwdThreads, 0, stream>>>(a);
+    else bwd_brute_kernel<C, false, T><<<blocks, kBwdThreads, 0, stream>>>(a);
   } else {
     // persistent: as many blocks as can be resident at once
-    const void* kfn = psi ? reinterpret_cast<const void*>(&bwd_grid_kernel<C, true>)
-                          : reinterpret_cast<const void*>(&bwd_grid_kernel<C, false>);
-    const unsigned pblocks = (unsigned)persistent_blocks(kfn, kBwdThreads, blocks);
-    if (psi) bwd_grid_kernel<C, true><<<pblocks, kBwdThreads, 0, stream>>>(a);
-    else bwd_grid_kernel<C, false><<<pblocks, kBwdThreads, 0, stream>>>(a);
+    const void* kfn = psi ? reinterpret_cast<const void*>(&bwd_grid_kernel<C, true, T>)
+                          : reinterpret_cast<const void*>(&bwd_grid_kernel<C, false, T>);
+    const unsigned gblocks = (unsigned)persistent_blocks(kfn, kBwdThreads, blocks);
+    if (psi) bwd_grid_kernel<C, true, T><<<gblocks, kBwdThreads, 0, stream>>>(a);
+    else bwd_grid_kernel<C, false, T><<<gblocks, kBwdThreads, 0, stream>>>(a);
   }
   if (ev.stop && (e = cudaEventRecord(ev.stop, stream)) != cudaSuccess) return e;
   if (!d.brute) {
     const int64_t max_split = std::min<int64_t>(a.n, kSplitMax);
-    bwd_split_combine_kernel<C><<<(unsigned)((max_split + 127) / 128), 128, 0, stream>>>(a);
+    bwd_split_combine_kernel<C, T><<<(unsigned)((max_split + 127) / 128), 128, 0, stream>>>(a);
     note_launches(1);
   }
-  bwd_epilogue_kernel<C><<<(unsigned)((a.n + 255) / 256), 256, 0, stream>>>(a);
+  bwd_epilogue_kernel<C, T><<<eblocks, 256, 0, stream>>>(a, true);
   note_launches(2);
   return cudaGetLastError();
+}
+
+template <int C>
+cudaError_t launch_c(const BwdArgs& a, const IndexDims& d, bool psi, bool f64,
+                     const KernelEvents& ev, cudaStream_t stream) {
+  return f64 ? launch_ct<C, double>(a, d, psi, ev, stream)
+             : launch_ct<C, float>(a, d, psi, ev, stream);
 }
 
 }  // namespace
@@ -578,16 +750,10 @@ cudaError_t launch_backward(const IndexDims& d, const IndexBuffers& b, const gpf
                             const float* grad_out, const float* out, const float* z,
                             const gpf_field_grad& g, const KernelEvents& ev,
                             cudaStream_t stream) {
+  // every gradient is written by the epilogue kernel (zeros for Gaussians
+  // out of reach), which leaves them untouched when the build set a flag
   const int64_t n = f.n;
-  if (!g.accumulate && n > 0) {
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(g.mean, 0, sizeof(float) * 3 * n, stream)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(g.quat, 0, sizeof(float) * 4 * n, stream)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(g.logscale, 0, sizeof(float) * 3 * n, stream)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(g.spectrum, 0, sizeof(float) * d.channels * n, stream)) != cudaSuccess)
-      return e;
-  }
-  if (q.m == 0 || n == 0) return cudaGetLastError();
+  if (n == 0) return cudaSuccess;
   BwdArgs a;
   a.grid = d.grid;
   a.header = b.header;
@@ -618,17 +784,22 @@ cudaError_t launch_backward(const IndexDims& d, const IndexBuffers& b, const gpf
   a.eps = p.eps;
   a.cut = d.cutoff;
   a.cut2 = isinf(d.cutoff) ? INFINITY : d.cutoff * d.cutoff;
+  a.rd = psi ? (double)p.r_max : 0.0;
+  a.r2d = a.rd * a.rd;
+  a.inv_rrd = psi ? 1.0 / fmax((double)p.r_max, 1e-6) : 0.0;
+  const bool f64 = p.f64_sums != 0;
+  a.f64 = f64 ? 1 : 0;
   a.g = g;
   a.next_work = &b.header->next_work;
   switch (d.channels) {
-    case 1: return launch_c<1>(a, d, psi, ev, stream);
-    case 2: return launch_c<2>(a, d, psi, ev, stream);
-    case 3: return launch_c<3>(a, d, psi, ev, stream);
-    case 4: return launch_c<4>(a, d, psi, ev, stream);
-    case 5: return launch_c<5>(a, d, psi, ev, stream);
-    case 6: return launch_c<6>(a, d, psi, ev, stream);
-    case 7: return launch_c<7>(a, d, psi, ev, stream);
-    case 8: return launch_c<8>(a, d, psi, ev, stream);
+    case 1: return launch_c<1>(a, d, psi, f64, ev, stream);
+    case 2: return launch_c<2>(a, d, psi, f64, ev, stream);
+    case 3: return launch_c<3>(a, d, psi, f64, ev, stream);
+    case 4: return launch_c<4>(a, d, psi, f64, ev, stream);
+    case 5: return launch_c<5>(a, d, psi, f64, ev, stream);
+    case 6: return launch_c<6>(a, d, psi, f64, ev, stream);
+    case 7: return launch_c<7>(a, d, psi, f64, ev, stream);
+    case 8: return launch_c<8>(a, d, psi, f64, ev, stream);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -33,14 +33,22 @@ struct DeviceHeader {
   // work counters of the persistent pair loops (reset before each launch)
   unsigned long long next_tile;       // forward: next tile of 32 hit points
   unsigned long long next_work;       // backward: next work item
-  uint32_t pad[52];
+  uint32_t nonfinite;    // 1 if a Gaussian parameter or an active hit point is not finite
+  uint32_t pad[51];
 };
 static_assert(sizeof(DeviceHeader) == 256, "header is one 256-byte block");
 
-// The index of the last build cannot be used (a full pair buffer or a sort
-// that gave up waiting): the kernels that read it return at once.
+// The index of the last build cannot be used (a full pair buffer, a sort
+// that gave up waiting, or a non-finite input): the kernels that read it
+// return at once and leave their outputs untouched.
 __device__ __forceinline__ bool index_unusable(const DeviceHeader* h) {
-  return (h->overflow | h->stalled) != 0u;
+  return (h->overflow | h->stalled | h->nonfinite) != 0u;
+}
+// The flags word of gpf_index_flags_async (GPF_FLAG_* of gpf.h).
+__device__ __forceinline__ uint32_t index_flags(const DeviceHeader* h) {
+  return (h->overflow ? (uint32_t)GPF_FLAG_CAPACITY : 0u) |
+         (h->stalled ? (uint32_t)GPF_FLAG_TIMEOUT : 0u) |
+         (h->nonfinite ? (uint32_t)GPF_FLAG_NONFINITE : 0u);
 }
 
 // Per-Gaussian record read by the pair loops, float32, stride rec_stride(C):
@@ -75,8 +83,8 @@ constexpr int kOrderSizeBits = 3;
 // The backward splits each Gaussian of the two top size ranks (bounds over
 // at least 2^12 query-level cells), up to kSplitMax of them, into kSplitWays
 // work units over its rows of cells, summing their partial sums in order.
-constexpr int kSplitWays = 16;
-constexpr int64_t kSplitMax = 16384;
+constexpr int kSplitWays = GPF_BWD_SPLIT_WAYS;
+constexpr int64_t kSplitMax = GPF_BWD_SPLIT_MAX;
 
 constexpr int kLevelBits = 4;  // levels < 2^kLevelBits = kMaxLevels
 constexpr uint32_t kLevelMask = (1u << kLevelBits) - 1u;

@@ -152,10 +152,14 @@ __device__ void lane_knn(const HybArgs& a, float px, float py, float pz, float (
   const int rmax = max(max(max(hx, mx - hx), max(hy, my - hy)), max(hz, mz - hz));
   const float cell = G.cell0 * (float)(1u << Lb);
   for (int R = 0; R <= min(rmax, kMaxRing); ++R) {
+    // the cells of the shell max(|dx|, |dy|, |dz|) = R only, O(R^2) of them:
+    // whole squares at dz = +-R; in between, whole rows at dy = +-R and the
+    // two end cells dx = +-R of every other row
     for (int dz = -R; dz <= R; ++dz)
-      for (int dy = -R; dy <= R; ++dy)
-        for (int dx = -R; dx <= R; ++dx) {
-          if (max(abs(dx), max(abs(dy), abs(dz))) != R) continue;   // the ring only
+      for (int dy = -R; dy <= R; ++dy) {
+        const bool full = dz == -R || dz == R || dy == -R || dy == R;
+        const int dx_step = full || R == 0 ? 1 : 2 * R;
+        for (int dx = -R; dx <= R; dx += dx_step) {
           const int cx = hx + dx, cy = hy + dy, cz = hz + dz;
           if (cx < 0 || cy < 0 || cz < 0 || cx > mx || cy > my || cz > mz) continue;
           const CellHash h = cell_hash(G, Lb, cx, cy, cz, kCentreSalt);
@@ -181,6 +185,7 @@ __device__ void lane_knn(const HybArgs& a, float px, float py, float pz, float (
             kg[pos] = g;
           }
         }
+      }
     // every mean in rings beyond R lies at least R cells away
     const float reach = (float)R * cell;
     if (found == k && kd[k - 1] <= reach * reach) break;

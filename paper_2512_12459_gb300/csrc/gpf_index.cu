@@ -159,13 +159,20 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = f.n;
   uint32_t level_bit = 0;
-  bool live = false, small = false, huge = false;
+  bool live = false, small = false, huge = false, bad = false;
   if (g < n) {
     const float* mean = static_cast<const float*>(f.mean);
     const float* spec = static_cast<const float*>(f.spectrum);
+    const float* quat = static_cast<const float*>(f.quat);
+    const float* lsc = static_cast<const float*>(f.logscale);
     const float mu[3] = {mean[g], mean[n + g], mean[2 * n + g]};
-    const Frame fr = gaussian_frame(static_cast<const float*>(f.quat),
-                                    static_cast<const float*>(f.logscale), n, g);
+    // every parameter finite
+    bool fin = isfinite(mu[0]) && isfinite(mu[1]) && isfinite(mu[2]);
+    for (int k = 0; k < 4; ++k) fin = fin && isfinite(quat[k * n + g]);
+    for (int k = 0; k < 3; ++k) fin = fin && isfinite(lsc[k * n + g]);
+    for (int c = 0; c < f.channels; ++c) fin = fin && isfinite(spec[(int64_t)c * n + g]);
+    bad = !fin;
+    const Frame fr = gaussian_frame(quat, lsc, n, g);
     // the record's first 16 floats in registers, stored as four float4 once
     // the level is known (rs is a multiple of 4, the record 16-byte aligned)
     float rv[16];
@@ -277,7 +284,7 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
   __syncthreads();
   const uint32_t m = __reduce_or_sync(kFullMask, level_bit);
   if ((threadIdx.x & 31) == 0 && m) atomicOr(&s_mask, m);
-  uint32_t v[4] = {live ? 1u : 0u, small ? 1u : 0u, huge ? 1u : 0u, 0u};
+  uint32_t v[4] = {live ? 1u : 0u, small ? 1u : 0u, huge ? 1u : 0u, bad ? 1u : 0u};
   block_counts(v, s_cnt);      // its __syncthreads also orders s_mask
   if (threadIdx.x == 0) {
     // the level bits: only when this block adds one (the mask fills up early)
@@ -285,6 +292,7 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
     if (v[0]) atomicAdd(&header->n_live, v[0]);
     if (v[1]) atomicAdd(&header->n_small, v[1]);
     if (v[2]) atomicAdd(&header->n_huge, v[2]);
+    if (v[3]) atomicExch(&header->nonfinite, 1u);
   }
 }
 
@@ -295,7 +303,7 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
                                   uint32_t* __restrict__ occ, int mark,
                                   uint32_t* __restrict__ qcount, DeviceHeader* header) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool active = false;
+  bool active = false, bad = false;
   uint32_t k = grid.key_inactive;
   uint32_t c0[3] = {0u, 0u, 0u};   // level-0 cell of an active hit point
   if (i < m) {
@@ -318,6 +326,7 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
     }
     active = facing && (valid == nullptr || valid[i] != 0);
     if (active) {
+      bad = !(isfinite(x[i]) && isfinite(x[m + i]) && isfinite(x[2 * m + i]));
       const uint32_t cx = coord0(x[i], grid.ox, grid.inv_cell0, grid.max0x);
       const uint32_t cy = coord0(x[m + i], grid.oy, grid.inv_cell0, grid.max0y);
       const uint32_t cz = coord0(x[2 * m + i], grid.oz, grid.inv_cell0, grid.max0z);
@@ -358,9 +367,10 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
   const uint32_t peers = __match_any_sync(kFullMask, active ? k : 0xffffffffu);
   if (active && (peers & lanemask_lt()) == 0) atomicAdd(&qcount[k], (uint32_t)__popc(peers));
   __shared__ uint32_t s_cnt[kBlockWarps][4];
-  uint32_t v[4] = {active ? 1u : 0u, 0u, 0u, 0u};
+  uint32_t v[4] = {active ? 1u : 0u, bad ? 1u : 0u, 0u, 0u};
   block_counts(v, s_cnt);
   if (threadIdx.x == 0 && v[0]) atomicAdd(&header->n_active, v[0]);
+  if (threadIdx.x == 0 && v[1]) atomicExch(&header->nonfinite, 1u);
 }
 
 // One (bucket, Gaussian) entry per occupied cell of every Gaussian's level
@@ -452,6 +462,10 @@ __global__ void bucket_range_kernel(const uint32_t* __restrict__ keys, const Dev
   if (i == n - 1 || keys[i + 1] != k) range[k].y = (uint32_t)(i + 1);
 }
 
+__global__ void index_flags_kernel(const DeviceHeader* header, uint32_t* flags) {
+  *flags = index_flags(header);
+}
+
 inline unsigned blocks_for(int64_t n, int t = kThreads) {
   return (unsigned)((n + t - 1) / t);
 }
@@ -537,6 +551,12 @@ cudaError_t launch_build(const IndexDims& d, const IndexBuffers& b, const gpf_fi
         b.gkey[b.gsorted], b.header, d.p_max, b.brange);
     note_launches(1);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_index_flags(const DeviceHeader* header, uint32_t* flags, cudaStream_t stream) {
+  index_flags_kernel<<<1, 1, 0, stream>>>(header, flags);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -67,8 +67,9 @@ struct IndexBuffers {
   uint32_t* qstart;     // [n_keys + 2] per-cell start of the sorted hit points
   float* qrec;          // [M_max * qrec_stride] packed hit points of the backward
   float* gacc;          // [N_max * gacc_stride] per-Gaussian sums of the backward
+                        // (room for float64 sums: the gradient-check build)
   float* bpart;         // [kSplitMax * kSplitWays * gacc_stride] partial sums of
-                        // the backward's split Gaussians
+                        // the backward's split Gaussians (room for float64)
   uint32_t* occ;        // [n_buckets / 32] occupancy bits of (level, cell) buckets
   uint32_t* gkey[2];    // [P_max] (bucket, Gaussian) entries, sort ping-pong
   uint32_t* gval[2];
@@ -134,8 +135,16 @@ int64_t mse_points_per_partial();
 cudaError_t launch_mse_parts(int64_t m, int channels, const float* out, const float* target,
                              const uint8_t* valid, float* loss, float* grad, float* psum,
                              uint32_t* pcnt, float* scale, cudaStream_t stream);
+// guard: the header of an index whose flags cancel the update (or null).
 cudaError_t launch_adam(const gpf_field& params, const gpf_field_grad& g, const gpf_field_grad& m,
-                        const gpf_field_grad& v, const gpf_adam_hparams& hp, cudaStream_t stream);
+                        const gpf_field_grad& v, const gpf_adam_hparams& hp,
+                        const DeviceHeader* guard, cudaStream_t stream);
+// gpf_index_flags_async: the GPF_FLAG_* word of a header into *flags.
+cudaError_t launch_index_flags(const DeviceHeader* header, uint32_t* flags, cudaStream_t stream);
+
+// ---- throughput probes (gpf_probe.cu): which 0 = FP32 FMA (flop/s), 1 =
+// ex2.approx (results/s); synchronous, on a stream of its own.
+cudaError_t measure_alu_peak(int which, int iters, double* per_second, double* seconds);
 
 // ---- loss without caller scratch (gpf_noalloc.cu)
 int64_t noalloc_max_points();

@@ -19,8 +19,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <mutex>
-
 #include "gpf_internal.h"
 
 namespace gpf {
@@ -38,26 +36,19 @@ struct NoAllocScratch {
 };
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
-// Device address of the scratch array, looked up once per device. In host
-// code the name g_noalloc_scratch only stands for the array; the address the
-// kernels need comes from cudaGetSymbolAddress with the device current.
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-NoAllocScratch* g_noalloc_ptr[kMaxDevices] = {};
-
+// Device address of the scratch array on the current device. In host code the
+// name g_noalloc_scratch only stands for the array; the address the kernels
+// need comes from cudaGetSymbolAddress with the device current. It is looked
+// up on every call and never cached: after cudaDeviceReset (or any other end
+// of the device's context) the library's device code is loaded again and the
+// array can sit at another address, so a cached pointer would go stale. Once
+// the code is loaded the lookup is a host-side table search; the first call
+// on a device (or in a new context) also loads the code there.
 cudaError_t noalloc_scratch(NoAllocScratch** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_noalloc_ptr[dev] = static_cast<NoAllocScratch*>(p);
-  }
-  *out = g_noalloc_ptr[dev];
+  *out = static_cast<NoAllocScratch*>(p);
   return cudaSuccess;
 }
 

@@ -128,6 +128,7 @@ struct AdamArgs {
   float b1, b2, eps;
   int64_t t_host;            // update index when counter is null
   const int64_t* counter;    // device count of updates applied, or null
+  const DeviceHeader* guard; // an index whose flags cancel the update, or null
 };
 
 // torch.optim.Adam's update order: m += (1-b1)(g-m); v = b2 v + (1-b2) g^2;
@@ -144,6 +145,8 @@ template <bool VEC>
 __global__ void adam_kernel(AdamArgs a) {
   __shared__ float s_step[4];
   __shared__ float s_inv_bc2_sqrt;
+  // gradients from an unusable build were never written: no update
+  if (a.guard && index_unusable(a.guard)) return;
   if (threadIdx.x == 0) {
     const int64_t t = a.counter ? *a.counter + 1 : a.t_host;
     const double bc1 = 1.0 - pow((double)a.b1, (double)t);
@@ -179,7 +182,10 @@ __global__ void adam_kernel(AdamArgs a) {
   }
 }
 
-__global__ void adam_count_kernel(int64_t* counter) { *counter += 1; }
+__global__ void adam_count_kernel(int64_t* counter, const DeviceHeader* guard) {
+  if (guard && index_unusable(guard)) return;
+  *counter += 1;
+}
 
 }  // namespace
 
@@ -223,7 +229,8 @@ cudaError_t launch_mse_parts(int64_t m, int channels, const float* out, const fl
 }
 
 cudaError_t launch_adam(const gpf_field& params, const gpf_field_grad& g, const gpf_field_grad& m,
-                        const gpf_field_grad& v, const gpf_adam_hparams& hp, cudaStream_t stream) {
+                        const gpf_field_grad& v, const gpf_adam_hparams& hp,
+                        const DeviceHeader* guard, cudaStream_t stream) {
   const int64_t n = params.n;
   if (n == 0) return cudaSuccess;
   AdamArgs a;
@@ -255,12 +262,13 @@ cudaError_t launch_adam(const gpf_field& params, const gpf_field_grad& g, const 
   a.eps = hp.eps;
   a.t_host = hp.step;
   a.counter = hp.step_counter;
+  a.guard = guard;
   const int64_t blocks = std::min<int64_t>((acc + 255) / 256, 152 * 8);
   if (vec) adam_kernel<true><<<(unsigned)blocks, 256, 0, stream>>>(a);
   else adam_kernel<false><<<(unsigned)blocks, 256, 0, stream>>>(a);
   note_launches(1);
   if (hp.step_counter) {
-    adam_count_kernel<<<1, 1, 0, stream>>>(hp.step_counter);
+    adam_count_kernel<<<1, 1, 0, stream>>>(hp.step_counter, guard);
     note_launches(1);
   }
   return cudaGetLastError();

@@ -49,6 +49,13 @@ class TrainStep:
         self.z = torch.empty((m,), dtype=torch.float32, device=dev)
         self.gout = torch.empty((c, m), dtype=torch.float32, device=dev)
         self.loss = torch.zeros((1,), dtype=torch.float32, device=dev)
+        self.mse_ws = api.gpf_mse_workspace(m, dev)
+        # device flags of each step's build (GPF_FLAG_*: 0 = usable), copied
+        # to pinned host memory at the end of the step, so that a caller can
+        # check a replayed step without synchronising the stream
+        self.flags = torch.zeros((1,), dtype=torch.int32, device=dev)
+        self.flags_host = torch.zeros((1,), dtype=torch.int32).pin_memory()
+        self.done = torch.cuda.Event()
         self.grad_hook = grad_hook        # e.g. a data-parallel gradient all-reduce
         self.graph: Optional[torch.cuda.CUDAGraph] = None
 
@@ -57,16 +64,22 @@ class TrainStep:
         q = self.queries
         f = self.store if self.store is not None else self.field
         self.index.build(f, q)
+        self.index.flags_async(self.flags)
         api.gpf_radiance_fwd(self.index, f, q, self.mode, r_max=self.r_max, eps=self.eps,
                              out=self.out, z=self.z)
-        api.gpf_mse_loss_grad(self.out, self.target, q.valid, loss=self.loss, grad=self.gout)
+        api.gpf_mse_loss_grad(self.out, self.target, q.valid, loss=self.loss, grad=self.gout,
+                              workspace=self.mse_ws)
         api.gpf_radiance_bwd(self.index, f, q, self.gout, self.out, self.z, self.mode,
                              r_max=self.r_max, eps=self.eps, grads=self.grads)
         if self.grad_hook is not None:
             self.grad_hook(self.grads)
-        api.gpf_adam_step(self.field, self.grads, self.state, lr=self.lr)
+        # an unusable build (a full pair buffer, a sort that gave up, a
+        # non-finite parameter) leaves the gradients unwritten: the guard
+        # cancels the update on the device
+        api.gpf_adam_step(self.field, self.grads, self.state, lr=self.lr, guard=self.index)
         if self.store is not None:
             self.field.quantize_into(self.store)
+        self.flags_host.copy_(self.flags, non_blocking=True)
 
     def capture(self, warmup: int = 1) -> None:
         """Run `warmup` real steps on a side stream (first-use set-up outside
@@ -89,6 +102,15 @@ class TrainStep:
             self.graph.replay()
         else:
             self.run_eager()
+        self.done.record()
+
+    def last_flags(self) -> Optional[int]:
+        """GPF_FLAG_* bits of the last step's build (0: it was usable and
+        the step was applied; else the step left the parameters as they
+        were), or None while that step is still running. Never blocks."""
+        if not self.done.query():
+            return None
+        return int(self.flags_host[0])
 
     def updates(self) -> int:
         """Adam updates applied so far (synchronises)."""

@@ -41,7 +41,8 @@ def test_every_declared_symbol_is_exported(lib, root_dir):
 def test_version_and_status_strings(lib):
     assert b"sm_103a" in lib.gpf_version()
     for s, name in [(0, b"GPF_OK"), (1, b"GPF_ERR_INVALID_ARG"), (4, b"GPF_ERR_CAPACITY"),
-                    (6, b"GPF_ERR_MISMATCH"), (7, b"GPF_ERR_TIMEOUT")]:
+                    (6, b"GPF_ERR_MISMATCH"), (7, b"GPF_ERR_TIMEOUT"),
+                    (8, b"GPF_ERR_NONFINITE")]:
         assert lib.gpf_status_string(s) == name
     assert lib.gpf_status_string(99) == b"GPF_ERR_UNKNOWN"
 
@@ -128,8 +129,23 @@ def test_host_validation_before_any_launch(lib):
                 _abi.gpf_query_params(0, 0.02, 0.0, 0), _abi.gpf_query_params(0, math.nan, 1e-6, 0)):
         assert lib.gpf_radiance_fwd(h, ctypes.byref(f), ctypes.byref(q), ctypes.byref(bad), fake,
                                     None, None) == 1
+    # f64_sums: 0 or 1, and in the backward only
+    p.f64_sums = 1
+    assert lib.gpf_radiance_fwd(h, ctypes.byref(f), ctypes.byref(q), ctypes.byref(p), fake,
+                                None, None) == 1
+    assert b"f64_sums" in lib.gpf_last_error()
+    p.f64_sums = 2
+    g = _abi.gpf_field_grad(fake, fake, fake, fake, 0, 0)
+    assert lib.gpf_radiance_bwd(h, ctypes.byref(f), ctypes.byref(q), ctypes.byref(p), fake, None,
+                                None, ctypes.byref(g), None) == 1
+    assert b"f64_sums" in lib.gpf_last_error()
     stats = _abi.gpf_index_stats_t()
     assert lib.gpf_index_stats(h, ctypes.byref(stats), None) == 5
+    # the flags word: a device pointer on a built index
+    assert lib.gpf_index_flags_async(None, fake, None) == 1
+    assert lib.gpf_index_flags_async(h, None, None) == 1
+    assert lib.gpf_index_flags_async(h, fake + 2, None) == 1
+    assert lib.gpf_index_flags_async(h, fake, None) == 5
     # timing events: any handles (or none) on a live index, never on NULL
     assert lib.gpf_index_set_timing_events(None, None, None, None, None) == 1
     assert lib.gpf_index_set_timing_events(h, None, None, None, None) == 0
@@ -160,6 +176,15 @@ def test_loss_and_adam_validation(lib):
     assert lib.gpf_adam_step(ctypes.byref(f), ctypes.byref(g), ctypes.byref(g), ctypes.byref(g),
                              ctypes.byref(hp), None) == 1
     assert b"step_counter" in lib.gpf_last_error()
+    # a guard index must have been built
+    h = ctypes.c_void_p()
+    cfg = _cfg()
+    assert lib.gpf_index_create(ctypes.byref(cfg), ctypes.byref(h)) == 0
+    hp.step, hp.step_counter, hp.guard = 1, None, h
+    assert lib.gpf_adam_step(ctypes.byref(f), ctypes.byref(g), ctypes.byref(g), ctypes.byref(g),
+                             ctypes.byref(hp), None) == 5
+    assert b"guard" in lib.gpf_last_error()
+    lib.gpf_index_destroy(h)
 
 
 def test_sort_validation(lib):

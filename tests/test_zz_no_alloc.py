@@ -49,15 +49,17 @@ def test_noalloc_loss_matches_the_workspace_entry_point(env):
         ref_loss, ref_grad = gpf.gpf_mse_loss_grad(out, tgt, valid)
         loss, grad = _noalloc(torch, lib, out, tgt, valid)
         torch.cuda.synchronize()
-        np.testing.assert_allclose(loss.cpu().numpy(), ref_loss.cpu().numpy(), rtol=1e-6)
-        np.testing.assert_allclose(grad.cpu().numpy(), ref_grad.cpu().numpy(), rtol=1e-6, atol=0)
+        # the same kernels in the same order: equal bit for bit, so a stale
+        # partial sum left by the previous (larger) call would show
+        np.testing.assert_array_equal(loss.cpu().numpy(), ref_loss.cpu().numpy())
+        np.testing.assert_array_equal(grad.cpu().numpy(), ref_grad.cpu().numpy())
     # no valid mask, and an empty problem
     out, tgt, _ = _case(torch, 5000, 2, 3)
     ref_loss, ref_grad = gpf.gpf_mse_loss_grad(out, tgt, None)
     loss, grad = _noalloc(torch, lib, out, tgt, None)
     torch.cuda.synchronize()
-    np.testing.assert_allclose(loss.cpu().numpy(), ref_loss.cpu().numpy(), rtol=1e-6)
-    np.testing.assert_allclose(grad.cpu().numpy(), ref_grad.cpu().numpy(), rtol=1e-6, atol=0)
+    np.testing.assert_array_equal(loss.cpu().numpy(), ref_loss.cpu().numpy())
+    np.testing.assert_array_equal(grad.cpu().numpy(), ref_grad.cpu().numpy())
     e = torch.empty((3, 0), device="cuda")
     loss, _ = _noalloc(torch, lib, e, e, None)
     assert loss.item() == 0.0
