@@ -156,7 +156,8 @@ typedef struct gpf_queries {
                               fewer than k_min of them, the k_min nearest
                               means (ties: the smaller index). No truncation
                               of the weights. ball_r = 0: kNN only; k_min = 0:
-                              ball only. Forward only (no gradient).         */
+                              ball only. The backward needs an index with
+                              max_nb_pairs > 0.                              */
 #define GPF_MAX_KMIN 16
 
 typedef struct gpf_query_params {
@@ -215,6 +216,11 @@ typedef struct gpf_grid_config {
   int64_t max_gaussians; /* capacity N_max (< 2^30)                          */
   int64_t max_queries;   /* capacity M_max (< 2^30)                          */
   int64_t max_pairs;     /* capacity of (cell, Gaussian) entries (< 2^30)    */
+  int64_t max_nb_pairs;  /* capacity of (hit point, Gaussian) pairs of the
+                            GPF_NB_BALL_KNN backward (< 2^30; 0: that
+                            backward is refused). A backward whose
+                            neighbourhoods hold more pairs sets the capacity
+                            flag and leaves its gradients untouched.         */
 } gpf_grid_config;
 
 /* Opaque host-side handle. It holds sizes and pointers into the workspace;
@@ -431,6 +437,13 @@ uint64_t gpf_launch_count(void);
  *             index's last build set a device flag.
  *   params    as gpf_radiance_fwd; f64_sums = 1 selects the float64
  *             gradient-check build of the sums.
+ * With GPF_NB_BALL_KNN the selection N(x) is held fixed (it is piecewise
+ * constant in the parameters): the library runs the forward's selection
+ * again, writes every selected (hit point, Gaussian) pair at a per-point
+ * offset, sorts the pairs by Gaussian (stable, so each Gaussian's hit points
+ * stay in index order) and sums each Gaussian's pairs in one warp, without
+ * atomics; the index needs max_nb_pairs at least the number of selected
+ * pairs, and more sets the capacity flag.
  * Errors: as gpf_radiance_fwd.
  */
 gpf_status gpf_radiance_bwd(const gpf_index *index, const gpf_field *field,

@@ -17,7 +17,8 @@ What it computes (paper arxiv 2512.12459):
   * the MSE loss of Sec. 4.3 and its gradient;
   * the Adam update of Sec. A.2 (lr 5e-4);
   * the paper's hybrid neighbourhood, ball(r) or the k_min nearest means
-    (Sec. 4.2, Neighborhood Search; Algorithm S3);
+    (Sec. 4.2, Neighborhood Search; Algorithm S3), and its gradient with the
+    selection held fixed;
   * the per-view photon density estimate the field replaces (Sec. 3.2,
     Eq. kde; the gather of Algorithm S1), a disk kernel over photons.
 
@@ -37,6 +38,7 @@ from .gpf_oracle import (  # noqa: F401
     radiance_bwd,
     disk_kde,
     hybrid_fwd,
+    hybrid_bwd,
     mse_loss,
     mse_loss_grad,
     adam_step,

@@ -319,6 +319,73 @@ def hybrid_fwd(mean, quat, logscale, spectrum, x, n, wo, albedo=None, valid=None
             "knn": knn & mask, "near": near & mask, "logw_max": logw}
 
 
+def hybrid_bwd(mean, quat, logscale, spectrum, x, n, wo, grad_out, albedo=None, valid=None,
+               mode: int = GPF_NORMALIZED, r_max: float = 0.02, eps: float = 1e-6,
+               ball_r: float = 0.02, k_min: int = 3) -> Dict[str, np.ndarray]:
+    """Gradient of sum_{c,m} grad_out[c,m] * O[c,m] for the hybrid
+    neighbourhood of hybrid_fwd (Sec. 4.2, Neighborhood Search and
+    Differentiable Accumulation): the selection N(x) (the ball of radius
+    ball_r around x, or the k_min nearest means when the ball holds fewer) is
+    piecewise constant in the parameters and contributes no derivative; over
+    the selected pairs the chain rule is the one of radiance_bwd with the
+    untruncated weights w_i = exp(-Q_i/2) psi(|d_i|). Returns mean, quat, logscale,
+    spectrum (as radiance_bwd) and fwd (hybrid_fwd's result)."""
+    P = _Prepared(mean, quat, logscale, spectrum)
+    X = np.asarray(x, dtype=_F64).T
+    M, C, N = X.shape[0], P.c, P.n
+    G = np.asarray(grad_out, dtype=_F64).T
+    fwd = hybrid_fwd(mean, quat, logscale, spectrum, x, n, wo, albedo, valid, mode, r_max, eps,
+                     ball_r, k_min)
+    mask = _query_mask(n, wo, valid, M)
+    rho = np.ones((M, C)) if albedo is None else np.asarray(albedo, dtype=_F64).T
+    gamma = G * rho * mask[:, None]
+    L, Z = fwd["L"].T, fwd["Z"]
+    if mode == GPF_SUM:
+        dL, dZ = gamma, np.zeros(M)
+    else:
+        big = Z > eps
+        Zc = np.where(big, Z, eps)
+        dL = gamma / Zc[:, None]
+        dZ = np.where(big, -np.sum(gamma * L, axis=1) / (Zc * Zc), 0.0)
+    g_mu = np.zeros((N, 3))
+    g_R = np.zeros((N, 3, 3))
+    g_l = np.zeros((N, 3))
+    g_phi = np.zeros((N, C))
+    r2 = float(ball_r) ** 2
+    idx = np.arange(N)
+    step = _chunk(N)
+    for a in range(0, M, step):
+        b = min(M, a + step)
+        d, u, Q, dist, _, w_all = _pairs(P, X[a:b], r_max, math.inf)
+        d2 = d[..., 0] ** 2 + d[..., 1] ** 2 + d[..., 2] ** 2
+        # the selection of hybrid_fwd, point by point
+        sel = np.zeros((b - a, N), dtype=bool)
+        for j in range(b - a):
+            ball = d2[j] <= r2
+            if ball.sum() >= k_min:
+                sel[j] = ball
+            else:
+                order = np.lexsort((idx, d2[j]))
+                sel[j, order[:min(k_min, N)]] = True
+        w = np.where(sel, w_all, 0.0)
+        beta = dL[a:b] @ P.phi.T + dZ[a:b, None]
+        bw = beta * w
+        g_phi += w.T @ dL[a:b]
+        g_l += np.einsum("mn,mnj->nj", bw, u * u)
+        g_R -= np.einsum("mn,mnk,mnj->nkj", bw, d, u) / P.s[:, None, :]
+        g_mu += np.einsum("mn,mnj,nkj->nk", bw, u, P.R / P.s[:, None, :])
+        dpsi = _falloff_dpsi_ddist(dist, r_max)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            coef = np.where(sel & (dist > 0.0),
+                            -beta * np.exp(-0.5 * Q) * dpsi / np.where(dist > 0, dist, 1.0),
+                            0.0)
+        g_mu += np.einsum("mn,mnk->nk", coef, d)
+    g_qhat = np.einsum("nkj,nakj->na", g_R, _rotmat_partials(P.qhat))
+    g_q = (g_qhat - P.qhat * np.sum(P.qhat * g_qhat, axis=1, keepdims=True)) / P.qnorm[:, None]
+    return {"mean": g_mu.T.copy(), "quat": g_q.T.copy(), "logscale": g_l.T.copy(),
+            "spectrum": g_phi.T.copy(), "fwd": fwd}
+
+
 def disk_kde(position, flux, x, n, wo, radius: float, albedo=None, valid=None,
              band: float = 1e-5) -> Dict[str, np.ndarray]:
     """The per-view photon density estimate that the field replaces (Sec. 3.2,

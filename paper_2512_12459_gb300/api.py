@@ -210,6 +210,7 @@ class GridConfig:
     coop_cells: int = 0        # forward tile shape (0 = library default, 4)
     field_storage: int = 0     # GPF_F32 or GPF_BF16 fields
     ball_radius: float = 0.0   # > 0: centre entries for GPF_NB_BALL_KNN queries
+    max_nb_pairs: int = 0      # capacity of the GPF_NB_BALL_KNN backward's pairs
 
     def c_struct(self) -> _abi.gpf_grid_config:
         return _abi.gpf_grid_config((ctypes.c_float * 3)(*self.origin), float(self.cell_size),
@@ -220,7 +221,7 @@ class GridConfig:
                                     int(self.coop_cells), int(self.field_storage),
                                     float(self.ball_radius), int(self.max_gaussians),
                                     int(self.max_queries),
-                                    int(self.max_pairs))
+                                    int(self.max_pairs), int(self.max_nb_pairs))
 
 
 def grid_for_bounds(lo: Sequence[float], hi: Sequence[float], cell_size: float, channels: int,
@@ -385,11 +386,13 @@ def gpf_radiance_bwd(index: Index, field: Field, queries: Queries, grad_out: tor
                      out: Optional[torch.Tensor] = None, z: Optional[torch.Tensor] = None,
                      mode: int = GPF_SUM, r_max: float = math.inf, eps: float = PAPER_EPS,
                      grads: Optional[Field] = None, accumulate: bool = False,
-                     stream=None, neighbourhood: int = 0, f64_sums: bool = False) -> Field:
+                     stream=None, neighbourhood: int = 0, f64_sums: bool = False,
+                     ball_r: float = PAPER_R, k_min: int = 3) -> Field:
     """Gradients (a Field of tensors) of sum(grad_out * O) w.r.t. mean, quat,
-    logscale and spectrum (the k-sigma neighbourhood; the library refuses
-    others). f64_sums=True runs the float64 gradient-check build of the
-    per-Gaussian sums (gpf_query_params.f64_sums)."""
+    logscale and spectrum, for the neighbourhood of the forward
+    (GPF_NB_KSIGMA, or GPF_NB_BALL_KNN with ball_r and k_min on an index with
+    max_nb_pairs > 0). f64_sums=True runs the float64 gradient-check build of
+    the per-Gaussian sums (gpf_query_params.f64_sums)."""
     m, c = queries.m, field.channels
     _need(grad_out, "grad_out", c, m)
     if grads is None:       # float32 gradients for either storage
@@ -405,7 +408,7 @@ def gpf_radiance_bwd(index: Index, field: Field, queries: Queries, grad_out: tor
         _need(out, "out", c, m)
         _need(z, "z", 0, m)
     fs, qs = field.c_struct(), queries.c_struct(c)
-    ps = _params(mode, r_max, eps, neighbourhood, f64_sums=f64_sums)
+    ps = _params(mode, r_max, eps, neighbourhood, ball_r, k_min, f64_sums=f64_sums)
     gs = _abi.gpf_field_grad(_ptr(grads.mean), _ptr(grads.quat), _ptr(grads.logscale),
                              _ptr(grads.spectrum), 1 if accumulate else 0, 0)
     check(index._lib.gpf_radiance_bwd(index.handle, ctypes.byref(fs), ctypes.byref(qs),

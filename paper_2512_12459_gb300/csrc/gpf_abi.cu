@@ -117,7 +117,18 @@ size_t layout(const gpf_index* ix, char* base, IndexBuffers* b) {
   t.occ = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * ((nb + 31) / 32)));
   t.brange = reinterpret_cast<uint2*>(take(sizeof(uint2) * nb));
   t.dec = d.bf16 ? reinterpret_cast<float*>(take(sizeof(float) * (10 + d.channels) * N)) : nullptr;
-  t.scan_ws = take(scan_workspace_bytes(std::max<int64_t>(std::max<int64_t>(N, 1), ncp)));
+  if (d.nb_max > 0) {
+    for (int k = 0; k < 2; ++k) {
+      t.nbkey[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * d.nb_max));
+      t.nbval[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * d.nb_max));
+    }
+    t.nbcnt = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (M + 1)));
+    t.nbrange = reinterpret_cast<uint2*>(take(sizeof(uint2) * std::max<int64_t>(N, 1)));
+    t.nbsort_ws = take(radix_sort_workspace_bytes(d.nb_max));
+    t.nbsorted = radix_sort_passes(d.grid.id_bits) % 2;
+  }
+  t.scan_ws = take(scan_workspace_bytes(
+      std::max<int64_t>(std::max<int64_t>(std::max<int64_t>(N, 1), ncp), M + 1)));
   t.qsort_ws = take(radix_sort_workspace_bytes(M > 0 ? M : 1));
   t.gsort_ws = take(radix_sort_workspace_bytes(P > 0 ? P : 1));
   t.osort_ws = take(radix_sort_workspace_bytes(N > 0 ? N : 1));
@@ -279,11 +290,14 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
   if (cfg->coop_cells < 0 || cfg->coop_cells > GPF_MAX_COOP_CELLS)
     return fail(GPF_ERR_INVALID_ARG, "coop_cells = %d outside 0..%d", cfg->coop_cells,
                 GPF_MAX_COOP_CELLS);
-  if (cfg->max_gaussians < 0 || cfg->max_queries < 0 || cfg->max_pairs < 0)
+  if (cfg->max_gaussians < 0 || cfg->max_queries < 0 || cfg->max_pairs < 0 ||
+      cfg->max_nb_pairs < 0)
     return fail(GPF_ERR_INVALID_ARG, "capacities must be >= 0");
   if (cfg->max_gaussians >= kMaxSortN || cfg->max_queries >= kMaxSortN ||
-      cfg->max_pairs >= kMaxSortN)
+      cfg->max_pairs >= kMaxSortN || cfg->max_nb_pairs >= kMaxSortN)
     return fail(GPF_ERR_INVALID_ARG, "capacities must be below 2^30");
+  if (cfg->max_nb_pairs > 0 && !(cfg->ball_radius > 0.0f))
+    return fail(GPF_ERR_INVALID_ARG, "max_nb_pairs > 0 needs ball_radius > 0 (centre entries)");
   const uint64_t cells = (uint64_t)cfg->dims[0] * cfg->dims[1] * cfg->dims[2];
   if (cells > (1ull << 28))
     return fail(GPF_ERR_INVALID_ARG, "grid has %llu cells, more than 2^28",
@@ -344,6 +358,7 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
   d.n_max = cfg->max_gaussians;
   d.m_max = cfg->max_queries;
   d.p_max = d.brute ? 0 : cfg->max_pairs;
+  d.nb_max = cfg->max_nb_pairs;
   ix->ws_bytes = layout(ix, nullptr, nullptr);
   ix->built = false;
   *out = ix;
@@ -493,8 +508,16 @@ gpf_status gpf_radiance_bwd(const gpf_index* index, const gpf_field* field,
   if ((s = check_same(index, field, queries)) != GPF_OK) return s;
   if (params->mode == GPF_DISK_KDE)
     return fail(GPF_ERR_INVALID_ARG, "GPF_DISK_KDE (the photon density estimate) has no gradient");
-  if (params->neighbourhood != GPF_NB_KSIGMA)
-    return fail(GPF_ERR_INVALID_ARG, "the backward supports the GPF_NB_KSIGMA neighbourhood only");
+  if (params->neighbourhood == GPF_NB_BALL_KNN) {
+    if (index->dims.grid.blevel < 0)
+      return fail(GPF_ERR_INVALID_ARG, "the index has no centre entries (ball_radius = 0)");
+    if (params->ball_r > index->cfg.ball_radius)
+      return fail(GPF_ERR_INVALID_ARG, "params.ball_r = %g exceeds the index's ball_radius %g",
+                  params->ball_r, index->cfg.ball_radius);
+    if (index->dims.nb_max <= 0)
+      return fail(GPF_ERR_INVALID_ARG,
+                  "the GPF_NB_BALL_KNN backward needs an index with max_nb_pairs > 0");
+  }
   if (!grads) return fail(GPF_ERR_INVALID_ARG, "grads is NULL");
   if (grads->reserved != 0) return fail(GPF_ERR_INVALID_ARG, "grads.reserved must be 0");
   if (field->n > 0) {

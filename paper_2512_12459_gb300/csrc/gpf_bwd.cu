@@ -57,6 +57,8 @@ struct BwdArgs {
   const float* rec;
   const uint4* box;
   const uint32_t* order;  // Gaussian ids in mean-cell order
+  const uint2* nbrange;   // hybrid neighbourhood: [start, end) of each Gaussian's pairs
+  const uint32_t* nbval;  // hybrid neighbourhood: the pairs' hit point positions
   int64_t n;
   const float* quat;
   const float* logscale;
@@ -635,6 +637,40 @@ bwd_brute_kernel(BwdArgs a) {
   if (NS == 32 || (lane & 1) == 0) static_cast<T*>(a.gacc)[gi * NS + slot] = sum;
 }
 
+// The paper's hybrid neighbourhood (GPF_NB_BALL_KNN): one warp per Gaussian
+// over its selected hit points (the sorted pairs of launch_hybrid_pairs),
+// lanes striding the run; the weights are untruncated (cut2 = +INF) and the
+// selection is what makes a pair count. Persistent over Gaussian ids.
+template <int C, bool PSI, typename T>
+__global__ void __launch_bounds__(kBwdThreads)
+bwd_hybrid_kernel(BwdArgs a) {
+  constexpr int QS = qrec_stride(C);
+  constexpr int NS = Acc<C, T>::NS;
+  const int lane = threadIdx.x & 31;
+  if (index_unusable(a.header)) return;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gi < a.n;
+       gi += warps) {
+    const uint2 rg = a.nbrange[gi];
+    T* dst = static_cast<T*>(a.gacc) + gi * NS;
+    if (rg.y <= rg.x) {
+      if (lane < NS) dst[lane] = T(0);
+      continue;
+    }
+    PairG<C, T> P;
+    load_pair_gaussian<C, T>(a, gi, P);
+    Acc<C, T> acc;
+    acc.zero();
+    for (uint32_t i = rg.x + lane; i < rg.y; i += kWarp)
+      bwd_pair<C, PSI, T>(P, a.qrec + (int64_t)a.nbval[i] * QS, a, acc);
+    T v[NS];
+    acc.to_array(v);
+    int slot;
+    const T sum = reduce_scatter<NS, T>(v, lane, &slot);
+    if (NS == 32 || (lane & 1) == 0) dst[slot] = sum;
+  }
+}
+
 // The split Gaussians' sums: their kSplitWays parts added in part order,
 // into gacc at the Gaussian's id (one thread per split Gaussian).
 template <int C, typename T>
@@ -660,12 +696,12 @@ __global__ void bwd_split_combine_kernel(BwdArgs a) {
 // visit (no hit point in reach) get zero gradients. With no hit points at
 // all (sums_ready = false) every Gaussian gets zero gradients.
 template <int C, typename T>
-__global__ void bwd_epilogue_kernel(BwdArgs a, bool sums_ready) {
+__global__ void bwd_epilogue_kernel(BwdArgs a, bool sums_ready, bool all_live) {
   constexpr int NS = Acc<C, T>::NS;
   const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= a.n || index_unusable(a.header)) return;
   Acc<C, T> acc;
-  if (sums_ready && a.glive[gi]) {
+  if (sums_ready && (all_live || a.glive[gi])) {
     T v[NS];
     const T* src = static_cast<const T*>(a.gacc) + gi * NS;
     if constexpr (sizeof(T) == 4) {
@@ -699,17 +735,31 @@ cudaError_t launch_ct(const BwdArgs& a, const IndexDims& d, bool psi, const Kern
   if (a.m == 0) {
     // no hit points: every gradient is zero (written by the epilogue, which
     // leaves them untouched when the build set a flag)
-    bwd_epilogue_kernel<C, T><<<eblocks, 256, 0, stream>>>(a, false);
+    bwd_epilogue_kernel<C, T><<<eblocks, 256, 0, stream>>>(a, false, false);
     note_launches(1);
     return cudaGetLastError();
   }
   const unsigned pblocks = (unsigned)((a.m + 255) / 256);
   pack_qrec_kernel<C><<<pblocks, 256, 0, stream>>>(a);
   note_launches(1);
+  cudaError_t e;
+  if (a.nbrange) {
+    // the hybrid neighbourhood: a warp per Gaussian over its selected pairs
+    const int64_t want = (a.n * kWarp + kBwdThreads - 1) / kBwdThreads;
+    const void* kfn = psi ? reinterpret_cast<const void*>(&bwd_hybrid_kernel<C, true, T>)
+                          : reinterpret_cast<const void*>(&bwd_hybrid_kernel<C, false, T>);
+    const unsigned hblocks = (unsigned)persistent_blocks(kfn, kBwdThreads, want);
+    if (ev.start && (e = cudaEventRecord(ev.start, stream)) != cudaSuccess) return e;
+    if (psi) bwd_hybrid_kernel<C, true, T><<<hblocks, kBwdThreads, 0, stream>>>(a);
+    else bwd_hybrid_kernel<C, false, T><<<hblocks, kBwdThreads, 0, stream>>>(a);
+    if (ev.stop && (e = cudaEventRecord(ev.stop, stream)) != cudaSuccess) return e;
+    bwd_epilogue_kernel<C, T><<<eblocks, 256, 0, stream>>>(a, true, true);
+    note_launches(2);
+    return cudaGetLastError();
+  }
   // brute force: a warp per Gaussian; grid: up to n / 32 lane warps + n warps
   const int64_t warps = d.brute ? a.n : a.n + (a.n + kWarp - 1) / kWarp;
   const unsigned blocks = (unsigned)((warps + kBwdWarps - 1) / kBwdWarps);
-  cudaError_t e;
   if (!d.brute &&
       (e = cudaMemsetAsync(a.next_work, 0, sizeof(unsigned long long), stream)) != cudaSuccess)
     return e;
@@ -731,7 +781,7 @@ cudaError_t launch_ct(const BwdArgs& a, const IndexDims& d, bool psi, const Kern
     bwd_split_combine_kernel<C, T><<<(unsigned)((max_split + 127) / 128), 128, 0, stream>>>(a);
     note_launches(1);
   }
-  bwd_epilogue_kernel<C, T><<<eblocks, 256, 0, stream>>>(a, true);
+  bwd_epilogue_kernel<C, T><<<eblocks, 256, 0, stream>>>(a, true, false);
   note_launches(2);
   return cudaGetLastError();
 }
@@ -773,6 +823,8 @@ cudaError_t launch_backward(const IndexDims& d, const IndexBuffers& b, const gpf
   a.rec = b.rec;
   a.box = b.box;
   a.order = b.oval[b.osorted];
+  a.nbrange = nullptr;
+  a.nbval = nullptr;
   a.n = n;
   a.quat = static_cast<const float*>(f.quat);
   a.logscale = static_cast<const float*>(f.logscale);
@@ -784,6 +836,14 @@ cudaError_t launch_backward(const IndexDims& d, const IndexBuffers& b, const gpf
   a.eps = p.eps;
   a.cut = d.cutoff;
   a.cut2 = isinf(d.cutoff) ? INFINITY : d.cutoff * d.cutoff;
+  if (p.neighbourhood == GPF_NB_BALL_KNN) {
+    // the selected pairs, sorted by Gaussian; no truncation of the weights
+    const cudaError_t e = launch_hybrid_pairs(d, b, q, p, n, stream);
+    if (e != cudaSuccess) return e;
+    a.nbrange = b.nbrange;
+    a.nbval = b.nbval[b.nbsorted];
+    a.cut2 = INFINITY;
+  }
   a.rd = psi ? (double)p.r_max : 0.0;
   a.r2d = a.rd * a.rd;
   a.inv_rrd = psi ? 1.0 / fmax((double)p.r_max, 1e-6) : 0.0;

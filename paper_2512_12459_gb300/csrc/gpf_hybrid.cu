@@ -19,9 +19,18 @@
 //     of centre cells around its own cell for the k_min nearest means (ring R
 //     can be closed once the k-th distance is at most R cells), then sums
 //     those instead.
+// The same selection serves the backward (Sec. 4.2, Differentiable
+// Accumulation, with N(x) held fixed): a counting pass writes each hit
+// point's number of selected Gaussians, their exclusive scan gives each
+// point its offset, an emitting pass writes the (Gaussian, hit point) pairs
+// there in the order the selection visits them, and a stable sort by
+// Gaussian leaves every Gaussian's hit points in increasing order: the
+// pairs, and so the backward's sums, do not depend on thread timing.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "gpf_internal.h"
 
@@ -33,6 +42,9 @@ constexpr int kHybWarps = 4;
 constexpr int kHybThreads = kHybWarps * kWarp;
 constexpr int kMaxTileCells = 512;   // larger grown boxes: per-lane 27-cell walks
 constexpr int kMaxRing = 64;         // kNN rings searched at most (then: what was found)
+// What a pass of the selection produces: the forward's sums, each hit
+// point's number of selected pairs, or the pairs themselves.
+constexpr int kHybSums = 0, kHybCount = 1, kHybEmit = 2;
 
 struct HybArgs {
   Grid grid;
@@ -53,7 +65,19 @@ struct HybArgs {
   float* out;
   float* z;
   unsigned long long* next_tile;
+  uint32_t* nbcnt;         // count pass: pairs per point; emit pass: their offsets
+  uint32_t* nbkey;         // emit pass: Gaussian ids of the pairs
+  uint32_t* nbval;         // emit pass: hit point positions of the pairs
+  int64_t nb_max;          // capacity of nbkey / nbval
 };
+
+// Pair j of hit point position k (emit pass): written when it fits.
+__device__ __forceinline__ void emit_pair(const HybArgs& a, uint32_t pos, uint32_t g, int64_t k) {
+  if ((int64_t)pos < a.nb_max) {
+    a.nbkey[pos] = g;
+    a.nbval[pos] = (uint32_t)k;
+  }
+}
 
 template <int RS>
 __device__ __forceinline__ void hyb_load_rec(const float* __restrict__ rec, uint32_t g,
@@ -101,10 +125,11 @@ __device__ __forceinline__ bool in_centre_cell(const Grid& G, const float* r, ui
          (coord0(r[2], G.oz, G.inv_cell0, G.max0z) >> Lb) == cz;
 }
 
-// Lane-by-lane ball sum over the 3 x 3 x 3 centre cells around the lane's own.
-template <int C, bool PSI>
+// Lane-by-lane ball sum over the 3 x 3 x 3 centre cells around the lane's own
+// (or its count, or its pairs from offset pos for hit point position k).
+template <int C, bool PSI, int MODE>
 __device__ void lane_ball(const HybArgs& a, float px, float py, float pz, float (&L)[C],
-                          float& Z, int& cnt) {
+                          float& Z, int& cnt, uint32_t pos, int64_t k) {
   constexpr int RS = rec_stride(C);
   const Grid& G = a.grid;
   const int Lb = G.blevel;
@@ -124,20 +149,25 @@ __device__ void lane_ball(const HybArgs& a, float px, float py, float pz, float 
           hyb_load_rec<RS>(a.rec, v & G.id_mask, rr);
           if (!in_centre_cell(G, rr, cx, cy, cz)) continue;
           if (mean_d2(rr, px, py, pz) > a.ball_r2) continue;
-          const float w = hyb_weight<PSI>(rr, px, py, pz, a);
+          if (MODE == kHybSums) {
+            const float w = hyb_weight<PSI>(rr, px, py, pz, a);
 #pragma unroll
-          for (int c = 0; c < C; ++c) L[c] = fmaf(w, rr[13 + c], L[c]);
-          Z += w;
+            for (int c = 0; c < C; ++c) L[c] = fmaf(w, rr[13 + c], L[c]);
+            Z += w;
+          } else if (MODE == kHybEmit) {
+            emit_pair(a, pos + (uint32_t)cnt, v & G.id_mask, k);
+          }
           ++cnt;
         }
       }
 }
 
 // The k_min nearest means by rings of centre cells around the lane's cell;
-// then the sums over them.
-template <int C, bool PSI>
-__device__ void lane_knn(const HybArgs& a, float px, float py, float pz, float (&L)[C],
-                         float& Z) {
+// then the sums over them (or their pairs from offset pos). Returns how many
+// were found (k_min unless the field is smaller or the rings run out).
+template <int C, bool PSI, int MODE>
+__device__ int lane_knn(const HybArgs& a, float px, float py, float pz, float (&L)[C],
+                        float& Z, uint32_t pos, int64_t k_pos) {
   constexpr int RS = rec_stride(C);
   const Grid& G = a.grid;
   const int Lb = G.blevel;
@@ -191,22 +221,33 @@ __device__ void lane_knn(const HybArgs& a, float px, float py, float pz, float (
     if (found == k && kd[k - 1] <= reach * reach) break;
   }
   for (int i = 0; i < found; ++i) {
-    float rr[RS];
-    hyb_load_rec<RS>(a.rec, kg[i], rr);
-    const float w = hyb_weight<PSI>(rr, px, py, pz, a);
+    if (MODE == kHybSums) {
+      float rr[RS];
+      hyb_load_rec<RS>(a.rec, kg[i], rr);
+      const float w = hyb_weight<PSI>(rr, px, py, pz, a);
 #pragma unroll
-    for (int c = 0; c < C; ++c) L[c] = fmaf(w, rr[13 + c], L[c]);
-    Z += w;
+      for (int c = 0; c < C; ++c) L[c] = fmaf(w, rr[13 + c], L[c]);
+      Z += w;
+    } else if (MODE == kHybEmit) {
+      emit_pair(a, pos + (uint32_t)i, kg[i], k_pos);
+    }
   }
+  return found;
 }
 
-template <int C, bool PSI>
+template <int C, bool PSI, int MODE>
 __global__ void __launch_bounds__(kHybThreads)
 hybrid_fwd_kernel(HybArgs a) {
   constexpr int RS = rec_stride(C);
   __shared__ __align__(16) float s_rec[kHybWarps][kWarp * RS];
+  __shared__ uint32_t s_gid[kHybWarps][kWarp];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   if (index_unusable(a.header)) return;
+  if (MODE == kHybEmit && (int64_t)a.header->nb_pairs > a.nb_max) {
+    // more pairs than room: flag it once; every later kernel leaves its outputs
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(const_cast<uint32_t*>(&a.header->overflow), 1u);
+    return;
+  }
   const Grid& G = a.grid;
   const int Lb = G.blevel;
   const int64_t n_act = a.header->n_active;
@@ -222,12 +263,14 @@ hybrid_fwd_kernel(HybArgs a) {
     const bool in_range = k < a.m;
     const bool active = k < n_act;
     const uint32_t q = in_range ? a.qval[k] : 0u;
-    if (in_range && !active) {
+    if (MODE == kHybSums && in_range && !active) {
 #pragma unroll
       for (int c = 0; c < C; ++c) a.out[(int64_t)c * a.m + q] = 0.0f;
       if (a.z) a.z[q] = 0.0f;
     }
+    if (MODE == kHybCount && in_range && !active) a.nbcnt[k] = 0u;
     if (tile * kWarp >= n_act) continue;  // warp-uniform
+    const uint32_t pos = MODE == kHybEmit && active ? a.nbcnt[k] : 0u;
     float px = 0.f, py = 0.f, pz = 0.f;
     if (active) {
       px = a.x[q];
@@ -284,10 +327,12 @@ hybrid_fwd_kernel(HybArgs a) {
               }
               const uint32_t kb = __ballot_sync(kFullMask, keep);
               if (keep) {
-                float4* dst = reinterpret_cast<float4*>(my_rec + __popc(kb & lanemask_lt()) * RS);
+                const int slot = __popc(kb & lanemask_lt());
+                float4* dst = reinterpret_cast<float4*>(my_rec + slot * RS);
 #pragma unroll
                 for (int q4 = 0; q4 < RS / 4; ++q4)
                   dst[q4] = make_float4(rr[4 * q4], rr[4 * q4 + 1], rr[4 * q4 + 2], rr[4 * q4 + 3]);
+                s_gid[wib][slot] = v & G.id_mask;
               }
               __syncwarp();
               const int nk = __popc(kb);
@@ -295,26 +340,33 @@ hybrid_fwd_kernel(HybArgs a) {
                 for (int s = 0; s < nk; ++s) {
                   const float* r = my_rec + s * RS;
                   if (mean_d2(r, px, py, pz) > a.ball_r2) continue;
-                  const float w = hyb_weight<PSI>(r, px, py, pz, a);
+                  if (MODE == kHybSums) {
+                    const float w = hyb_weight<PSI>(r, px, py, pz, a);
 #pragma unroll
-                  for (int c = 0; c < C; ++c) L[c] = fmaf(w, r[13 + c], L[c]);
-                  Z += w;
+                    for (int c = 0; c < C; ++c) L[c] = fmaf(w, r[13 + c], L[c]);
+                    Z += w;
+                  } else if (MODE == kHybEmit) {
+                    emit_pair(a, pos + (uint32_t)cnt, s_gid[wib][s], k);
+                  }
                   ++cnt;
                 }
               __syncwarp();
             }
           }
     } else if (active) {
-      lane_ball<C, PSI>(a, px, py, pz, L, Z, cnt);
+      lane_ball<C, PSI, MODE>(a, px, py, pz, L, Z, cnt, pos, k);
     }
-    // sparse neighbourhoods: the k_min nearest instead
+    // sparse neighbourhoods: the k_min nearest instead (in the emit pass they
+    // take the slots the ball's pairs were written to: there are at least as
+    // many of them, min(k_min, N) > cnt)
     if (active && a.n > 0 && cnt < a.k_min) {
 #pragma unroll
       for (int c = 0; c < C; ++c) L[c] = 0.0f;
       Z = 0.0f;
-      lane_knn<C, PSI>(a, px, py, pz, L, Z);
+      cnt = lane_knn<C, PSI, MODE>(a, px, py, pz, L, Z, pos, k);
     }
-    if (active) {
+    if (MODE == kHybCount && active) a.nbcnt[k] = (uint32_t)cnt;
+    if (MODE == kHybSums && active) {
       float scale = 1.0f;
       if (a.mode == GPF_NORMALIZED) scale = 1.0f / fmaxf(Z, a.eps);
 #pragma unroll
@@ -329,12 +381,11 @@ hybrid_fwd_kernel(HybArgs a) {
 
 }  // namespace
 
-cudaError_t launch_hybrid_forward(const IndexDims& d, const IndexBuffers& b,
-                                  const gpf_queries& q, const gpf_query_params& p, int64_t n,
-                                  float* out, float* z, const KernelEvents& ev,
-                                  cudaStream_t stream) {
-  if (q.m == 0) return cudaSuccess;
-  HybArgs a;
+namespace {
+
+HybArgs hyb_args(const IndexDims& d, const IndexBuffers& b, const gpf_queries& q,
+                 const gpf_query_params& p, int64_t n) {
+  HybArgs a{};
   a.grid = d.grid;
   a.qval = b.qval[b.qsorted];
   a.header = b.header;
@@ -354,19 +405,22 @@ cudaError_t launch_hybrid_forward(const IndexDims& d, const IndexBuffers& b,
   a.ball_r2 = p.ball_r * p.ball_r;
   a.k_min = (int64_t)p.k_min < n ? p.k_min : (int)n;
   a.n = n;
-  a.out = out;
-  a.z = z;
   a.next_tile = &b.header->next_tile;
+  return a;
+}
+
+// One pass of the selection kernel (persistent, tiles from the work counter).
+template <int MODE>
+cudaError_t hyb_pass(const HybArgs& a, int channels, bool psi, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(a.next_tile, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
-  const int64_t tiles = (q.m + kWarp - 1) / kWarp;
+  const int64_t tiles = (a.m + kWarp - 1) / kWarp;
   const int64_t want = (tiles + kHybWarps - 1) / kHybWarps;
-  if (ev.start && (e = cudaEventRecord(ev.start, stream)) != cudaSuccess) return e;
 #define GPF_HYB_LAUNCH(CC, PS)                                                               \
   do {                                                                                       \
     const unsigned blocks = (unsigned)persistent_blocks(                                     \
-        reinterpret_cast<const void*>(&hybrid_fwd_kernel<CC, PS>), kHybThreads, want);       \
-    hybrid_fwd_kernel<CC, PS><<<blocks, kHybThreads, 0, stream>>>(a);                        \
+        reinterpret_cast<const void*>(&hybrid_fwd_kernel<CC, PS, MODE>), kHybThreads, want); \
+    hybrid_fwd_kernel<CC, PS, MODE><<<blocks, kHybThreads, 0, stream>>>(a);                  \
   } while (0)
 #define GPF_HYB_CASE(CC)              \
   case CC:                            \
@@ -374,7 +428,7 @@ cudaError_t launch_hybrid_forward(const IndexDims& d, const IndexBuffers& b,
     else GPF_HYB_LAUNCH(CC, false);   \
     note_launches(1);                 \
     break;
-  switch (d.channels) {
+  switch (channels) {
     GPF_HYB_CASE(1)
     GPF_HYB_CASE(2)
     GPF_HYB_CASE(3)
@@ -388,8 +442,65 @@ cudaError_t launch_hybrid_forward(const IndexDims& d, const IndexBuffers& b,
   }
 #undef GPF_HYB_CASE
 #undef GPF_HYB_LAUNCH
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// [start, end) of every Gaussian's run of the sorted pairs (the others keep
+// the [0, 0) of the memset).
+__global__ void nb_range_kernel(const uint32_t* __restrict__ keys, const DeviceHeader* header,
+                                int64_t n_cap, uint2* __restrict__ range) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (index_unusable(header)) return;
+  const int64_t n = header->nb_pairs;
+  if (i >= n || i >= n_cap) return;
+  const uint32_t k = keys[i];
+  if (i == 0 || keys[i - 1] != k) range[k].x = (uint32_t)i;
+  if (i == n - 1 || keys[i + 1] != k) range[k].y = (uint32_t)(i + 1);
+}
+
+}  // namespace
+
+cudaError_t launch_hybrid_forward(const IndexDims& d, const IndexBuffers& b,
+                                  const gpf_queries& q, const gpf_query_params& p, int64_t n,
+                                  float* out, float* z, const KernelEvents& ev,
+                                  cudaStream_t stream) {
+  if (q.m == 0) return cudaSuccess;
+  HybArgs a = hyb_args(d, b, q, p, n);
+  a.out = out;
+  a.z = z;
+  cudaError_t e;
+  if (ev.start && (e = cudaEventRecord(ev.start, stream)) != cudaSuccess) return e;
+  if ((e = hyb_pass<kHybSums>(a, d.channels, isfinite(p.r_max), stream)) != cudaSuccess) return e;
   return ev.stop ? cudaEventRecord(ev.stop, stream) : cudaSuccess;
+}
+
+cudaError_t launch_hybrid_pairs(const IndexDims& d, const IndexBuffers& b, const gpf_queries& q,
+                                const gpf_query_params& p, int64_t n, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(b.nbrange, 0, sizeof(uint2) * (size_t)std::max<int64_t>(n, 1),
+                                  stream);
+  if (e != cudaSuccess) return e;
+  if (q.m == 0 || n == 0) return cudaMemsetAsync(&b.header->nb_pairs, 0, sizeof(uint32_t), stream);
+  HybArgs a = hyb_args(d, b, q, p, n);
+  a.nbcnt = b.nbcnt;
+  a.nbkey = b.nbkey[0];
+  a.nbval = b.nbval[0];
+  a.nb_max = d.nb_max;
+  const bool psi = isfinite(p.r_max);
+  // pairs per hit point, their offsets and total, the pairs themselves
+  if ((e = hyb_pass<kHybCount>(a, d.channels, psi, stream)) != cudaSuccess) return e;
+  if ((e = exclusive_scan_u32(b.nbcnt, b.nbcnt, q.m, &b.header->nb_pairs, b.scan_ws, stream)) !=
+      cudaSuccess)
+    return e;
+  if ((e = hyb_pass<kHybEmit>(a, d.channels, psi, stream)) != cudaSuccess) return e;
+  // by Gaussian, stable: each Gaussian's hit points stay in increasing order
+  e = radix_sort_pairs(b.nbkey[0], b.nbval[0], b.nbkey[1], b.nbval[1], d.nb_max,
+                       &b.header->nb_pairs, d.grid.id_bits, b.nbsort_ws, &b.header->stalled,
+                       stream);
+  if (e != cudaSuccess) return e;
+  nb_range_kernel<<<(unsigned)((d.nb_max + 255) / 256), 256, 0, stream>>>(
+      b.nbkey[b.nbsorted], b.header, d.nb_max, b.nbrange);
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 }  // namespace gpf

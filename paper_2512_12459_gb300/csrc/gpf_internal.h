@@ -74,6 +74,14 @@ struct IndexBuffers {
   uint32_t* gkey[2];    // [P_max] (bucket, Gaussian) entries, sort ping-pong
   uint32_t* gval[2];
   uint2* brange;        // [n_buckets] [start, end) of every bucket's list
+  // the GPF_NB_BALL_KNN backward (nb_max > 0): selected pairs, per-point
+  // counts / offsets, per-Gaussian ranges of the sorted pairs
+  uint32_t* nbkey[2];   // [nb_max] Gaussian ids (sort ping-pong)
+  uint32_t* nbval[2];   // [nb_max] sorted hit point positions
+  uint32_t* nbcnt;      // [M_max + 1] pairs per hit point, then their offsets
+  uint2* nbrange;       // [N_max] [start, end) of each Gaussian's pairs
+  void* nbsort_ws;
+  int nbsorted;
   float* dec;           // GPF_BF16 fields: decoded float32 [(10 + C), n] (rows
                         // mean 3, quat 4, logscale 3, spectrum C; N_max room)
   void* scan_ws;
@@ -91,6 +99,7 @@ struct IndexDims {
   int storage;          // storage form of the fields (gpf_field.storage)
   bool bf16;            // a 16-bit form (decoded at build)
   int64_t n_max, m_max, p_max;
+  int64_t nb_max;       // capacity of the GPF_NB_BALL_KNN backward's pairs
 };
 
 // GPF_BF16 fields are decoded into b.dec first and the build reads that.
@@ -118,6 +127,13 @@ cudaError_t launch_hybrid_forward(const IndexDims& dims, const IndexBuffers& b,
                                   const gpf_queries& q, const gpf_query_params& p, int64_t n,
                                   float* out, float* z, const KernelEvents& ev,
                                   cudaStream_t stream);
+// The selected (hit point, Gaussian) pairs of the GPF_NB_BALL_KNN query,
+// sorted by Gaussian: b.nbval[b.nbsorted] holds the hit point positions of
+// Gaussian g in [b.nbrange[g].x, b.nbrange[g].y) (gpf_hybrid.cu). Sets the
+// capacity flag when they exceed dims.nb_max.
+cudaError_t launch_hybrid_pairs(const IndexDims& dims, const IndexBuffers& b,
+                                const gpf_queries& q, const gpf_query_params& p, int64_t n,
+                                cudaStream_t stream);
 cudaError_t launch_backward(const IndexDims& dims, const IndexBuffers& b, const gpf_field& f,
                             const gpf_queries& q, const gpf_query_params& p,
                             const float* grad_out, const float* out, const float* z,

@@ -95,7 +95,7 @@ def make_index(field: Field, queries: Queries, cutoff_sigma: float = 3.0,
                max_queries: Optional[int] = None, headroom: float = 1.1, max_span: int = 4,
                query_cell: Optional[float] = None, hash_bits: Optional[int] = None,
                grid: Optional[GridConfig] = None, coop_cells: int = 0,
-               ball_radius: Optional[float] = None) -> Index:
+               ball_radius: Optional[float] = None, max_nb_pairs: int = 0) -> Index:
     """An index planned for (field, queries). With max_pairs=None the pair
     capacity comes from a trial build (gpf_index_stats) times `headroom`
     (room for the pairs to grow while the parameters are optimised)."""
@@ -109,6 +109,7 @@ def make_index(field: Field, queries: Queries, cutoff_sigma: float = 3.0,
     grid.field_storage = field.storage
     if ball_radius is not None:
         grid.ball_radius = float(ball_radius)
+    grid.max_nb_pairs = int(max_nb_pairs)
     grid.max_gaussians = max_gaussians if max_gaussians is not None else max(field.n, 1)
     grid.max_queries = max_queries if max_queries is not None else max(queries.m, 1)
     brute = brute_force or math.isinf(cutoff_sigma)

@@ -77,7 +77,7 @@ def test_sparse_field_falls_back_to_knn(gpf):
     assert ref["knn"].mean() > 0.9
 
 
-def test_hybrid_has_no_backward_and_needs_centre_entries(gpf):
+def test_hybrid_backward_needs_pair_room_and_centre_entries(gpf):
     import torch
     from paper_2512_12459_gb300.setup_index import make_index
     fnp, qnp = synth.config1_random(seed=97, n=200, m=500)
@@ -106,3 +106,98 @@ def test_hybrid_with_no_gaussians_returns_zeros(gpf):
                                   neighbourhood=gpf.GPF_NB_BALL_KNN, ball_r=R, k_min=3)
     torch.cuda.synchronize()
     assert torch.count_nonzero(out).item() == 0 and torch.count_nonzero(z).item() == 0
+
+
+def _bwd_case(gpf, fnp, qnp, mode, ball_r, k_min, cell=0.05, seed=0, f64=False, room=4.0):
+    """GPU gradients of the hybrid query and the oracle's, with the upstream
+    gradient zeroed at hit points whose selection float32 may decide
+    differently (a mean at the ball's edge, a k-th / (k+1)-th distance tie)."""
+    import torch
+    from paper_2512_12459_gb300.setup_index import make_index
+    field, queries = gpf.Field.from_numpy(fnp), gpf.Queries.from_numpy(qnp)
+    ref_f = oracle.hybrid_fwd(fnp.mean, fnp.quat, fnp.logscale, fnp.spectrum, qnp.x, qnp.n,
+                              qnp.wo, None, qnp.valid, mode=mode, r_max=R, ball_r=ball_r,
+                              k_min=k_min)
+    G = np.random.default_rng(seed).standard_normal((fnp.channels, qnp.m))
+    G[:, ref_f["near"]] = 0.0
+    G = G.astype(np.float32)
+    cap = int(room * max(1, ref_f["n_nb"].sum())) + 1024
+    idx = make_index(field, queries, query_cell=cell, ball_radius=max(ball_r, 0.02),
+                     max_nb_pairs=cap)
+    idx.build(field, queries)
+    out, z = gpf.gpf_radiance_fwd(idx, field, queries, mode, r_max=R,
+                                  neighbourhood=gpf.GPF_NB_BALL_KNN, ball_r=ball_r, k_min=k_min)
+    if f64:
+        # the gradient-check build is given the oracle's forward (rounded to
+        # float32), so that it checks the backward alone
+        out = torch.as_tensor(ref_f["out"], dtype=torch.float32, device="cuda").contiguous()
+        z = torch.as_tensor(ref_f["Z"], dtype=torch.float32, device="cuda").contiguous()
+    g = gpf.gpf_radiance_bwd(idx, field, queries, torch.as_tensor(G, device="cuda"), out, z, mode,
+                             r_max=R, neighbourhood=gpf.GPF_NB_BALL_KNN, ball_r=ball_r,
+                             k_min=k_min, f64_sums=f64)
+    torch.cuda.synchronize()
+    ref = oracle.hybrid_bwd(fnp.mean, fnp.quat, fnp.logscale, fnp.spectrum, qnp.x, qnp.n,
+                            qnp.wo, G, None, qnp.valid, mode=mode, r_max=R, ball_r=ball_r,
+                            k_min=k_min)
+    gg = {k: getattr(g, k).cpu().numpy().astype(np.float64)
+          for k in ("mean", "quat", "logscale", "spectrum")}
+    return gg, ref, ref_f, idx
+
+
+def _anisotropic(fnp, seed):
+    rng = np.random.default_rng(seed)
+    fnp.logscale = (fnp.logscale + rng.normal(0.0, 0.3, fnp.logscale.shape)).astype(np.float32)
+    return fnp
+
+
+@pytest.mark.parametrize("mode", [oracle.GPF_NORMALIZED, oracle.GPF_SUM])
+@pytest.mark.parametrize("ball_r,k_min", [(R, 3), (R, 0), (0.0, 3)])
+def test_hybrid_backward_matches_the_oracle(gpf, mode, ball_r, k_min):
+    """Sec. 4.2, Differentiable Accumulation over N(x) = ball(r) or kNN(k_min)
+    held fixed, and the ablation's ball-only and kNN-only selections."""
+    from gpu_helpers import GRAD_TOL, grad_err
+    pos, flux = synth.caustic_photons(4000, seed=191)
+    fnp = _anisotropic(synth.field_from_photons(pos, flux, seed=191), 191)
+    qnp = synth.pinhole_hitpoints((0.0, -6.0, 4.0), (0.0, 0.0, 0.5), 64, 48)
+    g, ref, ref_f, idx = _bwd_case(gpf, fnp, qnp, mode, ball_r, k_min)
+    if k_min and ball_r:
+        assert ref_f["knn"].any() and (~ref_f["knn"] & (ref_f["n_nb"] > k_min)).any()
+    for k in g:
+        assert grad_err(g[k], ref[k]) < GRAD_TOL, (k, grad_err(g[k], ref[k]))
+
+
+@pytest.mark.parametrize("mode", [oracle.GPF_NORMALIZED, oracle.GPF_SUM])
+def test_hybrid_backward_float64_sums(gpf, mode):
+    """The gradient-check build on the hybrid pairs: 1e-6 normwise."""
+    from gpu_helpers import grad_err
+    pos, flux = synth.caustic_photons(4000, seed=192)
+    fnp = _anisotropic(synth.field_from_photons(pos, flux, seed=192), 192)
+    qnp = synth.pinhole_hitpoints((0.0, -6.0, 4.0), (0.0, 0.0, 0.5), 64, 48)
+    g, ref, _, _ = _bwd_case(gpf, fnp, qnp, mode, R, 3, f64=True, seed=3)
+    for k in g:
+        assert grad_err(g[k], ref[k]) < 1e-6, (k, grad_err(g[k], ref[k]))
+
+
+def test_hybrid_backward_is_reproducible_and_flags_a_full_pair_buffer(gpf):
+    import torch
+    from paper_2512_12459_gb300 import _abi
+    from paper_2512_12459_gb300.setup_index import make_index
+    pos, flux = synth.caustic_photons(5000, seed=193)
+    fnp = synth.field_from_photons(pos, flux, seed=193)
+    qnp = synth.pinhole_hitpoints((0.0, -6.0, 4.0), (0.0, 0.0, 0.5), 64, 64)
+    g1, _, _, _ = _bwd_case(gpf, fnp, qnp, oracle.GPF_NORMALIZED, R, 3, seed=4)
+    g2, _, _, _ = _bwd_case(gpf, fnp, qnp, oracle.GPF_NORMALIZED, R, 3, seed=4)
+    for k in g1:
+        assert np.array_equal(g1[k], g2[k])
+    # room for fewer pairs than the neighbourhoods hold: flagged, untouched
+    field, queries = gpf.Field.from_numpy(fnp), gpf.Queries.from_numpy(qnp)
+    idx = make_index(field, queries, query_cell=0.05, ball_radius=R, max_nb_pairs=100)
+    idx.build(field, queries)
+    out, z = gpf.gpf_radiance_fwd(idx, field, queries, gpf.GPF_SUM, r_max=R,
+                                  neighbourhood=gpf.GPF_NB_BALL_KNN, ball_r=R, k_min=3)
+    grads = gpf.Field(*(torch.full_like(t, 7.0) for t in field.tensors()))
+    gpf.gpf_radiance_bwd(idx, field, queries, torch.ones_like(out), out, z, gpf.GPF_SUM, r_max=R,
+                         neighbourhood=gpf.GPF_NB_BALL_KNN, ball_r=R, k_min=3, grads=grads)
+    torch.cuda.synchronize()
+    assert all(torch.all(t == 7.0) for t in grads.tensors())
+    assert idx.stats()["flags"] & _abi.GPF_FLAG_CAPACITY

@@ -536,3 +536,74 @@ def test_hybrid_with_a_ball_holding_everything_is_the_untruncated_sum():
                             qnp.wo, mode=oracle.GPF_NORMALIZED, r_max=0.05,
                             cutoff_sigma=math.inf)
     np.testing.assert_allclose(a["out"], b["out"], rtol=1e-12, atol=1e-300)
+
+
+def _hybrid_objective(f, q, G, kw):
+    out = oracle.hybrid_fwd(f["mean"], f["quat"], f["logscale"], f["spectrum"], q["x"], q["n"],
+                            q["wo"], albedo=q.get("albedo"), **kw)["out"]
+    return float(np.sum(G * out))
+
+
+@pytest.mark.parametrize("mode", [oracle.GPF_SUM, oracle.GPF_NORMALIZED])
+@pytest.mark.parametrize("ball_r,k_min", [(0.09, 3), (0.0, 4), (0.12, 0)])
+def test_hybrid_gradient_matches_central_differences(mode, ball_r, k_min):
+    """hybrid_bwd against central differences of hybrid_fwd. The selection
+    N(x) is piecewise constant: the points are chosen so that no mean lies
+    within 1e-3 (relative, in squared distance) of a ball's edge and no k-th /
+    (k+1)-th nearest distances are that close, so steps of 1e-6 never change
+    it and the differences see the smooth part only."""
+    rng = np.random.default_rng(int(ball_r * 1000) * 31 + k_min * 7 + mode)
+    n, m, c = 7, 24, 3
+    f = {"mean": rng.uniform(0, 0.25, (3, n)), "quat": rng.standard_normal((4, n)),
+         "logscale": rng.normal(-2.4, 0.3, (3, n)), "spectrum": rng.uniform(-0.5, 1.0, (c, n))}
+    x = rng.uniform(0.0, 0.25, (3, m))
+    nn = rng.standard_normal((3, m)); wo = rng.standard_normal((3, m))
+    kw = dict(mode=mode, r_max=0.05, ball_r=ball_r, k_min=k_min)
+    fwd = oracle.hybrid_fwd(f["mean"], f["quat"], f["logscale"], f["spectrum"], x, nn, wo,
+                            band=1e-3, **kw)
+    keep = ~fwd["near"]
+    x, nn, wo = x[:, keep], nn[:, keep], wo[:, keep]
+    q = {"x": x, "n": nn, "wo": wo, "albedo": rng.uniform(0.3, 1.0, (c, x.shape[1]))}
+    assert x.shape[1] >= 12
+    G = rng.standard_normal((c, x.shape[1]))
+    an = oracle.hybrid_bwd(f["mean"], f["quat"], f["logscale"], f["spectrum"], x, nn, wo, G,
+                           albedo=q["albedo"], **kw)
+    for key in ("mean", "quat", "logscale", "spectrum"):
+        num = np.zeros_like(f[key])
+        for idx in np.ndindex(*f[key].shape):
+            fp = {k: v.copy() for k, v in f.items()}
+            fm = {k: v.copy() for k, v in f.items()}
+            fp[key][idx] += 1e-6
+            fm[key][idx] -= 1e-6
+            num[idx] = (_hybrid_objective(fp, q, G, kw) - _hybrid_objective(fm, q, G, kw)) / 2e-6
+        err = np.linalg.norm(num - an[key]) / max(np.linalg.norm(an[key]), 1e-300)
+        assert err < 1e-6, (key, err)
+        assert np.linalg.norm(an[key]) > 0.0
+
+
+def test_hybrid_gradient_with_a_ball_holding_everything_is_the_untruncated_gradient():
+    fnp, qnp = synth.config1_random(seed=34, n=40, m=30, albedo=True)
+    G = np.random.default_rng(34).standard_normal((3, 30))
+    for mode in (oracle.GPF_SUM, oracle.GPF_NORMALIZED):
+        a = oracle.hybrid_bwd(fnp.mean, fnp.quat, fnp.logscale, fnp.spectrum, qnp.x, qnp.n,
+                              qnp.wo, G, qnp.albedo, mode=mode, r_max=0.05, ball_r=10.0, k_min=3)
+        b = oracle.radiance_bwd(fnp.mean, fnp.quat, fnp.logscale, fnp.spectrum, qnp.x, qnp.n,
+                                qnp.wo, G, qnp.albedo, mode=mode, r_max=0.05,
+                                cutoff_sigma=math.inf)
+        for k in ("mean", "quat", "logscale", "spectrum"):
+            np.testing.assert_allclose(a[k], b[k], rtol=1e-12, atol=1e-14 * np.abs(b[k]).max())
+
+
+def test_hybrid_gradient_of_a_knn_only_selection_on_a_line():
+    """kNN only (k_min = 2) at the origin of the line field: only the two
+    nearest Gaussians get gradients; d O / d Phi_i = w_i for them (GPF_SUM),
+    and the others are exactly zero."""
+    dists = [0.01, 0.05, -0.09, 0.2]
+    mean, quat, lsc, spec = _line_field(dists, [1.0, 2.0, 4.0, 8.0])
+    x = np.zeros((3, 1))
+    nrm = np.array([[0.0], [0.0], [1.0]])
+    g = oracle.hybrid_bwd(mean, quat, lsc, spec, x, nrm, nrm, np.ones((1, 1)),
+                          mode=oracle.GPF_SUM, r_max=0.02, ball_r=0.0, k_min=2)
+    np.testing.assert_allclose(g["spectrum"][0], [_w_line(0.01), _w_line(0.05), 0.0, 0.0],
+                               rtol=1e-13, atol=0)
+    assert np.all(g["mean"][:, 2:] == 0) and np.all(g["logscale"][:, 2:] == 0)
