@@ -503,7 +503,9 @@ __global__ void __launch_bounds__(kBwdThreads, sizeof(T) == 4 ? 9 : 2)
 bwd_grid_kernel(BwdArgs a) {
   constexpr int QS = qrec_stride(C);
   constexpr int NS = Acc<C, T>::NS;
-  const int lane = threadIdx.x & 31;
+  // per warp: first hit point minus flattened start of each non-empty row
+  __shared__ uint32_t s_base[kBwdWarps][kWarp];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   if (index_unusable(a.header)) return;
   const int64_t n_small = a.header->n_small, n_live = a.header->n_live;
   const int64_t small_warps = (n_small + kWarp - 1) / kWarp;
@@ -588,21 +590,29 @@ bwd_grid_kernel(BwdArgs a) {
     }
     const uint32_t tot = __shfl_sync(kFullMask, incl, 31);
     const uint32_t excl = incl - cnt;
+    // item f of the flattened rows belongs to the non-empty row with the
+    // largest start excl <= f. The non-empty rows, ranked in lane order, keep
+    // (first hit point - start) in shared memory; a chunk's owner ranks come
+    // from the starts that fall inside it (a bit per start, OR-reduced over
+    // the warp) counted up to each lane, on top of the rank of the row that
+    // holds the chunk's first item.
+    const bool ne = cnt > 0;
+    const uint32_t ne_mask = __ballot_sync(kFullMask, ne);
+    if (ne) s_base[wib][__popc(ne_mask & lanemask_lt())] = qs - excl;
+    __syncwarp();
+    const uint32_t le = lanemask_lt() | (1u << lane);
     for (uint32_t f0 = 0; f0 < tot; f0 += kWarp) {
       const uint32_t f = f0 + lane;
-      int src = 0;
-#pragma unroll
-      for (int st = 16; st > 0; st >>= 1) {
-        const uint32_t vv = __shfl_sync(kFullMask, incl, src + st - 1);
-        if (vv <= f) src += st;
-      }
-      const uint32_t qs_s = __shfl_sync(kFullMask, qs, src);
-      const uint32_t ex_s = __shfl_sync(kFullMask, excl, src);
+      const uint32_t starts =
+          __reduce_or_sync(kFullMask, ne && excl > f0 && excl < f0 + kWarp ? 1u << (excl - f0) : 0u);
+      const int r0 = __popc(__ballot_sync(kFullMask, ne && excl <= f0)) - 1;
       if (f < tot) {
-        const int64_t k = (int64_t)qs_s + (f - ex_s);
-        bwd_pair<C, PSI, T>(P, a.qrec + k * QS, a, acc);
+        const int r = r0 + __popc(starts & le);
+        const uint32_t k = s_base[wib][r] + f;     // modulo 2^32: qs - excl may wrap
+        bwd_pair<C, PSI, T>(P, a.qrec + (int64_t)k * QS, a, acc);
       }
     }
+    __syncwarp();
   }
   T v[NS];
   acc.to_array(v);

@@ -149,7 +149,8 @@ __global__ void quantize_bf16_kernel(gpf_field src, gpf_field dst) {
 
 // Per Gaussian: record, level box, the number of cells of that box holding a
 // hit point (its list entries) and its key in the backward's order.
-__global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brute,
+__global__ void __launch_bounds__(kThreads, 4)
+preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brute,
                                   float* __restrict__ rec, int rs, uint4* __restrict__ box,
                                   const uint32_t* __restrict__ occ,
                                   uint32_t* __restrict__ gcount, uint8_t* __restrict__ glive,
@@ -163,20 +164,16 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
   if (g < n) {
     const float* mean = static_cast<const float*>(f.mean);
     const float* spec = static_cast<const float*>(f.spectrum);
-    const float* quat = static_cast<const float*>(f.quat);
-    const float* lsc = static_cast<const float*>(f.logscale);
     const float mu[3] = {mean[g], mean[n + g], mean[2 * n + g]};
-    // every parameter finite
-    bool fin = isfinite(mu[0]) && isfinite(mu[1]) && isfinite(mu[2]);
-    for (int k = 0; k < 4; ++k) fin = fin && isfinite(quat[k * n + g]);
-    for (int k = 0; k < 3; ++k) fin = fin && isfinite(lsc[k * n + g]);
-    for (int c = 0; c < f.channels; ++c) fin = fin && isfinite(spec[(int64_t)c * n + g]);
-    bad = !fin;
-    const Frame fr = gaussian_frame(quat, lsc, n, g);
+    const Frame fr = gaussian_frame(static_cast<const float*>(f.quat),
+                                    static_cast<const float*>(f.logscale), n, g);
     // the record's first 16 floats in registers, stored as four float4 once
     // the level is known (rs is a multiple of 4, the record 16-byte aligned)
     float rv[16];
     const float smax = fmaxf(fr.s[0], fmaxf(fr.s[1], fr.s[2]));
+    // non-finite parameters: an infinite log-scale shows in max s; the rest
+    // in the record (checked where it is stored)
+    uint32_t nf = ~__float_as_uint(smax) & 0x7f800000u ? 0u : 1u;
     rv[0] = mu[0]; rv[1] = mu[1]; rv[2] = mu[2];
     // bounding sphere of the k-sigma ellipsoid, widened by 1e-4 for rounding
     rv[3] = isinf(cutoff) ? INFINITY : cutoff * smax * 1.0001f;
@@ -275,8 +272,18 @@ __global__ void preprocess_kernel(gpf_field f, Grid grid, float cutoff, int brut
 #pragma unroll
     for (int v = 0; v < 4; ++v)
       r4[v] = make_float4(rv[4 * v], rv[4 * v + 1], rv[4 * v + 2], rv[4 * v + 3]);
-    for (int c = 16; c < rs; ++c)
-      rec[g * rs + c] = c - 13 < f.channels ? spec[(int64_t)(c - 13) * n + g] : 0.0f;
+    // every parameter finite: a NaN or infinite mean, quaternion or
+    // log-scale leaves a non-finite value in the record's mean or M = S^-1 R^T
+    // (an infinite log-scale in max s), and a spectrum value is stored as is
+#pragma unroll
+    for (int v = 0; v < 16; ++v)
+      if (v != 3) nf |= ~__float_as_uint(rv[v]) & 0x7f800000u ? 0u : 1u;
+    for (int c = 16; c < rs; ++c) {
+      const float sv = c - 13 < f.channels ? spec[(int64_t)(c - 13) * n + g] : 0.0f;
+      nf |= ~__float_as_uint(sv) & 0x7f800000u ? 0u : 1u;
+      rec[g * rs + c] = sv;
+    }
+    bad = nf != 0u;
   }
   __shared__ uint32_t s_cnt[kBlockWarps][4];
   __shared__ uint32_t s_mask;
