@@ -108,3 +108,26 @@ def test_bf16_fields_are_validated():
                                None)
     assert lib.gpf_adam_step(ctypes.byref(dst), ctypes.byref(g), ctypes.byref(g), ctypes.byref(g),
                              ctypes.byref(hp), None) == 1
+
+
+def test_bfloat16_spectra_cannot_hold_a_1e3_per_pixel_bound():
+    """The bound behind the 16-bit storage reading: a pixel carried by one
+    Gaussian has O = rho w Phi, so a bfloat16 spectrum's rounding error is the
+    pixel's error. Round to nearest keeps it below 2^-8 / (1 + 2^-8), the
+    value Phi = 1 + 2^-8 (a tie, rounded to even: 1) reaches it, and over
+    Exp(1) spectra the largest errors come close to it, far above 1e-3; a
+    float16 spectrum (10 stored bits) stays below 2^-11 < 1e-3."""
+    bound = 2.0 ** -8 / (1.0 + 2.0 ** -8)
+    phi = np.array([1.0 + 2.0 ** -8], dtype=np.float32)
+    got = storage.bf16_to_f32(storage.f32_to_bf16(phi))
+    assert got[0] == 1.0
+    np.testing.assert_allclose(abs(float(phi[0]) - float(got[0])) / float(phi[0]), bound,
+                               rtol=1e-12)
+    rng = np.random.default_rng(7)
+    x = rng.exponential(1.0, 1_000_000).astype(np.float32)
+    x = x[x > 1e-30]
+    rel = np.abs(storage.bf16_to_f32(storage.f32_to_bf16(x)).astype(np.float64) - x) / x
+    assert rel.max() <= bound * (1 + 1e-12)
+    assert rel.max() > 3.5e-3 and np.quantile(rel, 0.5) > 5e-4
+    half = np.abs(x.astype(np.float16).astype(np.float64) - x) / x
+    assert half[x > 6.2e-5].max() <= 2.0 ** -11
