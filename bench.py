@@ -416,7 +416,8 @@ def run_batched(args):
         "graph_host_launches_per_step": graph_launches / args.steps,
         "autotuned": {"query_cell": grid.cell_size * (1 << grid.query_level),
                       "query_level": grid.query_level, "max_span": grid.max_span,
-                      "coop_cells": grid.coop_cells, "levels": grid.levels,
+                      "coop_cells": grid.coop_cells, "split_items": grid.split_items,
+                      "levels": grid.levels,
                       "hash_bits": grid.hash_bits},
         "autotune_trials": [[k, round(ms, 3)] for k, ms in report],
         "setup_s": {"generate": round(gen_s, 1), "autotune": round(tune_s, 1)},
@@ -483,7 +484,8 @@ def run_train(args):
                    "hit_points": int(qnp.m), "active_hit_points": n_active,
                    "l2": "inputs larger than L2",
                    "grid": {"query_cell": grid.cell_size * (1 << grid.query_level),
-                            "max_span": grid.max_span, "coop_cells": grid.coop_cells}},
+                            "max_span": grid.max_span, "coop_cells": grid.coop_cells,
+                            "split_items": grid.split_items}},
         "loss": {str(i + 2): lh[i] for i in marks},   # step 1 ran before the capture
         "loss_ratio_last_first": lh[-1] / lh[0],
         "setup_s": {"generate": round(gen_s, 1)},
@@ -593,8 +595,11 @@ def run_kde(args):
                                torch.as_tensor(flux.T.copy(), dtype=torch.float32, device="cuda"),
                                R_MAX)
     queries = gpf.Queries.from_numpy(qnp)
+    # the dense caustic cores put up to ~10^5 photons in a tile's lists: tiles
+    # are split over several work units while the grid is tuned
     grid, _ = autotune(photons, queries, mode=gpf.GPF_DISK_KDE, r_max=R_MAX, repeats=1,
-                       max_spans=(3, 4, 6, 8), coop_options=(1, 2, 4, 8), backward=False)
+                       max_spans=(3, 4, 6, 8), coop_options=(1, 2, 4, 8), backward=False,
+                       split_options=(8192, 2048, 32768, 0))
     idx = make_index(photons, queries, grid=grid)
     out = torch.empty((3, queries.m), device="cuda")
     z = torch.empty((queries.m,), device="cuda")
@@ -629,7 +634,8 @@ def run_kde(args):
         "ms_breakdown": {"build": build_ms, "gather": gather_ms},
         "photons_gathered": gathered, "photons_per_hit_point": gathered / max(n_active, 1),
         "grid": {"query_cell": grid.cell_size * (1 << grid.query_level), "levels": grid.levels,
-                 "max_span": grid.max_span, "coop_cells": grid.coop_cells},
+                 "max_span": grid.max_span, "coop_cells": grid.coop_cells,
+                 "split_items": grid.split_items},
     }
     print(json.dumps(line), flush=True)
 
@@ -769,7 +775,7 @@ def main():
     ap.add_argument("--batched-photons", type=int, default=2_000_000)
     ap.add_argument("--bf16-photons", type=int, default=4_000_000)
     ap.add_argument("--bf16-views", type=int, default=16)
-    ap.add_argument("--grid", default=None, metavar="QUERY_CELL,MAX_SPAN,COOP",
+    ap.add_argument("--grid", default=None, metavar="QUERY_CELL,MAX_SPAN,COOP[,SPLIT]",
                     help="single workload: this grid instead of the autotuned one (the "
                          "profiling commands pin the grid the autotuner chose, so that every "
                          "run captures the same launches)")
@@ -836,9 +842,11 @@ def main():
     # scene (outside the timed region); headroom for the pairs to grow as
     # Adam moves the Gaussians
     if args.grid:
-        qc, span, coop = args.grid.split(",")
+        parts = args.grid.split(",")
+        qc, span, coop = parts[:3]
         idx = make_index(field, queries, cutoff_sigma=CUTOFF, headroom=1.25,
-                         query_cell=float(qc), max_span=int(span), coop_cells=int(coop))
+                         query_cell=float(qc), max_span=int(span), coop_cells=int(coop),
+                         split_items=int(parts[3]) if len(parts) > 3 else 0)
     else:
         tuned, _ = autotune(field, queries, cutoff_sigma=CUTOFF, r_max=R_MAX, repeats=2)
         idx = make_index(field, queries, grid=tuned, headroom=1.25)
@@ -1040,6 +1048,7 @@ def main():
                                 "levels": idx.grid.levels, "finest_cell": idx.grid.cell_size,
                                 "max_span": idx.grid.max_span,
                                 "coop_cells": idx.grid.coop_cells,
+                                "split_items": idx.grid.split_items,
                                 "autotuned": not args.grid}},
             "fwd_queries_per_s": n_active / (ms["fwd"] / 1e3),
             "fwd_bwd_queries_per_s": n_active / ((ms["fwd"] + ms["bwd"] + ms["loss"]) / 1e3),

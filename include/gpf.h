@@ -221,7 +221,19 @@ typedef struct gpf_grid_config {
                             backward is refused). A backward whose
                             neighbourhoods hold more pairs sets the capacity
                             flag and leaves its gradients untouched.         */
+  int32_t split_items;   /* forward load balance: 0 = every tile of 32 hit
+                            points is one work unit; > 0 = the build
+                            estimates each tile's work (the list entries its
+                            points walk) and splits a tile above this many
+                            into up to GPF_MAX_TILE_PARTS units over disjoint
+                            chunks of its lists, whose partial sums a final
+                            kernel adds in part order (results still
+                            deterministic; they differ from the unsplit sums
+                            by summation order only)                         */
+  int32_t reserved2;     /* 0                                                */
 } gpf_grid_config;
+#define GPF_MAX_TILE_PARTS 64
+#define GPF_MAX_SPLIT_UNITS 32768
 
 /* Opaque host-side handle. It holds sizes and pointers into the workspace;
  * the device data live in the caller's workspace. */

@@ -211,6 +211,7 @@ class GridConfig:
     field_storage: int = 0     # GPF_F32 or GPF_BF16 fields
     ball_radius: float = 0.0   # > 0: centre entries for GPF_NB_BALL_KNN queries
     max_nb_pairs: int = 0      # capacity of the GPF_NB_BALL_KNN backward's pairs
+    split_items: int = 0       # > 0: split forward tiles of more estimated work
 
     def c_struct(self) -> _abi.gpf_grid_config:
         return _abi.gpf_grid_config((ctypes.c_float * 3)(*self.origin), float(self.cell_size),
@@ -221,7 +222,8 @@ class GridConfig:
                                     int(self.coop_cells), int(self.field_storage),
                                     float(self.ball_radius), int(self.max_gaussians),
                                     int(self.max_queries),
-                                    int(self.max_pairs), int(self.max_nb_pairs))
+                                    int(self.max_pairs), int(self.max_nb_pairs),
+                                    int(self.split_items), 0)
 
 
 def grid_for_bounds(lo: Sequence[float], hi: Sequence[float], cell_size: float, channels: int,

@@ -117,6 +117,14 @@ size_t layout(const gpf_index* ix, char* base, IndexBuffers* b) {
   t.occ = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * ((nb + 31) / 32)));
   t.brange = reinterpret_cast<uint2*>(take(sizeof(uint2) * nb));
   t.dec = d.bf16 ? reinterpret_cast<float*>(take(sizeof(float) * (10 + d.channels) * N)) : nullptr;
+  if (d.split_items > 0) {
+    const int64_t tiles = (M + kWarp - 1) / kWarp;
+    t.tparts = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (tiles + 1)));
+    t.xoff = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (tiles + 1)));
+    t.xunit = reinterpret_cast<uint4*>(take(sizeof(uint4) * GPF_MAX_SPLIT_UNITS));
+    t.xsum = reinterpret_cast<float*>(
+        take(sizeof(float) * (size_t)GPF_MAX_SPLIT_UNITS * (d.channels + 1) * kWarp));
+  }
   if (d.nb_max > 0) {
     for (int k = 0; k < 2; ++k) {
       t.nbkey[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * d.nb_max));
@@ -128,7 +136,7 @@ size_t layout(const gpf_index* ix, char* base, IndexBuffers* b) {
     t.nbsorted = radix_sort_passes(d.grid.id_bits) % 2;
   }
   t.scan_ws = take(scan_workspace_bytes(
-      std::max<int64_t>(std::max<int64_t>(std::max<int64_t>(N, 1), ncp), M + 1)));
+      std::max<int64_t>(std::max<int64_t>(std::max<int64_t>(N, 1), ncp), M + 2)));
   t.qsort_ws = take(radix_sort_workspace_bytes(M > 0 ? M : 1));
   t.gsort_ws = take(radix_sort_workspace_bytes(P > 0 ? P : 1));
   t.osort_ws = take(radix_sort_workspace_bytes(N > 0 ? N : 1));
@@ -296,6 +304,8 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
   if (cfg->max_gaussians >= kMaxSortN || cfg->max_queries >= kMaxSortN ||
       cfg->max_pairs >= kMaxSortN || cfg->max_nb_pairs >= kMaxSortN)
     return fail(GPF_ERR_INVALID_ARG, "capacities must be below 2^30");
+  if (cfg->split_items < 0 || cfg->reserved2 != 0)
+    return fail(GPF_ERR_INVALID_ARG, "split_items must be >= 0 and reserved2 0");
   if (cfg->max_nb_pairs > 0 && !(cfg->ball_radius > 0.0f))
     return fail(GPF_ERR_INVALID_ARG, "max_nb_pairs > 0 needs ball_radius > 0 (centre entries)");
   const uint64_t cells = (uint64_t)cfg->dims[0] * cfg->dims[1] * cfg->dims[2];
@@ -359,6 +369,7 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
   d.m_max = cfg->max_queries;
   d.p_max = d.brute ? 0 : cfg->max_pairs;
   d.nb_max = cfg->max_nb_pairs;
+  d.split_items = cfg->split_items;
   ix->ws_bytes = layout(ix, nullptr, nullptr);
   ix->built = false;
   *out = ix;

@@ -35,7 +35,8 @@ struct DeviceHeader {
   unsigned long long next_work;       // backward: next work item
   uint32_t nonfinite;    // 1 if a Gaussian parameter or an active hit point is not finite
   uint32_t nb_pairs;     // (hit point, Gaussian) pairs of the last hybrid backward
-  uint32_t pad[50];
+  uint32_t n_xunits;     // work units of the split forward tiles (<= GPF_MAX_SPLIT_UNITS)
+  uint32_t pad[49];
 };
 static_assert(sizeof(DeviceHeader) == 256, "header is one 256-byte block");
 

@@ -56,6 +56,9 @@ struct FwdArgs {
   float* z;                // [M] or null
   unsigned long long* counts;  // count mode: [candidates, included]
   unsigned long long* next_tile;  // work counter, zero at launch
+  const uint32_t* tparts;  // split forward: parts of each tile (null: no splitting)
+  const uint4* xunit;      // split forward: (tile, part, parts, valid) of each split unit
+  float* xsum;             // split forward: [unit][C + 1][32] partial sums
 };
 
 __device__ __forceinline__ float warp_min(float v) {
@@ -176,8 +179,10 @@ __device__ __forceinline__ void load_rec(const float* __restrict__ rec, uint32_t
 }
 
 // COUNT: count the evaluated and included pairs instead of summing radiance.
-template <int C, bool BRUTE, int KERN, bool COUNT>
-__global__ void __launch_bounds__(kFwdThreads)
+// SPLIT: the index splits heavy tiles into parts (a separate instantiation,
+// so that an index without splitting runs the plain tile loop).
+template <int C, bool BRUTE, int KERN, bool COUNT, bool SPLIT>
+__global__ void __launch_bounds__(kFwdThreads, C <= 4 ? 6 : 5)
 fwd_kernel(FwdArgs a) {
   constexpr int RS = rec_stride(C);
   __shared__ __align__(16) float s_rec[kFwdWarps][kWarp * RS];
@@ -185,31 +190,57 @@ fwd_kernel(FwdArgs a) {
   __shared__ int s_leader[kFwdWarps][kUnionMax];
   __shared__ uint2 s_range[kFwdWarps][kMaxLevels][kWarp];
   __shared__ float s_acc[kFwdWarps][C + 1][kWarp];  // pooled-mode sums per hit point
+  // the warp's work unit: its tile's part and number of parts (kept here, not
+  // in registers, which the pair loops need)
+  __shared__ uint32_t s_part[kFwdWarps], s_parts[kFwdWarps];
 
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   if (index_unusable(a.header)) return;
   const int64_t n_act = a.header->n_active;
   const int64_t n_tiles = (a.m + kWarp - 1) / kWarp;
+  // split tiles (heavy ones, when the index asks for it) come first as
+  // n_x units, one per part; then every tile as one unit (a split tile's is
+  // skipped)
+  const int64_t n_x = SPLIT ? (int64_t)a.header->n_xunits : 0;
   uint32_t n_eval = 0, n_inc = 0;
-  // persistent: every warp takes the next tile until none is left, so a
+  // persistent: every warp takes the next unit until none is left, so a
   // warp that drew a light tile goes on with another one
   for (;;) {
   __syncwarp();
-  unsigned long long tile_u = 0;
-  if (lane == 0) tile_u = atomicAdd(a.next_tile, 1ull);
-  const int64_t tile = (int64_t)__shfl_sync(kFullMask, tile_u, 0);
-  if (tile >= n_tiles) break;
+  unsigned long long unit_u = 0;
+  if (lane == 0) unit_u = atomicAdd(a.next_tile, 1ull);
+  const int64_t unit = (int64_t)__shfl_sync(kFullMask, unit_u, 0);
+  if (unit >= n_x + n_tiles) break;
+  int64_t tile;
+  uint32_t part = 0, parts = 1;
+  if (SPLIT && unit < n_x) {
+    const uint4 xu = a.xunit[unit];
+    if (!xu.w) continue;                      // a slot left over at the capacity edge
+    tile = xu.x;
+    part = xu.y;
+    parts = xu.z;
+  } else {
+    tile = unit - n_x;
+    if (SPLIT && n_x && a.tparts[tile] > 1) continue;  // done by its parts
+  }
+  const bool split = SPLIT && parts > 1;
+  if (SPLIT && lane == 0) {
+    s_part[wib] = part;
+    s_parts[wib] = parts;
+  }
+  if (SPLIT) __syncwarp();
   const int64_t base = tile * kWarp;
   const int64_t k = base + lane;
   const bool in_range = k < a.m;
   const bool active = k < n_act;
   const uint32_t q = in_range ? a.qval[k] : 0u;
-  if (!COUNT && in_range && !active) {
+  if (!COUNT && !split && in_range && !active) {
 #pragma unroll
     for (int c = 0; c < C; ++c) a.out[(int64_t)c * a.m + q] = 0.0f;
     if (a.z) a.z[q] = 0.0f;
   }
-  if (base >= n_act) continue;  // warp-uniform
+  if (base >= n_act) continue;  // warp-uniform (never a split tile)
+  uint32_t gchunk = 0;  // chunks of this tile's lists seen so far, all levels and modes
 
   float px = 0.f, py = 0.f, pz = 0.f;
   if (active) {
@@ -291,16 +322,26 @@ fwd_kernel(FwdArgs a) {
                          uz = (uint32_t)((cj >> 40) & kCoordMax);
           const uint32_t tag = cell_hash(G, lev, ux, uy, uz).tag;
           const uint2 rg = s_range[wib][lev][s_leader[wib][j]];
-          // entry words of the first chunk; each later chunk is fetched while
-          // the previous one is being vetted
-          uint32_t v = rg.x + lane < rg.y ? __ldg(a.gval + rg.x + lane) : 0u;
+          // chunks of 32 entries; a split tile's part takes every parts-th
+          // chunk of the tile's lists. The entry words of the next chunk are
+          // fetched while the current one is being vetted.
+          const uint32_t parts_ = SPLIT ? s_parts[wib] : 1u;
+          uint32_t c_first = 0;
+          if (SPLIT && parts_ > 1) {     // warp-uniform: only for split tiles
+            c_first = (s_part[wib] + parts_ - gchunk % parts_) % parts_;
+            gchunk += (rg.y - rg.x + kWarp - 1) / kWarp;
+          }
+          const uint32_t step = parts_ * kWarp;
+          uint32_t e_first = rg.x + c_first * kWarp;
+          uint32_t v = e_first + lane < rg.y ? __ldg(a.gval + e_first + lane) : 0u;
           uint32_t carry = 0xffffffffu;
-          for (uint32_t e0 = rg.x; e0 < rg.y; e0 += kWarp) {
+          for (uint32_t e0 = e_first; e0 < rg.y; e0 += step) {
             const uint32_t e = e0 + lane;
-            const uint32_t vn = e + kWarp < rg.y ? __ldg(a.gval + e + kWarp) : 0u;
+            const uint32_t vn = e + step < rg.y ? __ldg(a.gval + e + step) : 0u;
             // a Gaussian listed twice in a bucket sits on consecutive entries
             uint32_t vprev = __shfl_up_sync(kFullMask, v, 1);
-            if (lane == 0) vprev = carry;
+            if (lane == 0)
+              vprev = parts_ == 1 ? carry : e0 > rg.x ? __ldg(a.gval + e0 - 1) : 0xffffffffu;
             carry = __shfl_sync(kFullMask, v, kWarp - 1);
             bool keep = e < rg.y && (v & ~G.id_mask) == tag && v != vprev;
             const uint32_t g = v & G.id_mask;
@@ -389,15 +430,24 @@ fwd_kernel(FwdArgs a) {
           const uint32_t start = __shfl_sync(kFullMask, rg.x, src);
           return i < total ? __ldg(a.gval + start + (i - first)) : 0u;
         };
-        int own_n = owner_of(lane);
-        uint32_t v_n = entry_of(lane, own_n);
-        for (uint32_t b = 0; b < total; b += kWarp) {
+        // a split tile's part takes every parts-th chunk of 32 items
+        const uint32_t parts_ = SPLIT ? s_parts[wib] : 1u;
+        uint32_t c_first = 0;
+        if (SPLIT && parts_ > 1) {
+          c_first = (s_part[wib] + parts_ - gchunk % parts_) % parts_;
+          gchunk += (total + kWarp - 1) / kWarp;
+        }
+        const uint32_t step = parts_ * kWarp;
+        const uint32_t b_first = c_first * kWarp;
+        int own_n = owner_of(b_first + lane);
+        uint32_t v_n = entry_of(b_first + lane, own_n);
+        for (uint32_t b = b_first; b < total; b += step) {
           const uint32_t i = b + lane;
           const bool live = i < total;
           const int own = own_n;
           const uint32_t v = v_n;
-          own_n = owner_of(i + kWarp);
-          v_n = entry_of(i + kWarp, own_n);
+          own_n = owner_of(i + step);
+          v_n = entry_of(i + step, own_n);
           const bool chg = own != cur;
           if (__any_sync(kFullMask, chg)) {
             pooled_flush<C>(s_acc[wib], lane, cur, chg && cur >= 0 && cur < kWarp, pc);
@@ -413,7 +463,9 @@ fwd_kernel(FwdArgs a) {
           const uint32_t kk = i - o_first;  // position in the owner's list
           // the owner's previous entry is the previous item
           uint32_t vprev = __shfl_up_sync(kFullMask, v, 1);
-          if (lane == 0) vprev = carry;
+          if (lane == 0)
+            vprev = parts_ == 1 ? carry
+                                : live && kk > 0 ? __ldg(a.gval + o_start + kk - 1) : 0xffffffffu;
           carry = __shfl_sync(kFullMask, v, kWarp - 1);
           if (live && (v & ~G.id_mask) == o_tag && !(kk > 0 && v == vprev)) {
             float rr[RS];
@@ -440,7 +492,13 @@ fwd_kernel(FwdArgs a) {
 #pragma unroll
     for (int c = 0; c < C; ++c) L[c] += s_acc[wib][c][lane];
     Z += s_acc[wib][C][lane];
-    if (active) {
+    if (SPLIT && s_parts[wib] > 1) {
+      // this part's sums; fwd_split_combine_kernel adds the parts in order
+      float* xs = a.xsum + (size_t)unit * (C + 1) * kWarp;
+#pragma unroll
+      for (int c = 0; c < C; ++c) xs[c * kWarp + lane] = L[c];
+      xs[C * kWarp + lane] = Z;
+    } else if (active) {
       float scale = 1.0f;
       if (a.mode == GPF_NORMALIZED) scale = 1.0f / fmaxf(Z, a.eps);
       else if (a.mode == GPF_DISK_KDE) scale = a.kde_scale;
@@ -467,7 +525,137 @@ fwd_kernel(FwdArgs a) {
   }
 }
 
+// The split tiles' outputs: one warp per split unit of part 0, adding the
+// tile's parts in part order, then the epilogue of fwd_kernel.
+template <int C>
+__global__ void fwd_split_combine_kernel(FwdArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (index_unusable(a.header) || u >= (int64_t)a.header->n_xunits) return;
+  const uint4 xu = a.xunit[u];
+  if (!xu.w || xu.y != 0u) return;
+  const int64_t k = (int64_t)xu.x * kWarp + lane;
+  float L[C], Z = 0.0f;
+#pragma unroll
+  for (int c = 0; c < C; ++c) L[c] = 0.0f;
+  for (uint32_t p = 0; p < xu.z; ++p) {
+    const float* xs = a.xsum + (size_t)(u + p) * (C + 1) * kWarp;
+#pragma unroll
+    for (int c = 0; c < C; ++c) L[c] += xs[c * kWarp + lane];
+    Z += xs[C * kWarp + lane];
+  }
+  if (k >= a.m) return;
+  const uint32_t q = a.qval[k];
+  const bool active = k < (int64_t)a.header->n_active;
+  float scale = 1.0f;
+  if (a.mode == GPF_NORMALIZED) scale = 1.0f / fmaxf(Z, a.eps);
+  else if (a.mode == GPF_DISK_KDE) scale = a.kde_scale;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const float rho = a.albedo ? a.albedo[(int64_t)c * a.m + q] : 1.0f;
+    a.out[(int64_t)c * a.m + q] = active ? rho * (L[c] * scale) : 0.0f;
+  }
+  if (a.z) a.z[q] = active ? Z : 0.0f;
+}
+
+// Estimated work of every tile of 32 hit points, from a sample of eight of its
+// points (every fourth: neighbouring points of the cell order see similar
+// lists), on every used level: where the sample falls in at most
+// Grid::coop cells, the distinct cells' lists, counted 8 times for the
+// staged evaluation of their survivors by the whole warp; else the points'
+// own lists, counted 4 times for the points not sampled. Then the tile's
+// number of parts. Four tiles per warp, eight lanes each.
+__global__ void tile_cost_kernel(Grid grid, const DeviceHeader* header, const float* __restrict__ x,
+                                 const uint32_t* __restrict__ qval, int64_t m,
+                                 const uint2* __restrict__ brange, int split_items,
+                                 uint32_t* __restrict__ tparts, uint32_t* __restrict__ xparts) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t tile = gt >> 3;
+  const int64_t n_tiles = (m + kWarp - 1) / kWarp;
+  const int64_t n_act = header->n_active;
+  const int64_t k = tile * kWarp + (lane & 7) * 4;
+  const bool active = tile < n_tiles && k < n_act && !index_unusable(header);
+  const uint32_t group = 0xffu << (lane & ~7);      // the 8 lanes of this tile
+  uint32_t c0x = 0, c0y = 0, c0z = 0;
+  uint2 rg[kMaxLevels];
+  const uint32_t lmask = header->level_mask;
+  if (active) {
+    const uint32_t q = qval[k];
+    c0x = coord0(x[q], grid.ox, grid.inv_cell0, grid.max0x);
+    c0y = coord0(x[m + q], grid.oy, grid.inv_cell0, grid.max0y);
+    c0z = coord0(x[2 * m + q], grid.oz, grid.inv_cell0, grid.max0z);
+  }
+#pragma unroll
+  for (int lev = 0; lev < kMaxLevels; ++lev) {
+    rg[lev] = make_uint2(0u, 0u);
+    if (active && lev < grid.levels && ((lmask >> lev) & 1u))
+      rg[lev] = __ldg(brange + cell_hash(grid, lev, c0x >> lev, c0y >> lev, c0z >> lev).bucket);
+  }
+  uint32_t cost = 0;
+#pragma unroll
+  for (int lev = 0; lev < kMaxLevels; ++lev) {
+    if (lev >= grid.levels || !((lmask >> lev) & 1u)) continue;
+    const unsigned long long packed =
+        active ? ((unsigned long long)(c0x >> lev) | ((unsigned long long)(c0y >> lev) << 20) |
+                  ((unsigned long long)(c0z >> lev) << 40))
+               : ~0ull;
+    const uint32_t peers = __match_any_sync(kFullMask, packed) & group;
+    const bool leader = active && (peers & lanemask_lt()) == 0;
+    const int nu = __popc(__ballot_sync(kFullMask, leader) & group);
+    const uint32_t len = rg[lev].y - rg[lev].x;
+    // (eight samples see at most 8 cells: all 8 distinct reads as more than 8)
+    cost += nu <= min(grid.coop, 7) ? (leader ? 8u * len : 0u) : 4u * len;
+  }
+  // the eight lanes of a tile are consecutive: sum them
+  cost += __shfl_xor_sync(kFullMask, cost, 1);
+  cost += __shfl_xor_sync(kFullMask, cost, 2);
+  cost += __shfl_xor_sync(kFullMask, cost, 4);
+  if ((lane & 7) == 0 && tile < n_tiles) {
+    uint32_t parts = 1;
+    if (cost > (uint32_t)split_items)
+      parts = min((cost + (uint32_t)split_items - 1) / (uint32_t)split_items,
+                  (uint32_t)GPF_MAX_TILE_PARTS);
+    tparts[tile] = parts;
+    xparts[tile] = parts > 1 ? parts : 0u;
+  }
+}
+
+// The split units: tile t's parts at xoff[t] .. xoff[t] + parts - 1 (the
+// exclusive scan of the parts of split tiles); a tile whose units would not
+// all fit under GPF_MAX_SPLIT_UNITS runs unsplit, and its slots below the
+// limit are marked empty.
+__global__ void tile_units_kernel(int64_t n_tiles, uint32_t* __restrict__ tparts,
+                                  const uint32_t* __restrict__ xoff, uint4* __restrict__ xunit,
+                                  DeviceHeader* header) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) header->n_xunits = min(xoff[n_tiles], (uint32_t)GPF_MAX_SPLIT_UNITS);
+  if (t >= n_tiles) return;
+  const uint32_t parts = tparts[t];
+  if (parts <= 1) return;
+  const uint32_t o = xoff[t];
+  const bool fits = (uint64_t)o + parts <= (uint64_t)GPF_MAX_SPLIT_UNITS;
+  if (!fits) tparts[t] = 1;
+  for (uint32_t p = 0; p < parts && o + p < (uint32_t)GPF_MAX_SPLIT_UNITS; ++p)
+    xunit[o + p] = make_uint4((uint32_t)t, p, parts, fits ? 1u : 0u);
+}
+
 }  // namespace
+
+cudaError_t launch_tile_split(const IndexDims& d, const IndexBuffers& b, const gpf_queries& q,
+                              cudaStream_t stream) {
+  const int64_t n_tiles = (q.m + kWarp - 1) / kWarp;
+  uint32_t* xoff = b.xoff;
+  tile_cost_kernel<<<(unsigned)((n_tiles * 8 + 255) / 256), 256, 0, stream>>>(
+      d.grid, b.header, q.x, b.qval[b.qsorted], q.m, b.brange, d.split_items, b.tparts, xoff);
+  note_launches(1);
+  cudaError_t e = exclusive_scan_u32(xoff, xoff, n_tiles + 1, nullptr, b.scan_ws, stream);
+  if (e != cudaSuccess) return e;
+  tile_units_kernel<<<(unsigned)((n_tiles + 256) / 256), 256, 0, stream>>>(
+      n_tiles, b.tparts, xoff, b.xunit, b.header);
+  note_launches(1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_forward(const IndexDims& d, const IndexBuffers& b, const gpf_queries& q,
                            const gpf_query_params& p, int64_t n, float* out, float* z,
@@ -504,17 +692,26 @@ cudaError_t launch_forward(const IndexDims& d, const IndexBuffers& b, const gpf_
   a.z = z;
   a.counts = counts;
   a.next_tile = &b.header->next_tile;
+  const bool split = d.split_items > 0 && !d.brute;
+  a.tparts = split ? b.tparts : nullptr;
+  a.xunit = split ? b.xunit : nullptr;
+  a.xsum = split ? b.xsum : nullptr;
   {
     const cudaError_t e = cudaMemsetAsync(a.next_tile, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return e;
   }
-  const int64_t tiles = (q.m + kWarp - 1) / kWarp;
+  const int64_t tiles = (q.m + kWarp - 1) / kWarp + (split ? GPF_MAX_SPLIT_UNITS : 0);
   const int64_t want = (tiles + kFwdWarps - 1) / kFwdWarps;
-#define GPF_FWD_LAUNCH(CC, BR, PS, CN)                                                    \
+#define GPF_FWD_LAUNCH2(CC, BR, PS, CN, SP)                                                \
   do {                                                                                    \
     const unsigned blocks = (unsigned)persistent_blocks(                                  \
-        reinterpret_cast<const void*>(&fwd_kernel<CC, BR, PS, CN>), kFwdThreads, want);   \
-    fwd_kernel<CC, BR, PS, CN><<<blocks, kFwdThreads, 0, stream>>>(a);                    \
+        reinterpret_cast<const void*>(&fwd_kernel<CC, BR, PS, CN, SP>), kFwdThreads, want); \
+    fwd_kernel<CC, BR, PS, CN, SP><<<blocks, kFwdThreads, 0, stream>>>(a);                \
+  } while (0)
+#define GPF_FWD_LAUNCH(CC, BR, PS, CN)                \
+  do {                                                \
+    if (!BR && split) GPF_FWD_LAUNCH2(CC, false, PS, CN, true); \
+    else GPF_FWD_LAUNCH2(CC, BR, PS, CN, false);      \
   } while (0)
 #define GPF_FWD_MODES(CC, BR)                                          \
   do {                                                                 \
@@ -523,11 +720,15 @@ cudaError_t launch_forward(const IndexDims& d, const IndexBuffers& b, const gpf_
     else if (kern == kKernFalloff) GPF_FWD_LAUNCH(CC, BR, kKernFalloff, false); \
     else GPF_FWD_LAUNCH(CC, BR, kKernGauss, false);                    \
   } while (0)
-#define GPF_FWD_CASE(CC)                  \
-  case CC:                                \
-    if (d.brute) GPF_FWD_MODES(CC, true); \
-    else GPF_FWD_MODES(CC, false);        \
-    note_launches(1);                     \
+#define GPF_FWD_CASE(CC)                                                              \
+  case CC:                                                                            \
+    if (d.brute) GPF_FWD_MODES(CC, true);                                             \
+    else GPF_FWD_MODES(CC, false);                                                    \
+    note_launches(1);                                                                 \
+    if (split && !counts) {                                                           \
+      fwd_split_combine_kernel<CC><<<GPF_MAX_SPLIT_UNITS / 4, 128, 0, stream>>>(a);   \
+      note_launches(1);                                                               \
+    }                                                                                 \
     break;
   const int kern = p.mode == GPF_DISK_KDE ? kKernDisk : psi ? kKernFalloff : kKernGauss;
   if (ev.start) {
@@ -549,6 +750,7 @@ cudaError_t launch_forward(const IndexDims& d, const IndexBuffers& b, const gpf_
 #undef GPF_FWD_CASE
 #undef GPF_FWD_MODES
 #undef GPF_FWD_LAUNCH
+#undef GPF_FWD_LAUNCH2
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return ev.stop ? cudaEventRecord(ev.stop, stream) : cudaSuccess;

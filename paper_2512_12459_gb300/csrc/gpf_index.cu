@@ -558,6 +558,10 @@ cudaError_t launch_build(const IndexDims& d, const IndexBuffers& b, const gpf_fi
         b.gkey[b.gsorted], b.header, d.p_max, b.brange);
     note_launches(1);
   }
+  if (d.split_items > 0 && q.m > 0) {
+    e = launch_tile_split(d, b, q, stream);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 

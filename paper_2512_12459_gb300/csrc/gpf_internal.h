@@ -82,6 +82,11 @@ struct IndexBuffers {
   uint2* nbrange;       // [N_max] [start, end) of each Gaussian's pairs
   void* nbsort_ws;
   int nbsorted;
+  // forward tile splitting (split_items > 0)
+  uint32_t* tparts;     // [tiles_max + 1] parts of each tile (1 = not split), then scanned
+  uint32_t* xoff;       // [tiles_max + 1] parts of each split tile (0 otherwise), then scanned
+  uint4* xunit;         // [GPF_MAX_SPLIT_UNITS] (tile, part, parts, valid) of every split unit
+  float* xsum;          // [GPF_MAX_SPLIT_UNITS * (C + 1) * 32] partial sums of split units
   float* dec;           // GPF_BF16 fields: decoded float32 [(10 + C), n] (rows
                         // mean 3, quat 4, logscale 3, spectrum C; N_max room)
   void* scan_ws;
@@ -100,11 +105,17 @@ struct IndexDims {
   bool bf16;            // a 16-bit form (decoded at build)
   int64_t n_max, m_max, p_max;
   int64_t nb_max;       // capacity of the GPF_NB_BALL_KNN backward's pairs
+  int split_items;      // > 0: split forward tiles above this estimated work
 };
 
 // GPF_BF16 fields are decoded into b.dec first and the build reads that.
 cudaError_t launch_build(const IndexDims& dims, const IndexBuffers& b, const gpf_field& f,
                          const gpf_queries& q, cudaStream_t stream);
+// Forward tile splitting (split_items > 0), after the bucket ranges exist:
+// each tile's estimated work, its parts, and the table of split units
+// (gpf_fwd.cu).
+cudaError_t launch_tile_split(const IndexDims& dims, const IndexBuffers& b, const gpf_queries& q,
+                              cudaStream_t stream);
 // The float32 field the pair loops read: f itself, or the decoded arrays of
 // the last build when f is in GPF_BF16 storage.
 gpf_field float32_view(const IndexDims& dims, const IndexBuffers& b, const gpf_field& f);

@@ -95,7 +95,8 @@ def make_index(field: Field, queries: Queries, cutoff_sigma: float = 3.0,
                max_queries: Optional[int] = None, headroom: float = 1.1, max_span: int = 4,
                query_cell: Optional[float] = None, hash_bits: Optional[int] = None,
                grid: Optional[GridConfig] = None, coop_cells: int = 0,
-               ball_radius: Optional[float] = None, max_nb_pairs: int = 0) -> Index:
+               ball_radius: Optional[float] = None, max_nb_pairs: int = 0,
+               split_items: Optional[int] = None) -> Index:
     """An index planned for (field, queries). With max_pairs=None the pair
     capacity comes from a trial build (gpf_index_stats) times `headroom`
     (room for the pairs to grow while the parameters are optimised)."""
@@ -110,6 +111,8 @@ def make_index(field: Field, queries: Queries, cutoff_sigma: float = 3.0,
     if ball_radius is not None:
         grid.ball_radius = float(ball_radius)
     grid.max_nb_pairs = int(max_nb_pairs)
+    if split_items is not None:
+        grid.split_items = int(split_items)
     grid.max_gaussians = max_gaussians if max_gaussians is not None else max(field.n, 1)
     grid.max_queries = max_queries if max_queries is not None else max(queries.m, 1)
     brute = brute_force or math.isinf(cutoff_sigma)
@@ -156,19 +159,22 @@ def time_step(index: Index, field: Field, queries: Queries, mode: int = 0, r_max
 def autotune(field: Field, queries: Queries, cutoff_sigma: float = 3.0, mode: int = 0,
              r_max: float = 0.02, query_cells: Optional[Sequence[float]] = None,
              max_spans: Sequence[int] = (3, 4, 6), coop_options: Sequence[int] = (2, 4, 8),
-             repeats: int = 3, headroom: float = 1.25, backward: bool = True):
+             repeats: int = 3, headroom: float = 1.25, backward: bool = True,
+             split_options: Sequence[int] = (0, 4096, 16384)):
     """Chooses the grid geometry and the forward tile shape for this field
     and batch of hit points by timing build + forward + backward, one knob at
     a time: the query cell size (the hit-point grid), then the largest span of
     a Gaussian's box in cells of its level (the cell size of every level),
-    then the cooperative-mode threshold of the forward's 32-point tiles.
+    then the cooperative-mode threshold of the forward's 32-point tiles,
+    then the work above which a tile is split over several units (0: never).
     Returns (best GridConfig, report), report = [(knobs, ms), ...] in the
     order tried. Results are independent of the choice; only speed differs.
     backward=False times build + forward only (a query without gradient,
     such as the GPF_DISK_KDE gather)."""
     if query_cells is None:
         query_cells = (0.01, 0.02, 0.04, 0.08)
-    best = {"query_cell": 0.02, "max_span": 4, "coop_cells": 4}
+    best = {"query_cell": 0.02, "max_span": 4, "coop_cells": 4,
+            "split_items": split_options[0]}    # the first option while the others are tuned
     report = []
     cache = {}
 
@@ -177,7 +183,7 @@ def autotune(field: Field, queries: Queries, cutoff_sigma: float = 3.0, mode: in
         if key not in cache:
             idx = make_index(field, queries, cutoff_sigma=cutoff_sigma, headroom=headroom,
                              query_cell=knobs["query_cell"], max_span=knobs["max_span"],
-                             coop_cells=knobs["coop_cells"])
+                             coop_cells=knobs["coop_cells"], split_items=knobs["split_items"])
             ms = time_step(idx, field, queries, mode, r_max, repeats, backward)
             cache[key] = (ms, idx.grid)
             report.append((dict(knobs), ms))
@@ -186,7 +192,7 @@ def autotune(field: Field, queries: Queries, cutoff_sigma: float = 3.0, mode: in
         return cache[key][0]
 
     for name, options in (("query_cell", query_cells), ("max_span", max_spans),
-                          ("coop_cells", coop_options)):
+                          ("coop_cells", coop_options), ("split_items", split_options)):
         scores = {}
         for v in options:
             knobs = dict(best, **{name: v})

@@ -237,3 +237,36 @@ def test_mismatched_inputs_are_refused(gpf):
     with pytest.raises(gpf.GPFError, match="INVALID_ARG"):
         gpf.gpf_radiance_fwd(idx, field, queries, mode=7)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("mode", [oracle.GPF_SUM, oracle.GPF_NORMALIZED])
+def test_split_tiles_equal_unsplit_and_the_oracle(gpf, mode):
+    """Forward load balancing: tiles whose estimated work exceeds split_items
+    run as up to GPF_MAX_TILE_PARTS units over disjoint chunks of their
+    lists, summed in part order. Same pairs as the unsplit forward (pair
+    counts equal), sums equal up to their order, parity with the oracle, and
+    bitwise reproducible."""
+    import torch
+    from paper_2512_12459_gb300.setup_index import make_index
+    fnp, qnp = _caustic(40000, seed=15, w=160, h=128)
+    field, queries = gpf.Field.from_numpy(fnp), gpf.Queries.from_numpy(qnp)
+    outs = {}
+    for split in (0, 64, 512):
+        idx = make_index(field, queries, query_cell=0.05, split_items=split)
+        idx.build(field, queries)
+        o, z = gpf.gpf_radiance_fwd(idx, field, queries, mode, r_max=0.02)
+        o2, _ = gpf.gpf_radiance_fwd(idx, field, queries, mode, r_max=0.02)
+        torch.cuda.synchronize()
+        assert torch.equal(o, o2)
+        outs[split] = (o.cpu().numpy().astype(np.float64), z.cpu().numpy().astype(np.float64),
+                       gpf.gpf_count_pairs(idx, field, queries))
+    base_o, base_z, base_c = outs[0]
+    for split in (64, 512):
+        o, z, c = outs[split]
+        assert c == base_c
+        np.testing.assert_allclose(o, base_o, rtol=2e-6, atol=1e-30)
+        np.testing.assert_allclose(z, base_z, rtol=2e-6, atol=1e-30)
+    sel = sample_active(qnp, 400, seed=16)
+    ref = oracle_fwd(fnp, qnp, mode, 0.02, 3.0, sel)
+    err, zero_ok = fwd_rel_err(outs[64][0][:, sel], ref)
+    assert err < FWD_TOL and zero_ok, err

@@ -21,13 +21,13 @@ def gpf():
     return g
 
 
-def _kde(gpf, pos, flux, qnp, radius, cell):
+def _kde(gpf, pos, flux, qnp, radius, cell, split_items=0):
     import torch
     from paper_2512_12459_gb300.setup_index import make_index
     field = gpf.photon_field(torch.as_tensor(pos, dtype=torch.float32, device="cuda"),
                              torch.as_tensor(flux, dtype=torch.float32, device="cuda"), radius)
     queries = gpf.Queries.from_numpy(qnp)
-    idx = make_index(field, queries, query_cell=cell)
+    idx = make_index(field, queries, query_cell=cell, split_items=split_items)
     idx.build(field, queries)
     out, z = gpf.gpf_radiance_fwd(idx, field, queries, gpf.GPF_DISK_KDE, r_max=radius)
     torch.cuda.synchronize()
@@ -57,11 +57,12 @@ def test_lattice_counts_are_exact(gpf, R):
     np.testing.assert_allclose(out, ref["out"], rtol=2e-7, atol=0)
 
 
-@pytest.mark.parametrize("radius", [0.02, 0.05])
-def test_caustic_photon_map_matches_the_oracle(gpf, radius):
+@pytest.mark.parametrize("radius,split", [(0.02, 0), (0.05, 0), (0.02, 256)])
+def test_caustic_photon_map_matches_the_oracle(gpf, radius, split):
+    """split > 0: the dense tiles' lists split over several work units."""
     pos, flux = synth.caustic_photons(60000, seed=81)
     qnp = synth.pinhole_hitpoints((0.0, -6.0, 4.0), (0.0, 0.0, 0.5), 160, 128)
-    out, z, _ = _kde(gpf, pos.T, flux.T, qnp, radius, 0.05)
+    out, z, _ = _kde(gpf, pos.T, flux.T, qnp, radius, 0.05, split)
     from gpu_helpers import sample_active
     sel = sample_active(qnp, 500, seed=82)
     ref = oracle.disk_kde(pos.T, flux.T, qnp.x[:, sel], qnp.n[:, sel], qnp.wo[:, sel], radius,
