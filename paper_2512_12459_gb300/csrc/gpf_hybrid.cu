@@ -15,10 +15,13 @@
 //     staged in shared memory and every lane tests and sums them for its own
 //     hit point (a tile whose grown box meets more than kMaxTileCells cells
 //     walks the 3 x 3 x 3 cells around each hit point lane by lane instead);
-//   * kNN: a lane whose ball holds fewer than k_min Gaussians searches rings
-//     of centre cells around its own cell for the k_min nearest means (ring R
-//     can be closed once the k-th distance is at most R cells), then sums
-//     those instead.
+//   * kNN: the hit points whose ball holds fewer than k_min Gaussians take
+//     the k_min nearest means instead, searched by the whole warp one centre
+//     cell of such points at a time: rings of cells around that cell, each
+//     ring's cells spread over the lanes and their listed means 32 at a time,
+//     every point keeping its own sorted list in shared memory; a cell beyond
+//     every point's k-th distance is skipped, and a point is settled once its
+//     k-th distance is within the searched box.
 // The same selection serves the backward (Sec. 4.2, Differentiable
 // Accumulation, with N(x) held fixed): a counting pass writes each hit
 // point's number of selected Gaussians, their exclusive scan gives each
@@ -28,6 +31,7 @@
 // pairs, and so the backward's sums, do not depend on thread timing.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <limits.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -162,85 +166,251 @@ __device__ void lane_ball(const HybArgs& a, float px, float py, float pz, float 
       }
 }
 
-// The k_min nearest means by rings of centre cells around the lane's cell;
-// then the sums over them (or their pairs from offset pos). Returns how many
-// were found (k_min unless the field is smaller or the rings run out).
+// Floats as unsigned keys of the same order (and back), for warp min / max.
+__device__ __forceinline__ uint32_t ord_f(float v) {
+  const uint32_t u = __float_as_uint(v);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unord_f(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// Cell i of ring R around centre cell (gx, gy, gz): the cells at Chebyshev
+// distance R, numbered as the two z faces (w x w each, w = 2R + 1, row by
+// row), then the 8R cells around the square of each slice between them.
+__device__ __forceinline__ void ring_cell(int R, int i, int gx, int gy, int gz, int& x, int& y,
+                                          int& z) {
+  if (R == 0) {
+    x = gx; y = gy; z = gz;
+    return;
+  }
+  const int w = 2 * R + 1, face = w * w;
+  if (i < 2 * face) {
+    z = i < face ? gz - R : gz + R;
+    const int j = i < face ? i : i - face;
+    x = gx - R + j % w;
+    y = gy - R + j / w;
+    return;
+  }
+  const int j = i - 2 * face, per = 8 * R;
+  z = gz - R + 1 + j / per;
+  const int p = j % per, side = p / (2 * R), t = p % (2 * R);
+  if (side == 0) { x = gx - R + t; y = gy - R; }
+  else if (side == 1) { x = gx + R; y = gy - R + t; }
+  else if (side == 2) { x = gx + R - t; y = gy + R; }
+  else { x = gx - R; y = gy + R - t; }
+}
+
+// Distance along one axis from [lo, hi] (points) to the cell spanning finest
+// cells [c_lo, c_hi) from the origin o, grown by half a finest cell.
+__device__ __forceinline__ float cell_gap(float o, float cell0, int c_lo, int c_hi, float lo,
+                                          float hi) {
+  const float a = o + ((float)c_lo - 0.5f) * cell0;
+  const float b = o + ((float)c_hi + 0.5f) * cell0;
+  return fmaxf(fmaxf(a - hi, lo - b), 0.0f);
+}
+
+// A warp's kNN lists in shared memory: entry i of lane l at d[i][l], g[i][l].
+struct KnnList {
+  float (*d)[kWarp];
+  uint32_t (*g)[kWarp];
+};
+
+// The k_min nearest means of the tile's points that need them (need: the
+// ball held fewer), searched by the whole warp together, one centre cell of
+// needing points at a time: the points of a cell have the same rings of
+// cells around them, which are now read once for all of them instead of
+// once per point. Ring 0 is the cell itself, ring R the cells at Chebyshev
+// distance R from it; the lanes share a ring's rows (a row of cells along
+// x; away from the ring's outer faces only its two end cells belong to the
+// ring), each lane walking its rows' entries, and every round the warp
+// stages one mean per lane in shared memory, where each needing lane of the
+// cell offers all of them to its own sorted list of the nearest (squared
+// distance, then index). A point is settled once it holds k_min means and
+// the k-th is no farther than the searched box's nearest face with cells
+// beyond it (every other mean lies beyond that face); a cell is done when
+// all its points are settled, or after kMaxRing rings. Then each needing
+// lane sums its nearest (or writes their pairs from offset pos); returns
+// how many it found.
 template <int C, bool PSI, int MODE>
-__device__ int lane_knn(const HybArgs& a, float px, float py, float pz, float (&L)[C],
-                        float& Z, uint32_t pos, int64_t k_pos) {
+__device__ int warp_knn(const HybArgs& a, bool need, float px, float py, float pz,
+                        float (&L)[C], float& Z, uint32_t pos, int64_t k_pos,
+                        float4* s_cand, KnnList s_list) {
   constexpr int RS = rec_stride(C);
   const Grid& G = a.grid;
   const int Lb = G.blevel;
   const int k = a.k_min;
-  float kd[GPF_MAX_KMIN];
-  uint32_t kg[GPF_MAX_KMIN];
+  const int lane = threadIdx.x & 31;
+  uint32_t todo = __ballot_sync(kFullMask, need);
+  if (todo == 0u) return 0;
+  float* kd = s_list.d[0] + lane;     // this lane's sorted list: entry i at [i * kWarp]
+  uint32_t* kg = s_list.g[0] + lane;
+  float thr_d = INFINITY;
+  uint32_t thr_g = 0xffffffffu;
   int found = 0;
+  // the point in units of the finest cell (the cell index before flooring),
+  // and its centre cell
+  const float tx = __fmul_rn(__fsub_rn(px, G.ox), G.inv_cell0);
+  const float ty = __fmul_rn(__fsub_rn(py, G.oy), G.inv_cell0);
+  const float tz = __fmul_rn(__fsub_rn(pz, G.oz), G.inv_cell0);
   const int hx = (int)(coord0(px, G.ox, G.inv_cell0, G.max0x) >> Lb);
   const int hy = (int)(coord0(py, G.oy, G.inv_cell0, G.max0y) >> Lb);
   const int hz = (int)(coord0(pz, G.oz, G.inv_cell0, G.max0z) >> Lb);
   const int mx = (int)(G.max0x >> Lb), my = (int)(G.max0y >> Lb), mz = (int)(G.max0z >> Lb);
-  const int rmax = max(max(max(hx, mx - hx), max(hy, my - hy)), max(hz, mz - hz));
-  const float cell = G.cell0 * (float)(1u << Lb);
-  for (int R = 0; R <= min(rmax, kMaxRing); ++R) {
-    // the cells of the shell max(|dx|, |dy|, |dz|) = R only, O(R^2) of them:
-    // whole squares at dz = +-R; in between, whole rows at dy = +-R and the
-    // two end cells dx = +-R of every other row
-    for (int dz = -R; dz <= R; ++dz)
-      for (int dy = -R; dy <= R; ++dy) {
-        const bool full = dz == -R || dz == R || dy == -R || dy == R;
-        const int dx_step = full || R == 0 ? 1 : 2 * R;
-        for (int dx = -R; dx <= R; dx += dx_step) {
-          const int cx = hx + dx, cy = hy + dy, cz = hz + dz;
-          if (cx < 0 || cy < 0 || cz < 0 || cx > mx || cy > my || cz > mz) continue;
-          const CellHash h = cell_hash(G, Lb, cx, cy, cz, kCentreSalt);
-          const uint2 rg = __ldg(a.brange + h.bucket);
-          for (uint32_t e = rg.x; e < rg.y; ++e) {
-            const uint32_t v = __ldg(a.gval + e);
-            if ((v & ~G.id_mask) != h.tag) continue;
-            const uint32_t g = v & G.id_mask;
-            float rr[4];
-            const float4 t = __ldg(reinterpret_cast<const float4*>(a.rec + (int64_t)g * RS));
-            rr[0] = t.x; rr[1] = t.y; rr[2] = t.z; rr[3] = t.w;
-            if (!in_centre_cell(G, rr, cx, cy, cz)) continue;
-            const float d2 = mean_d2(rr, px, py, pz);
-            // insert (d2, g) into the sorted list of the k nearest (ties: smaller id)
-            if (found == k && !(d2 < kd[k - 1] || (d2 == kd[k - 1] && g < kg[k - 1]))) continue;
-            int pos = found < k ? found++ : k - 1;
-            while (pos > 0 && (kd[pos - 1] > d2 || (kd[pos - 1] == d2 && kg[pos - 1] > g))) {
-              kd[pos] = kd[pos - 1];
-              kg[pos] = kg[pos - 1];
-              --pos;
+  while (todo) {
+    const int leader = __ffs(todo) - 1;
+    const int gx = __shfl_sync(kFullMask, hx, leader);
+    const int gy = __shfl_sync(kFullMask, hy, leader);
+    const int gz = __shfl_sync(kFullMask, hz, leader);
+    const bool mine = need && hx == gx && hy == gy && hz == gz;
+    todo &= ~__ballot_sync(kFullMask, mine);
+    // the box of the cell's needing points
+    const float bx0 = unord_f(__reduce_min_sync(kFullMask, mine ? ord_f(px) : 0xffffffffu));
+    const float by0 = unord_f(__reduce_min_sync(kFullMask, mine ? ord_f(py) : 0xffffffffu));
+    const float bz0 = unord_f(__reduce_min_sync(kFullMask, mine ? ord_f(pz) : 0xffffffffu));
+    const float bx1 = unord_f(__reduce_max_sync(kFullMask, mine ? ord_f(px) : 0u));
+    const float by1 = unord_f(__reduce_max_sync(kFullMask, mine ? ord_f(py) : 0u));
+    const float bz1 = unord_f(__reduce_max_sync(kFullMask, mine ? ord_f(pz) : 0u));
+    const int rmax = max(max(max(gx, mx - gx), max(gy, my - gy)), max(gz, mz - gz));
+    for (int R = 0; R <= min(rmax, kMaxRing); ++R) {
+      const int x0 = gx - R, x1 = gx + R, y0 = gy - R, y1 = gy + R, z0 = gz - R, z1 = gz + R;
+      const int w = 2 * R + 1;
+      const int n_ring = R == 0 ? 1 : 2 * w * w + (2 * R - 1) * 8 * R;
+      for (int c0 = 0; c0 < n_ring; c0 += kWarp) {
+        // one cell of the ring per lane: its entries, unless the cell lies
+        // beyond every needing point's k-th distance (box grown by half a
+        // finest cell for the rounding of the cell coordinates)
+        const uint32_t tmax = __reduce_max_sync(
+            kFullMask, mine ? __float_as_uint(found == k ? thr_d : INFINITY) : 0u);
+        int cx = 0, cy = 0, cz = 0;
+        uint32_t cnt = 0, eb = 0, tag = 0;
+        if (c0 + lane < n_ring) {
+          ring_cell(R, c0 + lane, gx, gy, gz, cx, cy, cz);
+          if (cx >= 0 && cx <= mx && cy >= 0 && cy <= my && cz >= 0 && cz <= mz) {
+            const float dx = cell_gap(G.ox, G.cell0, cx << Lb, (cx + 1) << Lb, bx0, bx1);
+            const float dy = cell_gap(G.oy, G.cell0, cy << Lb, (cy + 1) << Lb, by0, by1);
+            const float dz = cell_gap(G.oz, G.cell0, cz << Lb, (cz + 1) << Lb, bz0, bz1);
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * 0.99999f;
+            if (!(d2 > __uint_as_float(tmax))) {
+              const CellHash h = cell_hash(G, Lb, (uint32_t)cx, (uint32_t)cy, (uint32_t)cz, kCentreSalt);
+              const uint2 rg = __ldg(a.brange + h.bucket);
+              eb = rg.x;
+              cnt = rg.y - rg.x;
+              tag = h.tag;
             }
-            kd[pos] = d2;
-            kg[pos] = g;
           }
         }
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < kWarp; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(kFullMask, incl, o);
+          if (lane >= o) incl += t;
+        }
+        const uint32_t total = __shfl_sync(kFullMask, incl, kWarp - 1);
+        // the cells' entries, 32 at a time: entry f of the chunk belongs to
+        // the first lane whose inclusive count exceeds f
+        for (uint32_t f0 = 0; f0 < total; f0 += kWarp) {
+          const uint32_t f = f0 + lane;
+          int o = 0;
+#pragma unroll
+          for (int st = 16; st > 0; st >>= 1)
+            if (__shfl_sync(kFullMask, incl, o + st - 1) <= f) o += st;
+          const uint32_t e = __shfl_sync(kFullMask, eb, o) + f - (__shfl_sync(kFullMask, incl, o) -
+                                                                 __shfl_sync(kFullMask, cnt, o));
+          const uint32_t otag = __shfl_sync(kFullMask, tag, o);
+          const int ox = __shfl_sync(kFullMask, cx, o);
+          const int oy = __shfl_sync(kFullMask, cy, o);
+          const int oz = __shfl_sync(kFullMask, cz, o);
+          bool have = false;
+          float4 cand = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (f < total) {
+            const uint32_t v = __ldg(a.gval + e);
+            if ((v & ~G.id_mask) == otag) {
+              const uint32_t g = v & G.id_mask;
+              const float4 t = __ldg(reinterpret_cast<const float4*>(a.rec + (int64_t)g * RS));
+              const float mu[3] = {t.x, t.y, t.z};
+              if (in_centre_cell(G, mu, (uint32_t)ox, (uint32_t)oy, (uint32_t)oz)) {
+                cand = make_float4(t.x, t.y, t.z, __uint_as_float(g));
+                have = true;
+              }
+            }
+          }
+          const uint32_t hm = __ballot_sync(kFullMask, have);
+          if (hm == 0u) continue;
+          if (have) s_cand[__popc(hm & lanemask_lt())] = cand;
+          __syncwarp();
+          if (mine) {
+            const int nc = __popc(hm);
+            for (int s = 0; s < nc; ++s) {
+              const float4 c4 = s_cand[s];
+              const uint32_t g = __float_as_uint(c4.w);
+              const float ddx = px - c4.x, ddy = py - c4.y, ddz = pz - c4.z;
+              const float d2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+              if (!(d2 < thr_d || (d2 == thr_d && g < thr_g))) continue;
+              // insertion: the larger entries move up one slot (the k-th drops out)
+              int j = found < k ? found : k - 1;
+              for (; j > 0; --j) {
+                const float pd = kd[(j - 1) * kWarp];
+                const uint32_t pg = kg[(j - 1) * kWarp];
+                if (pd < d2 || (pd == d2 && pg < g)) break;
+                kd[j * kWarp] = pd;
+                kg[j * kWarp] = pg;
+              }
+              kd[j * kWarp] = d2;
+              kg[j * kWarp] = g;
+              if (found < k) ++found;
+              if (found == k) {
+                thr_d = kd[(k - 1) * kWarp];
+                thr_g = kg[(k - 1) * kWarp];
+              }
+            }
+          }
+          __syncwarp();
+        }
       }
-    // every mean in rings beyond R lies at least R cells away
-    const float reach = (float)R * cell;
-    if (found == k && kd[k - 1] <= reach * reach) break;
+      // the point's distance to the box's faces that have cells beyond them,
+      // in finest cells; half a cell less covers the rounding of the cell
+      // coordinates (below 2^-3 cells each at 2^20 cells)
+      bool settled = true;
+      if (mine) {
+        float gap = INFINITY;
+        if (x0 > 0) gap = fminf(gap, tx - (float)(x0 << Lb));
+        if (x1 < mx) gap = fminf(gap, (float)((x1 + 1) << Lb) - tx);
+        if (y0 > 0) gap = fminf(gap, ty - (float)(y0 << Lb));
+        if (y1 < my) gap = fminf(gap, (float)((y1 + 1) << Lb) - ty);
+        if (z0 > 0) gap = fminf(gap, tz - (float)(z0 << Lb));
+        if (z1 < mz) gap = fminf(gap, (float)((z1 + 1) << Lb) - tz);
+        const float reach = fmaxf(gap - 0.5f, 0.0f) * G.cell0 * 0.999999f;
+        settled = found == k && thr_d <= reach * reach;
+      }
+      if (__all_sync(kFullMask, settled)) break;
+    }
   }
+  if (!need) return 0;
   for (int i = 0; i < found; ++i) {
     if (MODE == kHybSums) {
       float rr[RS];
-      hyb_load_rec<RS>(a.rec, kg[i], rr);
+      hyb_load_rec<RS>(a.rec, kg[i * kWarp], rr);
       const float w = hyb_weight<PSI>(rr, px, py, pz, a);
 #pragma unroll
       for (int c = 0; c < C; ++c) L[c] = fmaf(w, rr[13 + c], L[c]);
       Z += w;
     } else if (MODE == kHybEmit) {
-      emit_pair(a, pos + (uint32_t)i, kg[i], k_pos);
+      emit_pair(a, pos + (uint32_t)i, kg[i * kWarp], k_pos);
     }
   }
   return found;
 }
 
 template <int C, bool PSI, int MODE>
-__global__ void __launch_bounds__(kHybThreads)
+__global__ void __launch_bounds__(kHybThreads, 6)
 hybrid_fwd_kernel(HybArgs a) {
   constexpr int RS = rec_stride(C);
   __shared__ __align__(16) float s_rec[kHybWarps][kWarp * RS];
   __shared__ uint32_t s_gid[kHybWarps][kWarp];
+  __shared__ float4 s_cand[kHybWarps][kWarp];     // the kNN search's staged means
+  __shared__ float s_kd[kHybWarps][GPF_MAX_KMIN][kWarp];     // and sorted lists
+  __shared__ uint32_t s_kg[kHybWarps][GPF_MAX_KMIN][kWarp];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   if (index_unusable(a.header)) return;
   if (MODE == kHybEmit && (int64_t)a.header->nb_pairs > a.nb_max) {
@@ -359,11 +529,16 @@ hybrid_fwd_kernel(HybArgs a) {
     // sparse neighbourhoods: the k_min nearest instead (in the emit pass they
     // take the slots the ball's pairs were written to: there are at least as
     // many of them, min(k_min, N) > cnt)
-    if (active && a.n > 0 && cnt < a.k_min) {
+    const bool need = active && a.n > 0 && cnt < a.k_min;
+    if (need) {
 #pragma unroll
       for (int c = 0; c < C; ++c) L[c] = 0.0f;
       Z = 0.0f;
-      cnt = lane_knn<C, PSI, MODE>(a, px, py, pz, L, Z, pos, k);
+    }
+    if (a.n > 0) {
+      const int nk = warp_knn<C, PSI, MODE>(a, need, px, py, pz, L, Z, pos, k, s_cand[wib],
+                                              KnnList{s_kd[wib], s_kg[wib]});
+      if (need) cnt = nk;
     }
     if (MODE == kHybCount && active) a.nbcnt[k] = (uint32_t)cnt;
     if (MODE == kHybSums && active) {
