@@ -258,7 +258,9 @@ typedef struct gpf_index_stats_t {
   uint32_t level_mask;   /* bit L set when some Gaussian lives on level L    */
   uint32_t flags;        /* GPF_FLAG_* bits (0 = usable)                     */
   int32_t overflow;      /* 1 if n_pairs exceeded max_pairs                  */
-  int32_t reserved;
+  int32_t n_hybrid_units; /* work units of the tiles the last GPF_NB_BALL_KNN
+                            forward split (tiles whose ball boxes list more
+                            than 512 centre entries; 0: none split)          */
 } gpf_index_stats_t;
 
 /* Gradients, each [rows, N] float32, device pointers owned by the caller. */

@@ -300,7 +300,8 @@ class Index:
         status = self._lib.gpf_index_stats(self._h, ctypes.byref(st), _stream(stream))
         out = {"n_pairs": st.n_pairs, "n_active": st.n_active, "n_live": st.n_live,
                "n_small": st.n_small, "n_huge": st.n_huge, "n_split": st.n_split,
-               "level_mask": st.level_mask, "flags": st.flags, "overflow": bool(st.overflow)}
+               "level_mask": st.level_mask, "flags": st.flags, "overflow": bool(st.overflow),
+               "n_hybrid_units": st.n_hybrid_units}
         flag_status = (_abi.GPF_ERR_CAPACITY, _abi.GPF_ERR_TIMEOUT, _abi.GPF_ERR_NONFINITE)
         if status != _abi.GPF_OK and (raise_on_flags or status not in flag_status):
             check(status, "gpf_index_stats")

@@ -125,6 +125,17 @@ size_t layout(const gpf_index* ix, char* base, IndexBuffers* b) {
     t.xsum = reinterpret_cast<float*>(
         take(sizeof(float) * (size_t)GPF_MAX_SPLIT_UNITS * (d.channels + 1) * kWarp));
   }
+  if (d.grid.blevel >= 0) {
+    const int64_t tiles = (M + kWarp - 1) / kWarp;
+    t.cocc = reinterpret_cast<uint32_t*>(
+        take(sizeof(uint32_t) * (((size_t)d.grid.cdx * d.grid.cdy * d.grid.cdz + 31) / 32)));
+    t.hparts = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (tiles + 1)));
+    t.hoff = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (tiles + 1)));
+    t.hitems = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (tiles + 1)));
+    t.hunit = reinterpret_cast<uint4*>(take(sizeof(uint4) * GPF_MAX_SPLIT_UNITS));
+    t.hsum = reinterpret_cast<float*>(
+        take(sizeof(float) * (size_t)GPF_MAX_SPLIT_UNITS * (d.channels + 2) * kWarp));
+  }
   if (d.nb_max > 0) {
     for (int k = 0; k < 2; ++k) {
       t.nbkey[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * d.nb_max));
@@ -342,6 +353,19 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
     d.grid.id_bits = ib;
     d.grid.id_mask = (uint32_t)((uint64_t(1) << ib) - 1);
   }
+  if (d.grid.blevel >= 0) {
+    // centre occupancy: cells of at least 4 x 4 x 4 centre cells, at most 2^20 bits
+    int sh = d.grid.blevel + 2;
+    auto n_cells = [&](int k) {
+      return (uint64_t)((d.grid.max0x >> k) + 1) * ((d.grid.max0y >> k) + 1) *
+             ((d.grid.max0z >> k) + 1);
+    };
+    while (sh < kCoordBits && n_cells(sh) > (1u << 20)) ++sh;
+    d.grid.cshift = sh;
+    d.grid.cdx = (d.grid.max0x >> sh) + 1;
+    d.grid.cdy = (d.grid.max0y >> sh) + 1;
+    d.grid.cdz = (d.grid.max0z >> sh) + 1;
+  }
   d.grid.dx = cfg->dims[0];
   d.grid.dy = cfg->dims[1];
   d.grid.dz = cfg->dims[2];
@@ -425,6 +449,7 @@ gpf_status gpf_index_stats(const gpf_index* index, gpf_index_stats_t* stats, gpf
   stats->flags = (h.overflow ? GPF_FLAG_CAPACITY : 0u) | (h.stalled ? GPF_FLAG_TIMEOUT : 0u) |
                  (h.nonfinite ? GPF_FLAG_NONFINITE : 0u);
   stats->overflow = (int32_t)h.overflow;
+  stats->n_hybrid_units = (int32_t)h.n_hunits;
   if (h.stalled)
     return fail(GPF_ERR_TIMEOUT, "a bounded wait of the index build's sort gave up");
   if (h.nonfinite)

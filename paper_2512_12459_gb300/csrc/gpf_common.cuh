@@ -36,7 +36,8 @@ struct DeviceHeader {
   uint32_t nonfinite;    // 1 if a Gaussian parameter or an active hit point is not finite
   uint32_t nb_pairs;     // (hit point, Gaussian) pairs of the last hybrid backward
   uint32_t n_xunits;     // work units of the split forward tiles (<= GPF_MAX_SPLIT_UNITS)
-  uint32_t pad[49];
+  uint32_t n_hunits;     // work units of the split hybrid forward tiles (same limit)
+  uint32_t pad[48];
 };
 static_assert(sizeof(DeviceHeader) == 256, "header is one 256-byte block");
 
@@ -142,7 +143,17 @@ struct Grid {
   int obits;               // bits of an order key (cell key and 2 class bits)
   int coop;                // forward: cooperative mode up to this many cells
   int blevel;              // centre level of the ball query (-1: no centre entries)
+  int cshift;              // level of the centre occupancy bits (>= blevel + 2)
+  uint32_t cdx, cdy, cdz;  // cells per axis on that level
 };
+
+// Bit of the centre occupancy map (one bit per cell of level cshift, set when
+// some Gaussian mean lies in it) for the centre-level cell (cx, cy, cz).
+__device__ __forceinline__ uint32_t cocc_bit(const Grid& g, uint32_t cx, uint32_t cy,
+                                             uint32_t cz) {
+  const int s = g.cshift - g.blevel;
+  return ((cz >> s) * g.cdy + (cy >> s)) * g.cdx + (cx >> s);
+}
 
 // Level-0 cell coordinate of v along one axis: floor((v - o) / c0) in float32,
 // clamped. Correctly rounded float ops and floor are monotone in v, so a point

@@ -627,9 +627,9 @@ __global__ void tile_cost_kernel(Grid grid, const DeviceHeader* header, const fl
 // limit are marked empty.
 __global__ void tile_units_kernel(int64_t n_tiles, uint32_t* __restrict__ tparts,
                                   const uint32_t* __restrict__ xoff, uint4* __restrict__ xunit,
-                                  DeviceHeader* header) {
+                                  uint32_t* n_units) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0) header->n_xunits = min(xoff[n_tiles], (uint32_t)GPF_MAX_SPLIT_UNITS);
+  if (t == 0) *n_units = min(xoff[n_tiles], (uint32_t)GPF_MAX_SPLIT_UNITS);
   if (t >= n_tiles) return;
   const uint32_t parts = tparts[t];
   if (parts <= 1) return;
@@ -642,19 +642,24 @@ __global__ void tile_units_kernel(int64_t n_tiles, uint32_t* __restrict__ tparts
 
 }  // namespace
 
+cudaError_t launch_split_units(int64_t n_tiles, uint32_t* tparts, uint32_t* xoff, uint4* xunit,
+                               uint32_t* n_units, void* scan_ws, cudaStream_t stream) {
+  cudaError_t e = exclusive_scan_u32(xoff, xoff, n_tiles + 1, nullptr, scan_ws, stream);
+  if (e != cudaSuccess) return e;
+  tile_units_kernel<<<(unsigned)((n_tiles + 256) / 256), 256, 0, stream>>>(n_tiles, tparts, xoff,
+                                                                           xunit, n_units);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tile_split(const IndexDims& d, const IndexBuffers& b, const gpf_queries& q,
                               cudaStream_t stream) {
   const int64_t n_tiles = (q.m + kWarp - 1) / kWarp;
-  uint32_t* xoff = b.xoff;
   tile_cost_kernel<<<(unsigned)((n_tiles * 8 + 255) / 256), 256, 0, stream>>>(
-      d.grid, b.header, q.x, b.qval[b.qsorted], q.m, b.brange, d.split_items, b.tparts, xoff);
+      d.grid, b.header, q.x, b.qval[b.qsorted], q.m, b.brange, d.split_items, b.tparts, b.xoff);
   note_launches(1);
-  cudaError_t e = exclusive_scan_u32(xoff, xoff, n_tiles + 1, nullptr, b.scan_ws, stream);
-  if (e != cudaSuccess) return e;
-  tile_units_kernel<<<(unsigned)((n_tiles + 256) / 256), 256, 0, stream>>>(
-      n_tiles, b.tparts, xoff, b.xunit, b.header);
-  note_launches(1);
-  return cudaGetLastError();
+  return launch_split_units(n_tiles, b.tparts, b.xoff, b.xunit, &b.header->n_xunits, b.scan_ws,
+                            stream);
 }
 
 cudaError_t launch_forward(const IndexDims& d, const IndexBuffers& b, const gpf_queries& q,

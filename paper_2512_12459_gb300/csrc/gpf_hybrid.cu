@@ -49,6 +49,13 @@ constexpr int kMaxRing = 64;         // kNN rings searched at most (then: what w
 // What a pass of the selection produces: the forward's sums, each hit
 // point's number of selected pairs, or the pairs themselves.
 constexpr int kHybSums = 0, kHybCount = 1, kHybEmit = 2;
+// The phases of a split forward (sums): whole tiles only; the parts of the
+// split tiles and the whole unsplit tiles; the split tiles' finish (their
+// parts added in part order, then the kNN and the output as for a whole tile).
+constexpr int kHybWhole = 0, kHybSplitParts = 1, kHybSplitFinish = 2;
+// listed centre-cell entries of a tile's grown box above which the tile is
+// split, and the entries each part takes (up to GPF_MAX_TILE_PARTS parts)
+constexpr uint32_t kHybSplitEntries = 512;
 
 struct HybArgs {
   Grid grid;
@@ -60,6 +67,7 @@ struct HybArgs {
   const float* rec;
   const uint2* brange;
   const uint32_t* gval;
+  const uint32_t* cocc;    // centre occupancy bits (Grid::cshift cells)
   int mode;
   float r, r2, inv_rr;     // falloff radius psi
   float eps;
@@ -73,6 +81,11 @@ struct HybArgs {
   uint32_t* nbkey;         // emit pass: Gaussian ids of the pairs
   uint32_t* nbval;         // emit pass: hit point positions of the pairs
   int64_t nb_max;          // capacity of nbkey / nbval
+  int phase;               // kHybWhole, kHybSplitParts or kHybSplitFinish
+  const uint32_t* hparts;  // split forward: parts of each tile
+  const uint32_t* hitems;  // listed entries of each tile's box
+  const uint4* hunit;      // (tile, part, parts, valid) of each unit
+  float* hsum;             // [unit][C + 2][32] partial L, Z, count
 };
 
 // Pair j of hit point position k (emit pass): written when it fits.
@@ -175,30 +188,19 @@ __device__ __forceinline__ float unord_f(uint32_t u) {
   return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
-// Cell i of ring R around centre cell (gx, gy, gz): the cells at Chebyshev
-// distance R, numbered as the two z faces (w x w each, w = 2R + 1, row by
-// row), then the 8R cells around the square of each slice between them.
-__device__ __forceinline__ void ring_cell(int R, int i, int gx, int gy, int gz, int& x, int& y,
-                                          int& z) {
-  if (R == 0) {
-    x = gx; y = gy; z = gz;
-    return;
-  }
-  const int w = 2 * R + 1, face = w * w;
-  if (i < 2 * face) {
-    z = i < face ? gz - R : gz + R;
-    const int j = i < face ? i : i - face;
-    x = gx - R + j % w;
-    y = gy - R + j / w;
-    return;
-  }
-  const int j = i - 2 * face, per = 8 * R;
-  z = gz - R + 1 + j / per;
-  const int p = j % per, side = p / (2 * R), t = p % (2 * R);
-  if (side == 0) { x = gx - R + t; y = gy - R; }
-  else if (side == 1) { x = gx + R; y = gy - R + t; }
-  else if (side == 2) { x = gx + R - t; y = gy + R; }
-  else { x = gx - R; y = gy + R - t; }
+// Cell j of the border of the rectangle [x0, x1] x [y0, y1] (both sides at
+// least 3 cells): along y0, up x1, back along y1, down x0.
+__device__ __forceinline__ void slice_border_cell(int j, int x0, int y0, int x1, int y1, int& x,
+                                                  int& y) {
+  const int wx = x1 - x0 + 1, wy = y1 - y0 + 1;
+  if (j < wx - 1) { x = x0 + j; y = y0; return; }
+  j -= wx - 1;
+  if (j < wy - 1) { x = x1; y = y0 + j; return; }
+  j -= wy - 1;
+  if (j < wx - 1) { x = x1 - j; y = y1; return; }
+  j -= wx - 1;
+  x = x0;
+  y = y1 - j;
 }
 
 // Distance along one axis from [lo, hi] (points) to the cell spanning finest
@@ -262,8 +264,16 @@ __device__ int warp_knn(const HybArgs& a, bool need, float px, float py, float p
     const int gx = __shfl_sync(kFullMask, hx, leader);
     const int gy = __shfl_sync(kFullMask, hy, leader);
     const int gz = __shfl_sync(kFullMask, hz, leader);
-    const bool mine = need && hx == gx && hy == gy && hz == gz;
+    const bool mine = ((todo >> lane) & 1u) && abs(hx - gx) <= 1 && abs(hy - gy) <= 1 &&
+                      abs(hz - gz) <= 1;
     todo &= ~__ballot_sync(kFullMask, mine);
+    // the box of their cells (at most 3 x 3 x 3)
+    const int qx0 = __reduce_min_sync(kFullMask, mine ? hx : INT_MAX);
+    const int qy0 = __reduce_min_sync(kFullMask, mine ? hy : INT_MAX);
+    const int qz0 = __reduce_min_sync(kFullMask, mine ? hz : INT_MAX);
+    const int qx1 = __reduce_max_sync(kFullMask, mine ? hx : INT_MIN);
+    const int qy1 = __reduce_max_sync(kFullMask, mine ? hy : INT_MIN);
+    const int qz1 = __reduce_max_sync(kFullMask, mine ? hz : INT_MIN);
     // the box of the cell's needing points
     const float bx0 = unord_f(__reduce_min_sync(kFullMask, mine ? ord_f(px) : 0xffffffffu));
     const float by0 = unord_f(__reduce_min_sync(kFullMask, mine ? ord_f(py) : 0xffffffffu));
@@ -271,101 +281,133 @@ __device__ int warp_knn(const HybArgs& a, bool need, float px, float py, float p
     const float bx1 = unord_f(__reduce_max_sync(kFullMask, mine ? ord_f(px) : 0u));
     const float by1 = unord_f(__reduce_max_sync(kFullMask, mine ? ord_f(py) : 0u));
     const float bz1 = unord_f(__reduce_max_sync(kFullMask, mine ? ord_f(pz) : 0u));
-    const int rmax = max(max(max(gx, mx - gx), max(gy, my - gy)), max(gz, mz - gz));
+    const int rmax = max(max(max(qx0, mx - qx1), max(qy0, my - qy1)), max(qz0, mz - qz1));
     for (int R = 0; R <= min(rmax, kMaxRing); ++R) {
-      const int x0 = gx - R, x1 = gx + R, y0 = gy - R, y1 = gy + R, z0 = gz - R, z1 = gz + R;
-      const int w = 2 * R + 1;
-      const int n_ring = R == 0 ? 1 : 2 * w * w + (2 * R - 1) * 8 * R;
-      for (int c0 = 0; c0 < n_ring; c0 += kWarp) {
-        // one cell of the ring per lane: its entries, unless the cell lies
-        // beyond every needing point's k-th distance (box grown by half a
-        // finest cell for the rounding of the cell coordinates)
-        const uint32_t tmax = __reduce_max_sync(
-            kFullMask, mine ? __float_as_uint(found == k ? thr_d : INFINITY) : 0u);
-        int cx = 0, cy = 0, cz = 0;
-        uint32_t cnt = 0, eb = 0, tag = 0;
-        if (c0 + lane < n_ring) {
-          ring_cell(R, c0 + lane, gx, gy, gz, cx, cy, cz);
-          if (cx >= 0 && cx <= mx && cy >= 0 && cy <= my && cz >= 0 && cz <= mz) {
-            const float dx = cell_gap(G.ox, G.cell0, cx << Lb, (cx + 1) << Lb, bx0, bx1);
-            const float dy = cell_gap(G.oy, G.cell0, cy << Lb, (cy + 1) << Lb, by0, by1);
-            const float dz = cell_gap(G.oz, G.cell0, cz << Lb, (cz + 1) << Lb, bz0, bz1);
-            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * 0.99999f;
-            if (!(d2 > __uint_as_float(tmax))) {
-              const CellHash h = cell_hash(G, Lb, (uint32_t)cx, (uint32_t)cy, (uint32_t)cz, kCentreSalt);
-              const uint2 rg = __ldg(a.brange + h.bucket);
-              eb = rg.x;
-              cnt = rg.y - rg.x;
-              tag = h.tag;
-            }
-          }
+      const int x0 = qx0 - R, x1 = qx1 + R, y0 = qy0 - R, y1 = qy1 + R, z0 = qz0 - R, z1 = qz1 + R;
+      // the ring slice by slice along z: the grown box's rectangle on its
+      // two z faces (every slice for R = 0), the rectangle's border between
+      const int wx = x1 - x0 + 1, wy = y1 - y0 + 1;
+      const int per = 2 * (wx + wy) - 4;
+      const float rwx = 1.0f / (float)wx;
+      // the occupancy cells under the rectangle (clipped to the grid)
+      const int cs = G.cshift - Lb;
+      const int ux0 = max(x0, 0) >> cs, uy0 = max(y0, 0) >> cs;
+      const int unx = (min(x1, mx) >> cs) - ux0 + 1, nu = unx * ((min(y1, my) >> cs) - uy0 + 1);
+      const float runx = 1.0f / (float)unx;
+      for (int sz = max(z0, 0); sz <= min(z1, mz); ++sz) {
+        // a slice with no mean under its rectangle is skipped whole
+        uint32_t any = 0u;
+        for (int u = lane; u < nu; u += kWarp) {
+          const int uy = (int)(((float)u + 0.5f) * runx);   // u / unx, exact at these sizes
+          const uint32_t bit = ((uint32_t)(sz >> cs) * G.cdy + (uint32_t)(uy0 + uy)) * G.cdx +
+                               (uint32_t)(ux0 + u - uy * unx);
+          any |= (__ldg(a.cocc + (bit >> 5)) >> (bit & 31u)) & 1u;
         }
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int o = 1; o < kWarp; o <<= 1) {
-          const uint32_t t = __shfl_up_sync(kFullMask, incl, o);
-          if (lane >= o) incl += t;
-        }
-        const uint32_t total = __shfl_sync(kFullMask, incl, kWarp - 1);
-        // the cells' entries, 32 at a time: entry f of the chunk belongs to
-        // the first lane whose inclusive count exceeds f
-        for (uint32_t f0 = 0; f0 < total; f0 += kWarp) {
-          const uint32_t f = f0 + lane;
-          int o = 0;
-#pragma unroll
-          for (int st = 16; st > 0; st >>= 1)
-            if (__shfl_sync(kFullMask, incl, o + st - 1) <= f) o += st;
-          const uint32_t e = __shfl_sync(kFullMask, eb, o) + f - (__shfl_sync(kFullMask, incl, o) -
-                                                                 __shfl_sync(kFullMask, cnt, o));
-          const uint32_t otag = __shfl_sync(kFullMask, tag, o);
-          const int ox = __shfl_sync(kFullMask, cx, o);
-          const int oy = __shfl_sync(kFullMask, cy, o);
-          const int oz = __shfl_sync(kFullMask, cz, o);
-          bool have = false;
-          float4 cand = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (f < total) {
-            const uint32_t v = __ldg(a.gval + e);
-            if ((v & ~G.id_mask) == otag) {
-              const uint32_t g = v & G.id_mask;
-              const float4 t = __ldg(reinterpret_cast<const float4*>(a.rec + (int64_t)g * RS));
-              const float mu[3] = {t.x, t.y, t.z};
-              if (in_centre_cell(G, mu, (uint32_t)ox, (uint32_t)oy, (uint32_t)oz)) {
-                cand = make_float4(t.x, t.y, t.z, __uint_as_float(g));
-                have = true;
+        if (!__any_sync(kFullMask, any != 0u)) continue;
+        const bool face = R == 0 || sz == z0 || sz == z1;
+        const int n_slice = face ? wx * wy : per;
+        for (int c0 = 0; c0 < n_slice; c0 += kWarp) {
+          // one cell of the slice per lane: its entries, unless the cell lies
+          // beyond every needing point's k-th distance (box grown by half a
+          // finest cell for the rounding of the cell coordinates)
+          const uint32_t tmax = __reduce_max_sync(
+              kFullMask, mine ? __float_as_uint(found == k ? thr_d : INFINITY) : 0u);
+          int cx = 0, cy = 0;
+          const int cz = sz;
+          uint32_t cnt = 0, eb = 0, tag = 0;
+          const int j = c0 + lane;
+          if (j < n_slice) {
+            if (face) {
+              const int q = (int)(((float)j + 0.5f) * rwx);   // j / wx, exact at these sizes
+              cy = y0 + q;
+              cx = x0 + j - q * wx;
+            } else {
+              slice_border_cell(j, x0, y0, x1, y1, cx, cy);
+            }
+            if (cx >= 0 && cx <= mx && cy >= 0 && cy <= my) {
+              const float dx = cell_gap(G.ox, G.cell0, cx << Lb, (cx + 1) << Lb, bx0, bx1);
+              const float dy = cell_gap(G.oy, G.cell0, cy << Lb, (cy + 1) << Lb, by0, by1);
+              const float dz = cell_gap(G.oz, G.cell0, cz << Lb, (cz + 1) << Lb, bz0, bz1);
+              const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * 0.99999f;
+              const uint32_t bit = cocc_bit(G, (uint32_t)cx, (uint32_t)cy, (uint32_t)cz);
+              const bool occupied = (__ldg(a.cocc + (bit >> 5)) >> (bit & 31u)) & 1u;
+              if (!(d2 > __uint_as_float(tmax)) && occupied) {
+                const CellHash h =
+                    cell_hash(G, Lb, (uint32_t)cx, (uint32_t)cy, (uint32_t)cz, kCentreSalt);
+                const uint2 rg = __ldg(a.brange + h.bucket);
+                eb = rg.x;
+                cnt = rg.y - rg.x;
+                tag = h.tag;
               }
             }
           }
-          const uint32_t hm = __ballot_sync(kFullMask, have);
-          if (hm == 0u) continue;
-          if (have) s_cand[__popc(hm & lanemask_lt())] = cand;
-          __syncwarp();
-          if (mine) {
-            const int nc = __popc(hm);
-            for (int s = 0; s < nc; ++s) {
-              const float4 c4 = s_cand[s];
-              const uint32_t g = __float_as_uint(c4.w);
-              const float ddx = px - c4.x, ddy = py - c4.y, ddz = pz - c4.z;
-              const float d2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-              if (!(d2 < thr_d || (d2 == thr_d && g < thr_g))) continue;
-              // insertion: the larger entries move up one slot (the k-th drops out)
-              int j = found < k ? found : k - 1;
-              for (; j > 0; --j) {
-                const float pd = kd[(j - 1) * kWarp];
-                const uint32_t pg = kg[(j - 1) * kWarp];
-                if (pd < d2 || (pd == d2 && pg < g)) break;
-                kd[j * kWarp] = pd;
-                kg[j * kWarp] = pg;
-              }
-              kd[j * kWarp] = d2;
-              kg[j * kWarp] = g;
-              if (found < k) ++found;
-              if (found == k) {
-                thr_d = kd[(k - 1) * kWarp];
-                thr_g = kg[(k - 1) * kWarp];
+          uint32_t incl = cnt;
+#pragma unroll
+          for (int o = 1; o < kWarp; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFullMask, incl, o);
+            if (lane >= o) incl += t;
+          }
+          const uint32_t total = __shfl_sync(kFullMask, incl, kWarp - 1);
+          // the cells' entries, 32 at a time: entry f of the chunk belongs to
+          // the first lane whose inclusive count exceeds f
+          for (uint32_t f0 = 0; f0 < total; f0 += kWarp) {
+            const uint32_t f = f0 + lane;
+            int o = 0;
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1)
+              if (__shfl_sync(kFullMask, incl, o + st - 1) <= f) o += st;
+            const uint32_t e = __shfl_sync(kFullMask, eb, o) + f -
+                               (__shfl_sync(kFullMask, incl, o) - __shfl_sync(kFullMask, cnt, o));
+            const uint32_t otag = __shfl_sync(kFullMask, tag, o);
+            const int ox = __shfl_sync(kFullMask, cx, o);
+            const int oy = __shfl_sync(kFullMask, cy, o);
+            const int oz = __shfl_sync(kFullMask, cz, o);
+            bool have = false;
+            float4 cand = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (f < total) {
+              const uint32_t v = __ldg(a.gval + e);
+              if ((v & ~G.id_mask) == otag) {
+                const uint32_t g = v & G.id_mask;
+                const float4 t = __ldg(reinterpret_cast<const float4*>(a.rec + (int64_t)g * RS));
+                const float mu[3] = {t.x, t.y, t.z};
+                if (in_centre_cell(G, mu, (uint32_t)ox, (uint32_t)oy, (uint32_t)oz)) {
+                  cand = make_float4(t.x, t.y, t.z, __uint_as_float(g));
+                  have = true;
+                }
               }
             }
+            const uint32_t hm = __ballot_sync(kFullMask, have);
+            if (hm == 0u) continue;
+            if (have) s_cand[__popc(hm & lanemask_lt())] = cand;
+            __syncwarp();
+            if (mine) {
+              const int nc = __popc(hm);
+              for (int s = 0; s < nc; ++s) {
+                const float4 c4 = s_cand[s];
+                const uint32_t g = __float_as_uint(c4.w);
+                const float ddx = px - c4.x, ddy = py - c4.y, ddz = pz - c4.z;
+                const float d2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+                if (!(d2 < thr_d || (d2 == thr_d && g < thr_g))) continue;
+                // insertion: the larger entries move up one slot (the k-th drops out)
+                int j = found < k ? found : k - 1;
+                for (; j > 0; --j) {
+                  const float pd = kd[(j - 1) * kWarp];
+                  const uint32_t pg = kg[(j - 1) * kWarp];
+                  if (pd < d2 || (pd == d2 && pg < g)) break;
+                  kd[j * kWarp] = pd;
+                  kg[j * kWarp] = pg;
+                }
+                kd[j * kWarp] = d2;
+                kg[j * kWarp] = g;
+                if (found < k) ++found;
+                if (found == k) {
+                  thr_d = kd[(k - 1) * kWarp];
+                  thr_g = kg[(k - 1) * kWarp];
+                }
+              }
+            }
+            __syncwarp();
           }
-          __syncwarp();
         }
       }
       // the point's distance to the box's faces that have cells beyond them,
@@ -403,7 +445,7 @@ __device__ int warp_knn(const HybArgs& a, bool need, float px, float py, float p
 }
 
 template <int C, bool PSI, int MODE>
-__global__ void __launch_bounds__(kHybThreads, 6)
+__global__ void __launch_bounds__(kHybThreads, 4)
 hybrid_fwd_kernel(HybArgs a) {
   constexpr int RS = rec_stride(C);
   __shared__ __align__(16) float s_rec[kHybWarps][kWarp * RS];
@@ -415,7 +457,8 @@ hybrid_fwd_kernel(HybArgs a) {
   if (index_unusable(a.header)) return;
   if (MODE == kHybEmit && (int64_t)a.header->nb_pairs > a.nb_max) {
     // more pairs than room: flag it once; every later kernel leaves its outputs
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(const_cast<uint32_t*>(&a.header->overflow), 1u);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+      atomicExch(const_cast<uint32_t*>(&a.header->overflow), 1u);
     return;
   }
   const Grid& G = a.grid;
@@ -423,17 +466,42 @@ hybrid_fwd_kernel(HybArgs a) {
   const int64_t n_act = a.header->n_active;
   const int64_t n_tiles = (a.m + kWarp - 1) / kWarp;
   float* my_rec = s_rec[wib];
+  const int64_t n_units = a.phase != kHybWhole ? (int64_t)a.header->n_hunits : 0;
   for (;;) {
     __syncwarp();
-    unsigned long long tile_u = 0;
-    if (lane == 0) tile_u = atomicAdd(a.next_tile, 1ull);
-    const int64_t tile = (int64_t)__shfl_sync(kFullMask, tile_u, 0);
+    unsigned long long item_u = 0;
+    if (lane == 0) item_u = atomicAdd(a.next_tile, 1ull);
+    const int64_t item = (int64_t)__shfl_sync(kFullMask, item_u, 0);
+    // the item: a whole tile, one part of a split tile (its partial sums
+    // only), or a split tile's finish
+    int64_t tile = item;
+    uint32_t part = 0, parts = 1;
+    if (a.phase == kHybSplitParts) {
+      if (item < n_units) {
+        const uint4 u = a.hunit[item];
+        if (!u.w) continue;
+        tile = u.x;
+        part = u.y;
+        parts = u.z;
+      } else {
+        tile = item - n_units;
+        if (tile < n_tiles && a.hparts[tile] > 1) continue;
+      }
+    } else if (a.phase == kHybSplitFinish) {
+      if (item >= n_units) break;
+      const uint4 u = a.hunit[item];
+      if (!u.w || u.y != 0) continue;
+      tile = u.x;
+      parts = u.z;
+    }
     if (tile >= n_tiles) break;
+    const bool partial = a.phase == kHybSplitParts && parts > 1;
+    const bool finish = a.phase == kHybSplitFinish;
     const int64_t k = tile * kWarp + lane;
     const bool in_range = k < a.m;
     const bool active = k < n_act;
     const uint32_t q = in_range ? a.qval[k] : 0u;
-    if (MODE == kHybSums && in_range && !active) {
+    if (MODE == kHybSums && in_range && !active && !partial) {
 #pragma unroll
       for (int c = 0; c < C; ++c) a.out[(int64_t)c * a.m + q] = 0.0f;
       if (a.z) a.z[q] = 0.0f;
@@ -471,60 +539,118 @@ hybrid_fwd_kernel(HybArgs a) {
     const uint32_t cy1 = coord0(b4 + a.ball_r, G.oy, G.inv_cell0, G.max0y) >> Lb;
     const uint32_t cz1 = coord0(b5 + a.ball_r, G.oz, G.inv_cell0, G.max0z) >> Lb;
     const int64_t n_cells = (int64_t)(cx1 - cx0 + 1) * (cy1 - cy0 + 1) * (cz1 - cz0 + 1);
-    if (a.n == 0) {
+    if (finish) {
+      // the parts' sums, added in part order
+      for (uint32_t p = 0; p < parts; ++p) {
+        const float* src = a.hsum + (size_t)(item + p) * (C + 2) * kWarp + lane;
+#pragma unroll
+        for (int c = 0; c < C; ++c) L[c] += src[c * kWarp];
+        Z += src[C * kWarp];
+        cnt += __float_as_int(src[(C + 1) * kWarp]);
+      }
+    } else if (a.n == 0) {
       // no Gaussians: the build left no lists to read
     } else if (n_cells <= kMaxTileCells) {
-      for (uint32_t cz = cz0; cz <= cz1; ++cz)
-        for (uint32_t cy = cy0; cy <= cy1; ++cy)
-          for (uint32_t cx = cx0; cx <= cx1; ++cx) {
-            const CellHash h = cell_hash(G, Lb, cx, cy, cz, kCentreSalt);
-            const uint2 rg = __ldg(a.brange + h.bucket);
-            for (uint32_t e0 = rg.x; e0 < rg.y; e0 += kWarp) {
-              const uint32_t e = e0 + lane;
-              const uint32_t v = e < rg.y ? __ldg(a.gval + e) : 0u;
-              bool keep = e < rg.y && (v & ~G.id_mask) == h.tag;
-              float rr[RS];
-              if (keep) {
-                hyb_load_rec<RS>(a.rec, v & G.id_mask, rr);
-                keep = in_centre_cell(G, rr, cx, cy, cz);
-                if (keep) {
-                  // the mean's distance to the tile's box, against ball_r
-                  const float ex = fmaxf(fmaxf(b0 - rr[0], rr[0] - b3), 0.0f);
-                  const float ey = fmaxf(fmaxf(b1 - rr[1], rr[1] - b4), 0.0f);
-                  const float ez = fmaxf(fmaxf(b2 - rr[2], rr[2] - b5), 0.0f);
-                  keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= a.ball_r2;
-                }
-              }
-              const uint32_t kb = __ballot_sync(kFullMask, keep);
-              if (keep) {
-                const int slot = __popc(kb & lanemask_lt());
-                float4* dst = reinterpret_cast<float4*>(my_rec + slot * RS);
+      // the box's listed entries in cell order; a part takes its share of them
+      uint32_t u_lo = 0, u_hi = 0xffffffffu;
+      if (partial) {
+        const uint64_t items = a.hitems[tile];
+        u_lo = (uint32_t)(items * part / parts);
+        u_hi = (uint32_t)(items * (part + 1) / parts);
+      }
+      // 32 cells at a time, one per lane, then their entries 32 at a time:
+      // entry f of the chunk belongs to the first lane whose inclusive count
+      // exceeds f
+      const uint32_t nx = cx1 - cx0 + 1, ny = cy1 - cy0 + 1;
+      uint32_t off = 0;     // entries of the chunks before this one
+      for (uint32_t c0 = 0; c0 < (uint32_t)n_cells && off < u_hi; c0 += kWarp) {
+        const uint32_t ci = c0 + lane;
+        uint32_t ccx = 0, ccy = 0, ccz = 0, eb = 0, len = 0, tag = 0;
+        if (ci < (uint32_t)n_cells) {
+          ccx = cx0 + ci % nx;
+          ccy = cy0 + (ci / nx) % ny;
+          ccz = cz0 + ci / (nx * ny);
+          const CellHash h = cell_hash(G, Lb, ccx, ccy, ccz, kCentreSalt);
+          const uint2 rg = __ldg(a.brange + h.bucket);
+          eb = rg.x;
+          len = rg.y - rg.x;
+          tag = h.tag;
+        }
+        uint32_t incl = len;
 #pragma unroll
-                for (int q4 = 0; q4 < RS / 4; ++q4)
-                  dst[q4] = make_float4(rr[4 * q4], rr[4 * q4 + 1], rr[4 * q4 + 2], rr[4 * q4 + 3]);
-                s_gid[wib][slot] = v & G.id_mask;
-              }
-              __syncwarp();
-              const int nk = __popc(kb);
-              if (active)
-                for (int s = 0; s < nk; ++s) {
-                  const float* r = my_rec + s * RS;
-                  if (mean_d2(r, px, py, pz) > a.ball_r2) continue;
-                  if (MODE == kHybSums) {
-                    const float w = hyb_weight<PSI>(r, px, py, pz, a);
+        for (int o = 1; o < kWarp; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(kFullMask, incl, o);
+          if (lane >= o) incl += t;
+        }
+        const uint32_t total = __shfl_sync(kFullMask, incl, kWarp - 1);
+        const uint32_t f_lo = u_lo > off ? min(u_lo - off, total) : 0u;
+        const uint32_t f_hi = min(u_hi - off, total);
+        off += total;
+        for (uint32_t f0 = f_lo; f0 < f_hi; f0 += kWarp) {
+          const uint32_t f = f0 + lane;
+          int o = 0;
 #pragma unroll
-                    for (int c = 0; c < C; ++c) L[c] = fmaf(w, r[13 + c], L[c]);
-                    Z += w;
-                  } else if (MODE == kHybEmit) {
-                    emit_pair(a, pos + (uint32_t)cnt, s_gid[wib][s], k);
-                  }
-                  ++cnt;
-                }
-              __syncwarp();
+          for (int st = 16; st > 0; st >>= 1)
+            if (__shfl_sync(kFullMask, incl, o + st - 1) <= f) o += st;
+          const uint32_t e = __shfl_sync(kFullMask, eb, o) + f -
+                             (__shfl_sync(kFullMask, incl, o) - __shfl_sync(kFullMask, len, o));
+          const uint32_t otag = __shfl_sync(kFullMask, tag, o);
+          const uint32_t ox = __shfl_sync(kFullMask, ccx, o);
+          const uint32_t oy = __shfl_sync(kFullMask, ccy, o);
+          const uint32_t oz = __shfl_sync(kFullMask, ccz, o);
+          const uint32_t v = f < f_hi ? __ldg(a.gval + e) : 0u;
+          bool keep = f < f_hi && (v & ~G.id_mask) == otag;
+          float rr[RS];
+          if (keep) {
+            hyb_load_rec<RS>(a.rec, v & G.id_mask, rr);
+            keep = in_centre_cell(G, rr, ox, oy, oz);
+            if (keep) {
+              // the mean's distance to the tile's box, against ball_r
+              const float ex = fmaxf(fmaxf(b0 - rr[0], rr[0] - b3), 0.0f);
+              const float ey = fmaxf(fmaxf(b1 - rr[1], rr[1] - b4), 0.0f);
+              const float ez = fmaxf(fmaxf(b2 - rr[2], rr[2] - b5), 0.0f);
+              keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= a.ball_r2;
             }
           }
+          const uint32_t kb = __ballot_sync(kFullMask, keep);
+          if (kb == 0u) continue;
+          if (keep) {
+            const int slot = __popc(kb & lanemask_lt());
+            float4* dst = reinterpret_cast<float4*>(my_rec + slot * RS);
+#pragma unroll
+            for (int q4 = 0; q4 < RS / 4; ++q4)
+              dst[q4] = make_float4(rr[4 * q4], rr[4 * q4 + 1], rr[4 * q4 + 2], rr[4 * q4 + 3]);
+            s_gid[wib][slot] = v & G.id_mask;
+          }
+          __syncwarp();
+          const int nk = __popc(kb);
+          if (active)
+            for (int s = 0; s < nk; ++s) {
+              const float* r = my_rec + s * RS;
+              if (mean_d2(r, px, py, pz) > a.ball_r2) continue;
+              if (MODE == kHybSums) {
+                const float w = hyb_weight<PSI>(r, px, py, pz, a);
+#pragma unroll
+                for (int c = 0; c < C; ++c) L[c] = fmaf(w, r[13 + c], L[c]);
+                Z += w;
+              } else if (MODE == kHybEmit) {
+                emit_pair(a, pos + (uint32_t)cnt, s_gid[wib][s], k);
+              }
+              ++cnt;
+            }
+          __syncwarp();
+        }
+      }
     } else if (active) {
       lane_ball<C, PSI, MODE>(a, px, py, pz, L, Z, cnt, pos, k);
+    }
+    if (partial) {
+      float* dst = a.hsum + (size_t)item * (C + 2) * kWarp + lane;
+#pragma unroll
+      for (int c = 0; c < C; ++c) dst[c * kWarp] = L[c];
+      dst[C * kWarp] = Z;
+      dst[(C + 1) * kWarp] = __int_as_float(cnt);
+      continue;
     }
     // sparse neighbourhoods: the k_min nearest instead (in the emit pass they
     // take the slots the ball's pairs were written to: there are at least as
@@ -554,6 +680,69 @@ hybrid_fwd_kernel(HybArgs a) {
   }
 }
 
+// The split forward's plan: each tile's listed centre-cell entries in its
+// box grown by ball_r (the cells the ball sums walk, in the same order), and
+// from them its parts (1: whole); one warp per tile.
+template <int C>
+__global__ void __launch_bounds__(kHybThreads)
+hyb_cost_kernel(HybArgs a, uint32_t* __restrict__ hparts, uint32_t* __restrict__ hoff,
+                uint32_t* __restrict__ hitems) {
+  const int lane = threadIdx.x & 31;
+  const int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_tiles = (a.m + kWarp - 1) / kWarp;
+  if (tile >= n_tiles) return;
+  const Grid& G = a.grid;
+  const int Lb = G.blevel;
+  const int64_t n_act = a.header->n_active;
+  uint32_t items = 0;
+  if (!index_unusable(a.header) && tile * kWarp < n_act && a.n > 0) {
+    const int64_t k = tile * kWarp + lane;
+    const bool active = k < n_act;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    if (active) {
+      const uint32_t q = a.qval[k];
+      px = a.x[q];
+      py = a.x[a.m + q];
+      pz = a.x[2 * a.m + q];
+    }
+    float b0 = active ? px : INFINITY, b1 = active ? py : INFINITY, b2 = active ? pz : INFINITY;
+    float b3 = active ? px : -INFINITY, b4 = active ? py : -INFINITY, b5 = active ? pz : -INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      b0 = fminf(b0, __shfl_xor_sync(kFullMask, b0, o));
+      b1 = fminf(b1, __shfl_xor_sync(kFullMask, b1, o));
+      b2 = fminf(b2, __shfl_xor_sync(kFullMask, b2, o));
+      b3 = fmaxf(b3, __shfl_xor_sync(kFullMask, b3, o));
+      b4 = fmaxf(b4, __shfl_xor_sync(kFullMask, b4, o));
+      b5 = fmaxf(b5, __shfl_xor_sync(kFullMask, b5, o));
+    }
+    const uint32_t cx0 = coord0(b0 - a.ball_r, G.ox, G.inv_cell0, G.max0x) >> Lb;
+    const uint32_t cy0 = coord0(b1 - a.ball_r, G.oy, G.inv_cell0, G.max0y) >> Lb;
+    const uint32_t cz0 = coord0(b2 - a.ball_r, G.oz, G.inv_cell0, G.max0z) >> Lb;
+    const uint32_t cx1 = coord0(b3 + a.ball_r, G.ox, G.inv_cell0, G.max0x) >> Lb;
+    const uint32_t cy1 = coord0(b4 + a.ball_r, G.oy, G.inv_cell0, G.max0y) >> Lb;
+    const uint32_t cz1 = coord0(b5 + a.ball_r, G.oz, G.inv_cell0, G.max0z) >> Lb;
+    const uint32_t nx = cx1 - cx0 + 1, ny = cy1 - cy0 + 1;
+    const int64_t n_cells = (int64_t)nx * ny * (cz1 - cz0 + 1);
+    if (n_cells <= kMaxTileCells) {
+      for (uint32_t i = lane; i < (uint32_t)n_cells; i += kWarp) {
+        const uint32_t cx = cx0 + i % nx, cy = cy0 + (i / nx) % ny, cz = cz0 + i / (nx * ny);
+        const uint2 rg = __ldg(a.brange + cell_hash(G, Lb, cx, cy, cz, kCentreSalt).bucket);
+        items += rg.y - rg.x;
+      }
+      items = __reduce_add_sync(kFullMask, items);
+    }
+  }
+  if (lane == 0) {
+    uint32_t parts = 1;
+    if (items > kHybSplitEntries)
+      parts = min((items + kHybSplitEntries - 1) / kHybSplitEntries, (uint32_t)GPF_MAX_TILE_PARTS);
+    hparts[tile] = parts;
+    hoff[tile] = parts > 1 ? parts : 0u;
+    hitems[tile] = items;
+  }
+}
+
 }  // namespace
 
 namespace {
@@ -570,6 +759,7 @@ HybArgs hyb_args(const IndexDims& d, const IndexBuffers& b, const gpf_queries& q
   a.rec = b.rec;
   a.brange = b.brange;
   a.gval = b.gval[b.gsorted];
+  a.cocc = b.cocc;
   a.mode = p.mode;
   const bool psi = isfinite(p.r_max);
   a.r = psi ? p.r_max : 0.0f;
@@ -645,7 +835,35 @@ cudaError_t launch_hybrid_forward(const IndexDims& d, const IndexBuffers& b,
   a.z = z;
   cudaError_t e;
   if (ev.start && (e = cudaEventRecord(ev.start, stream)) != cudaSuccess) return e;
-  if ((e = hyb_pass<kHybSums>(a, d.channels, isfinite(p.r_max), stream)) != cudaSuccess) return e;
+  const bool psi = isfinite(p.r_max);
+  if (n > 0) {
+    // heavy tiles split into parts over their listed entries, then finished
+    const int64_t n_tiles = (q.m + kWarp - 1) / kWarp;
+    const unsigned blocks = (unsigned)((n_tiles + kHybWarps - 1) / kHybWarps);
+    switch (d.channels) {
+#define GPF_HYB_COST(CC)                                                                      \
+  case CC:                                                                                    \
+    hyb_cost_kernel<CC><<<blocks, kHybThreads, 0, stream>>>(a, b.hparts, b.hoff, b.hitems); \
+    break;
+      GPF_HYB_COST(1) GPF_HYB_COST(2) GPF_HYB_COST(3) GPF_HYB_COST(4)
+      GPF_HYB_COST(5) GPF_HYB_COST(6) GPF_HYB_COST(7) GPF_HYB_COST(8)
+#undef GPF_HYB_COST
+      default:
+        return cudaErrorInvalidValue;
+    }
+    note_launches(1);
+    if ((e = launch_split_units(n_tiles, b.hparts, b.hoff, b.hunit, &b.header->n_hunits,
+                                b.scan_ws, stream)) != cudaSuccess)
+      return e;
+    a.hparts = b.hparts;
+    a.hitems = b.hitems;
+    a.hunit = b.hunit;
+    a.hsum = b.hsum;
+    a.phase = kHybSplitParts;
+    if ((e = hyb_pass<kHybSums>(a, d.channels, psi, stream)) != cudaSuccess) return e;
+    a.phase = kHybSplitFinish;
+  }
+  if ((e = hyb_pass<kHybSums>(a, d.channels, psi, stream)) != cudaSuccess) return e;
   return ev.stop ? cudaEventRecord(ev.stop, stream) : cudaSuccess;
 }
 

@@ -87,6 +87,14 @@ struct IndexBuffers {
   uint32_t* xoff;       // [tiles_max + 1] parts of each split tile (0 otherwise), then scanned
   uint4* xunit;         // [GPF_MAX_SPLIT_UNITS] (tile, part, parts, valid) of every split unit
   float* xsum;          // [GPF_MAX_SPLIT_UNITS * (C + 1) * 32] partial sums of split units
+  // a centre level (ball_radius > 0): occupancy bits of the centre cells'
+  // coarse cells (Grid::cshift), and the hybrid forward's tile splitting
+  uint32_t* cocc;       // [cdx * cdy * cdz / 32] set: some mean lies in the cell
+  uint32_t* hparts;     // [tiles_max + 1] parts of each tile (1 = not split)
+  uint32_t* hoff;       // [tiles_max + 1] parts of each split tile (0 otherwise), then scanned
+  uint32_t* hitems;     // [tiles_max] listed entries of the centre cells of each tile's box
+  uint4* hunit;         // [GPF_MAX_SPLIT_UNITS] (tile, part, parts, valid) of every split unit
+  float* hsum;          // [GPF_MAX_SPLIT_UNITS * (C + 2) * 32] partial L, Z and count
   float* dec;           // GPF_BF16 fields: decoded float32 [(10 + C), n] (rows
                         // mean 3, quat 4, logscale 3, spectrum C; N_max room)
   void* scan_ws;
@@ -114,6 +122,12 @@ cudaError_t launch_build(const IndexDims& dims, const IndexBuffers& b, const gpf
 // Forward tile splitting (split_items > 0), after the bucket ranges exist:
 // each tile's estimated work, its parts, and the table of split units
 // (gpf_fwd.cu).
+// The unit list of split tiles: xoff (each tile's parts if split, else 0)
+// is scanned in place, tile t's units are written at xunit[xoff[t] ...], and
+// *n_units (device memory) receives their number; a tile whose units would
+// not all fit under GPF_MAX_SPLIT_UNITS gets tparts = 1 and runs unsplit.
+cudaError_t launch_split_units(int64_t n_tiles, uint32_t* tparts, uint32_t* xoff, uint4* xunit,
+                               uint32_t* n_units, void* scan_ws, cudaStream_t stream);
 cudaError_t launch_tile_split(const IndexDims& dims, const IndexBuffers& b, const gpf_queries& q,
                               cudaStream_t stream);
 // The float32 field the pair loops read: f itself, or the decoded arrays of

@@ -77,6 +77,27 @@ def test_sparse_field_falls_back_to_knn(gpf):
     assert ref["knn"].mean() > 0.9
 
 
+@pytest.mark.parametrize("mode", [oracle.GPF_NORMALIZED, oracle.GPF_SUM])
+def test_dense_tiles_are_split_and_match_the_oracle(gpf, mode):
+    """A dense caustic (30,000 photons with a 3 cm spread) seen from close
+    by: every tile's ball box lists thousands of means, so the forward splits
+    the tiles into parts over their entries and adds the parts' sums in
+    order; each hit point still sums its whole ball (or its k_min nearest at
+    the rim)."""
+    rng = np.random.default_rng(97)
+    n = 30000
+    pos = np.zeros((n, 3))
+    pos[:, :2] = rng.standard_normal((n, 2)) * 0.03
+    pos[:, 0] += 2.0                            # on the floor, clear of the sphere
+    flux = rng.exponential(1.0, (n, 3))
+    fnp = synth.field_from_photons(pos, flux, seed=97)
+    qnp = synth.pinhole_hitpoints((2.0, -0.15, 0.15), (2.0, 0.0, 0.0), 64, 48)
+    out, (idx, *_rest) = _run(gpf, fnp, qnp, mode, R, 3)
+    assert idx.stats()["n_hybrid_units"] > 0
+    sel = sample_active(qnp, 300, seed=98)
+    _check(fnp, qnp, out, mode, R, 3, sel)
+
+
 def test_hybrid_backward_needs_pair_room_and_centre_entries(gpf):
     import torch
     from paper_2512_12459_gb300.setup_index import make_index
