@@ -731,6 +731,65 @@ def run_scaling(args):
         torch.cuda.empty_cache()
         return float(np.mean(times))
 
+    def hybrid_step_ms(n, k_min):
+        # the paper's training step through its own neighbourhood: build,
+        # hybrid forward, MSE, hybrid backward (the selected pairs sorted by
+        # Gaussian), Adam; the pair room from a trial step
+        pos, flux = synth.caustic_photons(n, seed=0)
+        fnp = synth.field_from_photons(pos, flux, seed=0)
+        field = gpf.Field.from_numpy(fnp)
+        tgt = gpf.Field.from_numpy(synth.perturbed_copy(fnp, seed=1))
+        kw = dict(neighbourhood=gpf.GPF_NB_BALL_KNN, ball_r=R_MAX, k_min=k_min)
+        ti = make_index(tgt, queries, query_cell=CELL, ball_radius=R_MAX)
+        ti.build(tgt, queries)
+        target = gpf.gpf_radiance_fwd(ti, tgt, queries, gpf.GPF_NORMALIZED, r_max=R_MAX,
+                                      **kw)[0].clone()
+        del ti
+        state = gpf.AdamState.zeros_like(field)
+        grads = gpf.Field.zeros_like(field)
+        out = torch.empty((3, queries.m), device="cuda")
+        z = torch.empty((queries.m,), device="cuda")
+        gout = torch.empty_like(out)
+        cap = 64 * queries.m
+        for _ in range(3):
+            idx = make_index(field, queries, query_cell=CELL, ball_radius=R_MAX, max_nb_pairs=cap)
+
+            def step():
+                idx.build(field, queries)
+                gpf.gpf_radiance_fwd(idx, field, queries, gpf.GPF_NORMALIZED, r_max=R_MAX,
+                                     out=out, z=z, **kw)
+                gpf.gpf_mse_loss_grad(out, target, queries.valid, grad=gout)
+                gpf.gpf_radiance_bwd(idx, field, queries, gout, out, z, gpf.GPF_NORMALIZED,
+                                     r_max=R_MAX, grads=grads, **kw)
+                gpf.gpf_adam_step(field, grads, state, lr=LR, guard=idx)
+
+            step()
+            st = idx.stats()
+            if not st["overflow"]:
+                break
+            cap = int(st["n_nb_pairs"] * 1.1) + 1024
+            del idx
+            torch.cuda.empty_cache()
+        times = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step()
+            e1.record()
+            e1.synchronize()
+            if i >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+        pairs = idx.stats()["n_nb_pairs"]
+        del idx, field, state, grads, target
+        torch.cuda.empty_cache()
+        return float(np.mean(times)), pairs
+
+    step_rows = []
+    for n in (10_000, 100_000):
+        ms, pairs = hybrid_step_ms(n, 3)
+        step_rows.append({"gaussians": n, "k_min": 3, "ms_per_step": ms, "selected_pairs": pairs,
+                          "queries_per_s": n_active / ms * 1e3})
     for n in (10_000, 50_000, 100_000, 200_000):
         ms = hybrid_ms(n, 3)
         hyb_rows.append({"gaussians": n, "k_min": 3, "build_fwd_ms": ms,
@@ -747,6 +806,7 @@ def run_scaling(args):
                        "active_hit_points": n_active, "l2": "flushed between steps"},
             "rows": rows,
             "hybrid_query_rows": hyb_rows, "hybrid_k_rows": k_rows,
+            "hybrid_training_step_rows": step_rows,
             "paper_table_s1_s": {"10000": 7.230, "50000": 12.70, "100000": 16.37, "200000": 24.35},
             "paper_table_s2_s": {"1": 16.21, "3": 16.37, "5": 16.48, "10": 16.34}}
     print(json.dumps(line), flush=True)

@@ -261,6 +261,9 @@ typedef struct gpf_index_stats_t {
   int32_t n_hybrid_units; /* work units of the tiles the last GPF_NB_BALL_KNN
                             forward split (tiles whose ball boxes list more
                             than 512 centre entries; 0: none split)          */
+  int64_t n_nb_pairs;    /* (hit point, Gaussian) pairs the last GPF_NB_BALL_KNN
+                            backward selected (above max_nb_pairs: the
+                            capacity flag, and the room a rebuild needs)     */
 } gpf_index_stats_t;
 
 /* Gradients, each [rows, N] float32, device pointers owned by the caller. */

@@ -71,7 +71,8 @@ class gpf_grid_config(ctypes.Structure):
 class gpf_index_stats_t(ctypes.Structure):
     _fields_ = [("n_pairs", c_i64), ("n_active", c_i64), ("n_live", c_i64), ("n_small", c_i64),
                 ("n_huge", c_i64), ("n_split", c_i64), ("level_mask", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32), ("overflow", c_i32), ("n_hybrid_units", c_i32)]
+                ("flags", ctypes.c_uint32), ("overflow", c_i32), ("n_hybrid_units", c_i32),
+                ("n_nb_pairs", c_i64)]
 
 
 class gpf_field_grad(ctypes.Structure):

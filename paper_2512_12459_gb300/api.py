@@ -301,7 +301,7 @@ class Index:
         out = {"n_pairs": st.n_pairs, "n_active": st.n_active, "n_live": st.n_live,
                "n_small": st.n_small, "n_huge": st.n_huge, "n_split": st.n_split,
                "level_mask": st.level_mask, "flags": st.flags, "overflow": bool(st.overflow),
-               "n_hybrid_units": st.n_hybrid_units}
+               "n_hybrid_units": st.n_hybrid_units, "n_nb_pairs": st.n_nb_pairs}
         flag_status = (_abi.GPF_ERR_CAPACITY, _abi.GPF_ERR_TIMEOUT, _abi.GPF_ERR_NONFINITE)
         if status != _abi.GPF_OK and (raise_on_flags or status not in flag_status):
             check(status, "gpf_index_stats")

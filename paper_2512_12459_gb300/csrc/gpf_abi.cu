@@ -450,6 +450,7 @@ gpf_status gpf_index_stats(const gpf_index* index, gpf_index_stats_t* stats, gpf
                  (h.nonfinite ? GPF_FLAG_NONFINITE : 0u);
   stats->overflow = (int32_t)h.overflow;
   stats->n_hybrid_units = (int32_t)h.n_hunits;
+  stats->n_nb_pairs = h.nb_pairs;
   if (h.stalled)
     return fail(GPF_ERR_TIMEOUT, "a bounded wait of the index build's sort gave up");
   if (h.nonfinite)
