@@ -460,7 +460,11 @@ uint64_t gpf_launch_count(void);
  * offset, sorts the pairs by Gaussian (stable, so each Gaussian's hit points
  * stay in index order) and sums each Gaussian's pairs in one warp, without
  * atomics; the index needs max_nb_pairs at least the number of selected
- * pairs, and more sets the capacity flag.
+ * pairs, and more sets the capacity flag. When the last GPF_NB_BALL_KNN
+ * gpf_radiance_fwd on this build (and index) had the same ball_r and k_min,
+ * it has already written each hit point's number of selected pairs, and
+ * the selection runs once here instead of twice; that forward must then be
+ * ordered before this call (the same stream, or an event).
  * Errors: as gpf_radiance_fwd.
  */
 gpf_status gpf_radiance_bwd(const gpf_index *index, const gpf_field *field,

@@ -71,6 +71,14 @@ struct gpf_index {
   gpf_queries queries;
   // gpf_index_set_timing_events
   KernelEvents fwd_ev, bwd_ev;
+  // the last GPF_NB_BALL_KNN forward on this build wrote each hit point's
+  // number of selected pairs (and its split parts' ball counts) for these
+  // ball_r and k_min: a backward with the same selection need not count
+  struct {
+    bool valid;
+    float ball_r;
+    int32_t k_min;
+  } hyb_counts;
 };
 
 namespace {
@@ -421,6 +429,7 @@ gpf_status gpf_build_index(gpf_index* index, const gpf_field* field, const gpf_q
                 index->ws_bytes);
   layout(index, static_cast<char*>(workspace), &index->buf);
   index->built = false;
+  index->hyb_counts.valid = false;
   cudaError_t e = launch_build(index->dims, index->buf, *field, *queries,
                                reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "gpf_build_index");
@@ -494,13 +503,20 @@ gpf_status gpf_radiance_fwd(const gpf_index* index, const gpf_field* field,
     GPF_CHECK_PTR(out, "out");
     if (z_out && !aligned(z_out, 4)) return fail(GPF_ERR_INVALID_ARG, "z_out is not aligned");
   }
+  const bool hyb = params->neighbourhood == GPF_NB_BALL_KNN;
+  const bool counts = hyb && index->dims.nb_max > 0;
   cudaError_t e =
-      params->neighbourhood == GPF_NB_BALL_KNN
-          ? launch_hybrid_forward(index->dims, index->buf, *queries, *params, field->n, out, z_out,
-                                  index->fwd_ev, reinterpret_cast<cudaStream_t>(stream))
+      hyb ? launch_hybrid_forward(index->dims, index->buf, *queries, *params, field->n, out, z_out,
+                                  counts, index->fwd_ev, reinterpret_cast<cudaStream_t>(stream))
           : launch_forward(index->dims, index->buf, *queries, *params, field->n, out, z_out,
                            nullptr, index->fwd_ev, reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "gpf_radiance_fwd");
+  if (hyb) {
+    auto& hc = const_cast<gpf_index*>(index)->hyb_counts;
+    hc.valid = counts;
+    hc.ball_r = params->ball_r;
+    hc.k_min = params->k_min;
+  }
   return GPF_OK;
 }
 
@@ -570,10 +586,15 @@ gpf_status gpf_radiance_bwd(const gpf_index* index, const gpf_field* field,
       GPF_CHECK_PTR(z, "z");
     }
   }
+  auto& hc = const_cast<gpf_index*>(index)->hyb_counts;
+  const bool counted = params->neighbourhood == GPF_NB_BALL_KNN && hc.valid &&
+                       hc.ball_r == params->ball_r && hc.k_min == params->k_min;
   cudaError_t e = launch_backward(index->dims, index->buf,
                                   float32_view(index->dims, index->buf, *field), *queries, *params,
-                                  grad_out, out,
-                                  z, *grads, index->bwd_ev, reinterpret_cast<cudaStream_t>(stream));
+                                  grad_out, out, z, *grads, counted, index->bwd_ev,
+                                  reinterpret_cast<cudaStream_t>(stream));
+  // the pair offsets have replaced the counts
+  if (params->neighbourhood == GPF_NB_BALL_KNN) hc.valid = false;
   if (e != cudaSuccess) return cuda_fail(e, "gpf_radiance_bwd");
   return GPF_OK;
 }

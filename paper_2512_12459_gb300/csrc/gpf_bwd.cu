@@ -808,7 +808,7 @@ cudaError_t launch_c(const BwdArgs& a, const IndexDims& d, bool psi, bool f64,
 cudaError_t launch_backward(const IndexDims& d, const IndexBuffers& b, const gpf_field& f,
                             const gpf_queries& q, const gpf_query_params& p,
                             const float* grad_out, const float* out, const float* z,
-                            const gpf_field_grad& g, const KernelEvents& ev,
+                            const gpf_field_grad& g, bool hyb_counted, const KernelEvents& ev,
                             cudaStream_t stream) {
   // every gradient is written by the epilogue kernel (zeros for Gaussians
   // out of reach), which leaves them untouched when the build set a flag
@@ -848,7 +848,7 @@ cudaError_t launch_backward(const IndexDims& d, const IndexBuffers& b, const gpf
   a.cut2 = isinf(d.cutoff) ? INFINITY : d.cutoff * d.cutoff;
   if (p.neighbourhood == GPF_NB_BALL_KNN) {
     // the selected pairs, sorted by Gaussian; no truncation of the weights
-    const cudaError_t e = launch_hybrid_pairs(d, b, q, p, n, stream);
+    const cudaError_t e = launch_hybrid_pairs(d, b, q, p, n, hyb_counted, stream);
     if (e != cudaSuccess) return e;
     a.nbrange = b.nbrange;
     a.nbval = b.nbval[b.nbsorted];

@@ -506,9 +506,18 @@ hybrid_fwd_kernel(HybArgs a) {
       for (int c = 0; c < C; ++c) a.out[(int64_t)c * a.m + q] = 0.0f;
       if (a.z) a.z[q] = 0.0f;
     }
-    if (MODE == kHybCount && in_range && !active) a.nbcnt[k] = 0u;
+    // (the forward writes the counts too when asked to)
+    const bool counts = MODE == kHybCount || (MODE == kHybSums && a.nbcnt != nullptr);
+    if (counts && in_range && !active && !partial) a.nbcnt[k] = 0u;
     if (tile * kWarp >= n_act) continue;  // warp-uniform
-    const uint32_t pos = MODE == kHybEmit && active ? a.nbcnt[k] : 0u;
+    uint32_t pos = MODE == kHybEmit && active ? a.nbcnt[k] : 0u;
+    if (MODE == kHybEmit && partial) {
+      // after the ball pairs of the tile's earlier parts (their counts from
+      // the counting pass)
+      for (uint32_t p = 0; p < part; ++p)
+        pos += (uint32_t)__float_as_int(a.hsum[(size_t)(item - part + p) * (C + 2) * kWarp +
+                                               (C + 1) * kWarp + lane]);
+    }
     float px = 0.f, py = 0.f, pz = 0.f;
     if (active) {
       px = a.x[q];
@@ -645,6 +654,9 @@ hybrid_fwd_kernel(HybArgs a) {
       lane_ball<C, PSI, MODE>(a, px, py, pz, L, Z, cnt, pos, k);
     }
     if (partial) {
+      // the part's sums (its ball count in the counting pass); the emitting
+      // pass has written its pairs and keeps the counts
+      if (MODE == kHybEmit) continue;
       float* dst = a.hsum + (size_t)item * (C + 2) * kWarp + lane;
 #pragma unroll
       for (int c = 0; c < C; ++c) dst[c * kWarp] = L[c];
@@ -666,7 +678,7 @@ hybrid_fwd_kernel(HybArgs a) {
                                               KnnList{s_kd[wib], s_kg[wib]});
       if (need) cnt = nk;
     }
-    if (MODE == kHybCount && active) a.nbcnt[k] = (uint32_t)cnt;
+    if (counts && active) a.nbcnt[k] = (uint32_t)cnt;
     if (MODE == kHybSums && active) {
       float scale = 1.0f;
       if (a.mode == GPF_NORMALIZED) scale = 1.0f / fmaxf(Z, a.eps);
@@ -823,42 +835,51 @@ __global__ void nb_range_kernel(const uint32_t* __restrict__ keys, const DeviceH
   if (i == n - 1 || keys[i + 1] != k) range[k].y = (uint32_t)(i + 1);
 }
 
-}  // namespace
-
-cudaError_t launch_hybrid_forward(const IndexDims& d, const IndexBuffers& b,
-                                  const gpf_queries& q, const gpf_query_params& p, int64_t n,
-                                  float* out, float* z, const KernelEvents& ev,
-                                  cudaStream_t stream) {
-  if (q.m == 0) return cudaSuccess;
-  HybArgs a = hyb_args(d, b, q, p, n);
-  a.out = out;
-  a.z = z;
-  cudaError_t e;
-  if (ev.start && (e = cudaEventRecord(ev.start, stream)) != cudaSuccess) return e;
-  const bool psi = isfinite(p.r_max);
-  if (n > 0) {
-    // heavy tiles split into parts over their listed entries, then finished
-    const int64_t n_tiles = (q.m + kWarp - 1) / kWarp;
-    const unsigned blocks = (unsigned)((n_tiles + kHybWarps - 1) / kHybWarps);
-    switch (d.channels) {
+// The split plan of a selection pass: each tile's listed ball entries and
+// parts (hyb_cost_kernel), the unit list of the split tiles, and the
+// buffers that the passes read it from.
+cudaError_t hyb_split_plan(HybArgs& a, const IndexDims& d, const IndexBuffers& b,
+                           const gpf_queries& q, cudaStream_t stream) {
+  const int64_t n_tiles = (q.m + kWarp - 1) / kWarp;
+  const unsigned blocks = (unsigned)((n_tiles + kHybWarps - 1) / kHybWarps);
+  switch (d.channels) {
 #define GPF_HYB_COST(CC)                                                                      \
   case CC:                                                                                    \
     hyb_cost_kernel<CC><<<blocks, kHybThreads, 0, stream>>>(a, b.hparts, b.hoff, b.hitems); \
     break;
-      GPF_HYB_COST(1) GPF_HYB_COST(2) GPF_HYB_COST(3) GPF_HYB_COST(4)
-      GPF_HYB_COST(5) GPF_HYB_COST(6) GPF_HYB_COST(7) GPF_HYB_COST(8)
+    GPF_HYB_COST(1) GPF_HYB_COST(2) GPF_HYB_COST(3) GPF_HYB_COST(4)
+    GPF_HYB_COST(5) GPF_HYB_COST(6) GPF_HYB_COST(7) GPF_HYB_COST(8)
 #undef GPF_HYB_COST
-      default:
-        return cudaErrorInvalidValue;
-    }
-    note_launches(1);
-    if ((e = launch_split_units(n_tiles, b.hparts, b.hoff, b.hunit, &b.header->n_hunits,
-                                b.scan_ws, stream)) != cudaSuccess)
-      return e;
-    a.hparts = b.hparts;
-    a.hitems = b.hitems;
-    a.hunit = b.hunit;
-    a.hsum = b.hsum;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  note_launches(1);
+  cudaError_t e = launch_split_units(n_tiles, b.hparts, b.hoff, b.hunit, &b.header->n_hunits,
+                                     b.scan_ws, stream);
+  if (e != cudaSuccess) return e;
+  a.hparts = b.hparts;
+  a.hitems = b.hitems;
+  a.hunit = b.hunit;
+  a.hsum = b.hsum;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_hybrid_forward(const IndexDims& d, const IndexBuffers& b,
+                                  const gpf_queries& q, const gpf_query_params& p, int64_t n,
+                                  float* out, float* z, bool write_counts,
+                                  const KernelEvents& ev, cudaStream_t stream) {
+  if (q.m == 0) return cudaSuccess;
+  HybArgs a = hyb_args(d, b, q, p, n);
+  a.out = out;
+  a.z = z;
+  if (write_counts) a.nbcnt = b.nbcnt;
+  cudaError_t e;
+  if (ev.start && (e = cudaEventRecord(ev.start, stream)) != cudaSuccess) return e;
+  const bool psi = isfinite(p.r_max);
+  if (n > 0) {
+    if ((e = hyb_split_plan(a, d, b, q, stream)) != cudaSuccess) return e;
     a.phase = kHybSplitParts;
     if ((e = hyb_pass<kHybSums>(a, d.channels, psi, stream)) != cudaSuccess) return e;
     a.phase = kHybSplitFinish;
@@ -868,7 +889,8 @@ cudaError_t launch_hybrid_forward(const IndexDims& d, const IndexBuffers& b,
 }
 
 cudaError_t launch_hybrid_pairs(const IndexDims& d, const IndexBuffers& b, const gpf_queries& q,
-                                const gpf_query_params& p, int64_t n, cudaStream_t stream) {
+                                const gpf_query_params& p, int64_t n, bool counted,
+                                cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(b.nbrange, 0, sizeof(uint2) * (size_t)std::max<int64_t>(n, 1),
                                   stream);
   if (e != cudaSuccess) return e;
@@ -879,11 +901,29 @@ cudaError_t launch_hybrid_pairs(const IndexDims& d, const IndexBuffers& b, const
   a.nbval = b.nbval[0];
   a.nb_max = d.nb_max;
   const bool psi = isfinite(p.r_max);
-  // pairs per hit point, their offsets and total, the pairs themselves
-  if ((e = hyb_pass<kHybCount>(a, d.channels, psi, stream)) != cudaSuccess) return e;
+  // pairs per hit point, their offsets and total, the pairs themselves; the
+  // heavy tiles split as in the forward: their parts count (then write) the
+  // ball pairs of their share of the entries, the finish adds the counts
+  // (then writes the kNN pairs of the points that fall back)
+  if (counted) {
+    // the forward's plan and counts
+    a.hparts = b.hparts;
+    a.hitems = b.hitems;
+    a.hunit = b.hunit;
+    a.hsum = b.hsum;
+  } else {
+    if ((e = hyb_split_plan(a, d, b, q, stream)) != cudaSuccess) return e;
+    a.phase = kHybSplitParts;
+    if ((e = hyb_pass<kHybCount>(a, d.channels, psi, stream)) != cudaSuccess) return e;
+    a.phase = kHybSplitFinish;
+    if ((e = hyb_pass<kHybCount>(a, d.channels, psi, stream)) != cudaSuccess) return e;
+  }
   if ((e = exclusive_scan_u32(b.nbcnt, b.nbcnt, q.m, &b.header->nb_pairs, b.scan_ws, stream)) !=
       cudaSuccess)
     return e;
+  a.phase = kHybSplitParts;
+  if ((e = hyb_pass<kHybEmit>(a, d.channels, psi, stream)) != cudaSuccess) return e;
+  a.phase = kHybSplitFinish;
   if ((e = hyb_pass<kHybEmit>(a, d.channels, psi, stream)) != cudaSuccess) return e;
   // by Gaussian, stable: each Gaussian's hit points stay in increasing order
   e = radix_sort_pairs(b.nbkey[0], b.nbval[0], b.nbkey[1], b.nbval[1], d.nb_max,

@@ -148,21 +148,26 @@ cudaError_t launch_forward(const IndexDims& dims, const IndexBuffers& b, const g
                            unsigned long long* counts, const KernelEvents& ev,
                            cudaStream_t stream);
 // The GPF_NB_BALL_KNN forward (gpf_hybrid.cu).
+// write_counts: also each hit point's number of selected pairs into nbcnt
+// (and each split part's ball count), for launch_hybrid_pairs(counted).
 cudaError_t launch_hybrid_forward(const IndexDims& dims, const IndexBuffers& b,
                                   const gpf_queries& q, const gpf_query_params& p, int64_t n,
-                                  float* out, float* z, const KernelEvents& ev,
-                                  cudaStream_t stream);
+                                  float* out, float* z, bool write_counts,
+                                  const KernelEvents& ev, cudaStream_t stream);
 // The selected (hit point, Gaussian) pairs of the GPF_NB_BALL_KNN query,
 // sorted by Gaussian: b.nbval[b.nbsorted] holds the hit point positions of
 // Gaussian g in [b.nbrange[g].x, b.nbrange[g].y) (gpf_hybrid.cu). Sets the
 // capacity flag when they exceed dims.nb_max.
+// counted: the last forward of this build wrote the counts for the same
+// selection (launch_hybrid_forward with write_counts), so they are not
+// computed again.
 cudaError_t launch_hybrid_pairs(const IndexDims& dims, const IndexBuffers& b,
                                 const gpf_queries& q, const gpf_query_params& p, int64_t n,
-                                cudaStream_t stream);
+                                bool counted, cudaStream_t stream);
 cudaError_t launch_backward(const IndexDims& dims, const IndexBuffers& b, const gpf_field& f,
                             const gpf_queries& q, const gpf_query_params& p,
                             const float* grad_out, const float* out, const float* z,
-                            const gpf_field_grad& g, const KernelEvents& ev,
+                            const gpf_field_grad& g, bool hyb_counted, const KernelEvents& ev,
                             cudaStream_t stream);
 
 // ---- loss and optimiser (gpf_optim.cu)

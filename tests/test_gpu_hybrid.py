@@ -84,12 +84,7 @@ def test_dense_tiles_are_split_and_match_the_oracle(gpf, mode):
     the tiles into parts over their entries and adds the parts' sums in
     order; each hit point still sums its whole ball (or its k_min nearest at
     the rim)."""
-    rng = np.random.default_rng(97)
-    n = 30000
-    pos = np.zeros((n, 3))
-    pos[:, :2] = rng.standard_normal((n, 2)) * 0.03
-    pos[:, 0] += 2.0                            # on the floor, clear of the sphere
-    flux = rng.exponential(1.0, (n, 3))
+    pos, flux = _dense_blob(30000, 97)
     fnp = synth.field_from_photons(pos, flux, seed=97)
     qnp = synth.pinhole_hitpoints((2.0, -0.15, 0.15), (2.0, 0.0, 0.0), 64, 48)
     out, (idx, *_rest) = _run(gpf, fnp, qnp, mode, R, 3)
@@ -187,6 +182,34 @@ def test_hybrid_backward_matches_the_oracle(gpf, mode, ball_r, k_min):
         assert grad_err(g[k], ref[k]) < GRAD_TOL, (k, grad_err(g[k], ref[k]))
 
 
+def _dense_blob(n, seed):
+    """n photons with a 3 cm spread on the floor at (2, 0), clear of the sphere."""
+    rng = np.random.default_rng(seed)
+    pos = np.zeros((n, 3))
+    pos[:, :2] = rng.standard_normal((n, 2)) * 0.03
+    pos[:, 0] += 2.0
+    return pos, rng.exponential(1.0, (n, 3))
+
+
+@pytest.mark.parametrize("mode", [oracle.GPF_NORMALIZED, oracle.GPF_SUM])
+def test_dense_tiles_backward_matches_the_oracle(gpf, mode):
+    """The backward's selection passes split the dense tiles like the forward:
+    each part counts, then writes, the ball pairs of its share of the tile's
+    entries after those of the earlier parts. Same pairs, same gradients."""
+    from gpu_helpers import GRAD_TOL, grad_err
+    pos, flux = _dense_blob(12000, 195)
+    fnp = _anisotropic(synth.field_from_photons(pos, flux, seed=195), 195)
+    qnp = synth.pinhole_hitpoints((2.0, -0.15, 0.15), (2.0, 0.0, 0.0), 48, 36)
+    g, ref, ref_f, idx = _bwd_case(gpf, fnp, qnp, mode, R, 3, seed=5)
+    st = idx.stats()
+    assert st["n_hybrid_units"] > 0
+    assert ref_f["knn"].any() and (ref_f["n_nb"] > 500).any()
+    # every point's selection but those float32 may decide differently
+    assert abs(st["n_nb_pairs"] - int(ref_f["n_nb"].sum())) <= 16 * int(ref_f["near"].sum())
+    for k in g:
+        assert grad_err(g[k], ref[k]) < GRAD_TOL, (k, grad_err(g[k], ref[k]))
+
+
 @pytest.mark.parametrize("mode", [oracle.GPF_NORMALIZED, oracle.GPF_SUM])
 def test_hybrid_backward_float64_sums(gpf, mode):
     """The gradient-check build on the hybrid pairs: 1e-6 normwise."""
@@ -222,3 +245,37 @@ def test_hybrid_backward_is_reproducible_and_flags_a_full_pair_buffer(gpf):
     torch.cuda.synchronize()
     assert all(torch.all(t == 7.0) for t in grads.tensors())
     assert idx.stats()["flags"] & _abi.GPF_FLAG_CAPACITY
+
+
+def test_backward_reuses_the_forwards_counts_only_for_the_same_selection(gpf):
+    """After a GPF_NB_BALL_KNN forward with the same ball_r and k_min the
+    backward takes that forward's per-point counts instead of counting again;
+    after a forward with another k_min, or with no forward since the build,
+    it counts itself. The gradients are bitwise the same in all three."""
+    import torch
+    from paper_2512_12459_gb300.setup_index import make_index
+    pos, flux = _dense_blob(6000, 196)
+    fnp = synth.field_from_photons(pos, flux, seed=196)
+    qnp = synth.pinhole_hitpoints((2.0, -0.15, 0.15), (2.0, 0.0, 0.0), 48, 36)
+    field, queries = gpf.Field.from_numpy(fnp), gpf.Queries.from_numpy(qnp)
+    idx = make_index(field, queries, query_cell=0.05, ball_radius=R, max_nb_pairs=4_000_000)
+    G = torch.as_tensor(np.random.default_rng(7).standard_normal((3, queries.m)),
+                        dtype=torch.float32, device="cuda")
+    kw = dict(neighbourhood=gpf.GPF_NB_BALL_KNN, ball_r=R, k_min=3)
+
+    def grads(forward_k):
+        idx.build(field, queries)
+        if forward_k is not None:
+            gpf.gpf_radiance_fwd(idx, field, queries, gpf.GPF_SUM, r_max=R,
+                                 neighbourhood=gpf.GPF_NB_BALL_KNN, ball_r=R, k_min=forward_k)
+        g = gpf.gpf_radiance_bwd(idx, field, queries, G, mode=gpf.GPF_SUM, r_max=R, **kw)
+        torch.cuda.synchronize()
+        assert idx.stats()["flags"] == 0
+        return [t.clone() for t in g.tensors()], idx.stats()["n_nb_pairs"]
+
+    same, n_same = grads(3)
+    other, n_other = grads(8)
+    none, n_none = grads(None)
+    assert n_same == n_other == n_none > 0
+    for a, b, c in zip(same, other, none):
+        assert torch.equal(a, b) and torch.equal(a, c)
