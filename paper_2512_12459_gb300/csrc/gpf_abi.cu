@@ -137,6 +137,8 @@ size_t layout(const gpf_index* ix, char* base, IndexBuffers* b) {
     const int64_t tiles = (M + kWarp - 1) / kWarp;
     t.cocc = reinterpret_cast<uint32_t*>(
         take(sizeof(uint32_t) * (((size_t)d.grid.cdx * d.grid.cdy * d.grid.cdz + 31) / 32)));
+    if (d.grid.fwords)
+      t.focc = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * focc_words(d.grid)));
     t.hparts = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (tiles + 1)));
     t.hoff = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (tiles + 1)));
     t.hitems = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (tiles + 1)));
@@ -373,6 +375,13 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
     d.grid.cdx = (d.grid.max0x >> sh) + 1;
     d.grid.cdy = (d.grid.max0y >> sh) + 1;
     d.grid.cdz = (d.grid.max0z >> sh) + 1;
+    // fine centre occupancy: one bit per centre cell, rows along x in whole
+    // words, when it takes at most 2^24 words (64 MB)
+    const int L = d.grid.blevel;
+    const uint64_t fw = ((uint64_t)(d.grid.max0x >> L) + 32) / 32;
+    const uint64_t fr = (uint64_t)((d.grid.max0y >> L) + 1) * ((d.grid.max0z >> L) + 1);
+    d.grid.fwords = fw * fr <= (1u << 24) ? (uint32_t)fw : 0u;
+    d.grid.fdy = (d.grid.max0y >> L) + 1;
   }
   d.grid.dx = cfg->dims[0];
   d.grid.dy = cfg->dims[1];

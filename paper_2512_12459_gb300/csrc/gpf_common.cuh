@@ -143,9 +143,19 @@ struct Grid {
   int obits;               // bits of an order key (cell key and 2 class bits)
   int coop;                // forward: cooperative mode up to this many cells
   int blevel;              // centre level of the ball query (-1: no centre entries)
-  int cshift;              // level of the centre occupancy bits (>= blevel + 2)
+  int cshift;              // level of the coarse centre occupancy bits (>= blevel + 2)
   uint32_t cdx, cdy, cdz;  // cells per axis on that level
+  uint32_t fwords;         // 32-bit words per x row of the fine (centre-level)
+                           // occupancy bits (0: no fine bits)
+  uint32_t fdy;            // centre-level cells along y
 };
+
+// Word of the fine centre occupancy bits holding centre cell (cx, cy, cz)
+// (bit cx & 31 of it): rows along x, padded to whole words.
+__device__ __forceinline__ uint32_t focc_word(const Grid& g, uint32_t cx, uint32_t cy,
+                                              uint32_t cz) {
+  return (cz * g.fdy + cy) * g.fwords + (cx >> 5);
+}
 
 // Bit of the centre occupancy map (one bit per cell of level cshift, set when
 // some Gaussian mean lies in it) for the centre-level cell (cx, cy, cz).

@@ -68,6 +68,7 @@ struct HybArgs {
   const uint2* brange;
   const uint32_t* gval;
   const uint32_t* cocc;    // centre occupancy bits (Grid::cshift cells)
+  const uint32_t* focc;    // and per centre cell (Grid::fwords > 0)
   int mode;
   float r, r2, inv_rr;     // falloff radius psi
   float eps;
@@ -294,8 +295,14 @@ __device__ int warp_knn(const HybArgs& a, bool need, float px, float py, float p
       const int ux0 = max(x0, 0) >> cs, uy0 = max(y0, 0) >> cs;
       const int unx = (min(x1, mx) >> cs) - ux0 + 1, nu = unx * ((min(y1, my) >> cs) - uy0 + 1);
       const float runx = 1.0f / (float)unx;
+      // the fine bits' words under the rectangle: rows fy0.., words fw0..
+      const int fx0 = max(x0, 0), fx1 = min(x1, mx), fy0 = max(y0, 0);
+      const int fw0 = fx0 >> 5, fnw = (fx1 >> 5) - fw0 + 1;
+      const int fn = G.fwords ? fnw * (min(y1, my) - fy0 + 1) : 0;
+      const float rfnw = 1.0f / (float)fnw;
       for (int sz = max(z0, 0); sz <= min(z1, mz); ++sz) {
-        // a slice with no mean under its rectangle is skipped whole
+        // a slice with no mean under its rectangle is skipped whole: first by
+        // the coarse bits (a few words in cache), then by the fine ones
         uint32_t any = 0u;
         for (int u = lane; u < nu; u += kWarp) {
           const int uy = (int)(((float)u + 0.5f) * runx);   // u / unx, exact at these sizes
@@ -304,6 +311,19 @@ __device__ int warp_knn(const HybArgs& a, bool need, float px, float py, float p
           any |= (__ldg(a.cocc + (bit >> 5)) >> (bit & 31u)) & 1u;
         }
         if (!__any_sync(kFullMask, any != 0u)) continue;
+        if (G.fwords) {
+          any = 0u;
+          for (int u = lane; u < fn; u += kWarp) {
+            const int r = (int)(((float)u + 0.5f) * rfnw);  // u / fnw, exact at these sizes
+            const int w = fw0 + u - r * fnw;
+            // the bits of word w inside [fx0, fx1]
+            const int b0 = max(fx0 - 32 * w, 0), b1 = min(fx1 - 32 * w, 31);
+            const uint32_t m = (b1 == 31 ? 0xffffffffu : (2u << b1) - 1u) & ~((1u << b0) - 1u);
+            any |= __ldg(a.focc + ((uint32_t)sz * G.fdy + (uint32_t)(fy0 + r)) * G.fwords +
+                         (uint32_t)w) & m;
+          }
+          if (!__any_sync(kFullMask, any != 0u)) continue;
+        }
         const bool face = R == 0 || sz == z0 || sz == z1;
         const int n_slice = face ? wx * wy : per;
         for (int c0 = 0; c0 < n_slice; c0 += kWarp) {
@@ -329,8 +349,14 @@ __device__ int warp_knn(const HybArgs& a, bool need, float px, float py, float p
               const float dy = cell_gap(G.oy, G.cell0, cy << Lb, (cy + 1) << Lb, by0, by1);
               const float dz = cell_gap(G.oz, G.cell0, cz << Lb, (cz + 1) << Lb, bz0, bz1);
               const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * 0.99999f;
-              const uint32_t bit = cocc_bit(G, (uint32_t)cx, (uint32_t)cy, (uint32_t)cz);
-              const bool occupied = (__ldg(a.cocc + (bit >> 5)) >> (bit & 31u)) & 1u;
+              bool occupied;
+              if (G.fwords) {
+                occupied = (__ldg(a.focc + focc_word(G, (uint32_t)cx, (uint32_t)cy, (uint32_t)cz)) >>
+                            (cx & 31)) & 1u;
+              } else {
+                const uint32_t bit = cocc_bit(G, (uint32_t)cx, (uint32_t)cy, (uint32_t)cz);
+                occupied = (__ldg(a.cocc + (bit >> 5)) >> (bit & 31u)) & 1u;
+              }
               if (!(d2 > __uint_as_float(tmax)) && occupied) {
                 const CellHash h =
                     cell_hash(G, Lb, (uint32_t)cx, (uint32_t)cy, (uint32_t)cz, kCentreSalt);
@@ -772,6 +798,7 @@ HybArgs hyb_args(const IndexDims& d, const IndexBuffers& b, const gpf_queries& q
   a.brange = b.brange;
   a.gval = b.gval[b.gsorted];
   a.cocc = b.cocc;
+  a.focc = b.focc;
   a.mode = p.mode;
   const bool psi = isfinite(p.r_max);
   a.r = psi ? p.r_max : 0.0f;

@@ -390,7 +390,8 @@ __global__ void emit_kernel(Grid grid, int64_t n, int64_t p_max, const float* __
                             const uint32_t* __restrict__ goffset,
                             uint32_t* __restrict__ gkey, uint32_t* __restrict__ gval,
                             int passes, uint32_t* __restrict__ digit_counts,
-                            uint32_t* __restrict__ cocc, DeviceHeader* header) {
+                            uint32_t* __restrict__ cocc, uint32_t* __restrict__ focc,
+                            DeviceHeader* header) {
   // the digit counts of the entry sort, added here as the keys are written
   __shared__ uint32_t cnt[kSortMaxPasses * kSortBins];
   for (int i = threadIdx.x; i < passes * kSortBins; i += blockDim.x) cnt[i] = 0;
@@ -417,6 +418,7 @@ __global__ void emit_kernel(Grid grid, int64_t n, int64_t p_max, const float* __
       put(pos, h.bucket, (uint32_t)g | h.tag);
       const uint32_t bit = cocc_bit(grid, cx, cy, cz);
       atomicOr(cocc + (bit >> 5), 1u << (bit & 31u));
+      if (grid.fwords) atomicOr(focc + focc_word(grid, cx, cy, cz), 1u << (cx & 31u));
       ++pos;
     }
     if (bw.x != kNoBox) {
@@ -547,11 +549,14 @@ cudaError_t launch_build(const IndexDims& d, const IndexBuffers& b, const gpf_fi
     e = cudaMemsetAsync(
         b.cocc, 0, sizeof(uint32_t) * (((size_t)grid.cdx * grid.cdy * grid.cdz + 31) / 32), stream);
     if (e != cudaSuccess) return e;
+    if (grid.fwords && (e = cudaMemsetAsync(b.focc, 0, sizeof(uint32_t) * focc_words(grid),
+                                            stream)) != cudaSuccess)
+      return e;
   }
   emit_kernel<<<blocks_for(f.n), kThreads, 0, stream>>>(
       grid, f.n, d.p_max, b.rec, rec_stride(d.channels), b.box, b.occ, b.gmask, b.goffset,
       b.gkey[0], b.gval[0], radix_sort_passes(grid.hash_bits), radix_sort_counts(b.gsort_ws),
-      b.cocc, b.header);
+      b.cocc, b.focc, b.header);
   note_launches(1);
   e = radix_sort_pairs(b.gkey[0], b.gval[0], b.gkey[1], b.gval[1], d.p_max, &b.header->n_pairs,
                        grid.hash_bits, b.gsort_ws, &b.header->stalled, stream, true);

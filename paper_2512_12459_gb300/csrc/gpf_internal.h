@@ -10,6 +10,10 @@
 namespace gpf {
 
 inline size_t align_up(size_t b, size_t a = 256) { return (b + a - 1) / a * a; }
+// Words of the fine centre occupancy bits (Grid::fwords per row).
+inline size_t focc_words(const Grid& g) {
+  return (size_t)g.fwords * g.fdy * ((g.max0z >> g.blevel) + 1);
+}
 
 // Host-side count of the kernels this library has launched (gpf_launch_count).
 void note_launches(uint64_t k);
@@ -90,6 +94,7 @@ struct IndexBuffers {
   // a centre level (ball_radius > 0): occupancy bits of the centre cells'
   // coarse cells (Grid::cshift), and the hybrid forward's tile splitting
   uint32_t* cocc;       // [cdx * cdy * cdz / 32] set: some mean lies in the cell
+  uint32_t* focc;       // [focc_words] the same per centre cell (Grid::fwords > 0)
   uint32_t* hparts;     // [tiles_max + 1] parts of each tile (1 = not split)
   uint32_t* hoff;       // [tiles_max + 1] parts of each split tile (0 otherwise), then scanned
   uint32_t* hitems;     // [tiles_max] listed entries of the centre cells of each tile's box
