@@ -89,6 +89,14 @@ struct HybArgs {
   float* hsum;             // [unit][C + 2][32] partial L, Z, count
 };
 
+// Does some mean lie in centre cell (cx, cy, cz)? The fine occupancy bits
+// when the index has them, else every cell may hold one.
+__device__ __forceinline__ bool centre_cell_occupied(const HybArgs& a, uint32_t cx, uint32_t cy,
+                                                     uint32_t cz) {
+  if (!a.grid.fwords) return true;
+  return (__ldg(a.focc + focc_word(a.grid, cx, cy, cz)) >> (cx & 31u)) & 1u;
+}
+
 // Pair j of hit point position k (emit pass): written when it fits.
 __device__ __forceinline__ void emit_pair(const HybArgs& a, uint32_t pos, uint32_t g, int64_t k) {
   if ((int64_t)pos < a.nb_max) {
@@ -605,11 +613,15 @@ hybrid_fwd_kernel(HybArgs a) {
           ccx = cx0 + ci % nx;
           ccy = cy0 + (ci / nx) % ny;
           ccz = cz0 + ci / (nx * ny);
-          const CellHash h = cell_hash(G, Lb, ccx, ccy, ccz, kCentreSalt);
-          const uint2 rg = __ldg(a.brange + h.bucket);
-          eb = rg.x;
-          len = rg.y - rg.x;
-          tag = h.tag;
+          // (a cell that holds no mean is not looked up: hyb_cost_kernel
+          // skips the same cells)
+          if (centre_cell_occupied(a, ccx, ccy, ccz)) {
+            const CellHash h = cell_hash(G, Lb, ccx, ccy, ccz, kCentreSalt);
+            const uint2 rg = __ldg(a.brange + h.bucket);
+            eb = rg.x;
+            len = rg.y - rg.x;
+            tag = h.tag;
+          }
         }
         uint32_t incl = len;
 #pragma unroll
@@ -765,6 +777,7 @@ hyb_cost_kernel(HybArgs a, uint32_t* __restrict__ hparts, uint32_t* __restrict__
     if (n_cells <= kMaxTileCells) {
       for (uint32_t i = lane; i < (uint32_t)n_cells; i += kWarp) {
         const uint32_t cx = cx0 + i % nx, cy = cy0 + (i / nx) % ny, cz = cz0 + i / (nx * ny);
+        if (!centre_cell_occupied(a, cx, cy, cz)) continue;
         const uint2 rg = __ldg(a.brange + cell_hash(G, Lb, cx, cy, cz, kCentreSalt).bucket);
         items += rg.y - rg.x;
       }
