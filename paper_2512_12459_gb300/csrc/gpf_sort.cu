@@ -9,7 +9,8 @@
 //   1. per pass, one kernel: a block claims the next tile of 3072 keys from
 //      an atomic counter (so every earlier tile is held by a block that is
 //      already running); each warp ranks its own 384 keys, 32 at a time
-//      (__match_any_sync groups, per-warp digit counters in shared memory);
+//      (groups of equal digits from bit ballots, per-warp digit counters in
+//      shared memory);
 //      the block publishes its digit counts, orders its keys by digit in
 //      shared memory, adds up the counts the earlier tiles published for each
 //      digit, walking back until a tile whose inclusive prefix is known,
@@ -204,7 +205,15 @@ onesweep_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __res
     const int li = warp * kWarpKeys + it * kWarp + lane;
     const bool ok = li < tile_n;
     const uint32_t d = ok ? (keys_in[base + li] >> shift) & (kBins - 1) : kBins;
-    const uint32_t peers = __match_any_sync(kFullMask, d);
+    // the lanes with the same digit: nine ballots (validity, then each digit
+    // bit), cheaper here than __match_any_sync
+    uint32_t peers = __ballot_sync(kFullMask, ok);
+    if (!ok) peers = ~peers;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const uint32_t m = __ballot_sync(kFullMask, (d >> b) & 1u);
+      peers &= ((d >> b) & 1u) ? m : ~m;
+    }
     uint32_t r0 = 0;
     if (ok) r0 = wcnt[warp][d];
     __syncwarp();
