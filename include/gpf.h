@@ -462,9 +462,10 @@ uint64_t gpf_launch_count(void);
  * atomics; the index needs max_nb_pairs at least the number of selected
  * pairs, and more sets the capacity flag. When the last GPF_NB_BALL_KNN
  * gpf_radiance_fwd on this build (and index) had the same ball_r and k_min,
- * it has already written each hit point's number of selected pairs, and
- * the selection runs once here instead of twice; that forward must then be
- * ordered before this call (the same stream, or an event).
+ * it has already written each hit point's number of selected pairs and the
+ * k_min nearest of the points that fell back, and the selection's ball part
+ * runs once here instead of the whole selection twice; that forward must
+ * then be ordered before this call (the same stream, or an event).
  * Errors: as gpf_radiance_fwd.
  */
 gpf_status gpf_radiance_bwd(const gpf_index *index, const gpf_field *field,

@@ -152,6 +152,8 @@ size_t layout(const gpf_index* ix, char* base, IndexBuffers* b) {
       t.nbval[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * d.nb_max));
     }
     t.nbcnt = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (M + 1)));
+    t.nbknn = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * std::max<int64_t>(M, 1) *
+                                               GPF_MAX_KMIN));
     t.nbrange = reinterpret_cast<uint2*>(take(sizeof(uint2) * std::max<int64_t>(N, 1)));
     t.nbsort_ws = take(radix_sort_workspace_bytes(d.nb_max));
     t.nbsorted = radix_sort_passes(d.grid.id_bits) % 2;

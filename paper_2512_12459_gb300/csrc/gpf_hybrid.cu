@@ -79,6 +79,9 @@ struct HybArgs {
   float* z;
   unsigned long long* next_tile;
   uint32_t* nbcnt;         // count pass: pairs per point; emit pass: their offsets
+  uint32_t* knn_ids;       // [M][GPF_MAX_KMIN] kNN ids of the points that fall back:
+                           // written by the forward, read by an emit pass (knn_stored)
+  bool knn_stored;
   uint32_t* nbkey;         // emit pass: Gaussian ids of the pairs
   uint32_t* nbval;         // emit pass: hit point positions of the pairs
   int64_t nb_max;          // capacity of nbkey / nbval
@@ -471,6 +474,7 @@ __device__ int warp_knn(const HybArgs& a, bool need, float px, float py, float p
 #pragma unroll
       for (int c = 0; c < C; ++c) L[c] = fmaf(w, rr[13 + c], L[c]);
       Z += w;
+      if (a.knn_ids) a.knn_ids[k_pos * GPF_MAX_KMIN + i] = kg[i * kWarp];
     } else if (MODE == kHybEmit) {
       emit_pair(a, pos + (uint32_t)i, kg[i * kWarp], k_pos);
     }
@@ -711,7 +715,16 @@ hybrid_fwd_kernel(HybArgs a) {
       for (int c = 0; c < C; ++c) L[c] = 0.0f;
       Z = 0.0f;
     }
-    if (a.n > 0) {
+    if (MODE == kHybEmit && a.knn_stored) {
+      // the forward's search, in its order: as many ids as the point's pairs
+      if (need) {
+        const uint32_t end = k + 1 < a.m ? a.nbcnt[k + 1] : a.header->nb_pairs;
+        const uint32_t nk = end - pos;
+        for (uint32_t i = 0; i < nk; ++i)
+          emit_pair(a, pos + i, a.knn_ids[k * GPF_MAX_KMIN + i], k);
+        cnt = (int)nk;
+      }
+    } else if (a.n > 0) {
       const int nk = warp_knn<C, PSI, MODE>(a, need, px, py, pz, L, Z, pos, k, s_cand[wib],
                                               KnnList{s_kd[wib], s_kg[wib]});
       if (need) cnt = nk;
@@ -914,7 +927,10 @@ cudaError_t launch_hybrid_forward(const IndexDims& d, const IndexBuffers& b,
   HybArgs a = hyb_args(d, b, q, p, n);
   a.out = out;
   a.z = z;
-  if (write_counts) a.nbcnt = b.nbcnt;
+  if (write_counts) {
+    a.nbcnt = b.nbcnt;
+    a.knn_ids = b.nbknn;
+  }
   cudaError_t e;
   if (ev.start && (e = cudaEventRecord(ev.start, stream)) != cudaSuccess) return e;
   const bool psi = isfinite(p.r_max);
@@ -946,7 +962,9 @@ cudaError_t launch_hybrid_pairs(const IndexDims& d, const IndexBuffers& b, const
   // ball pairs of their share of the entries, the finish adds the counts
   // (then writes the kNN pairs of the points that fall back)
   if (counted) {
-    // the forward's plan and counts
+    // the forward's plan, counts and kNN ids
+    a.knn_ids = b.nbknn;
+    a.knn_stored = true;
     a.hparts = b.hparts;
     a.hitems = b.hitems;
     a.hunit = b.hunit;

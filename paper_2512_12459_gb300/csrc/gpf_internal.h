@@ -83,6 +83,8 @@ struct IndexBuffers {
   uint32_t* nbkey[2];   // [nb_max] Gaussian ids (sort ping-pong)
   uint32_t* nbval[2];   // [nb_max] sorted hit point positions
   uint32_t* nbcnt;      // [M_max + 1] pairs per hit point, then their offsets
+  uint32_t* nbknn;      // [M_max * GPF_MAX_KMIN] the forward's kNN ids of each point
+                        // that fell back (read by launch_hybrid_pairs(counted))
   uint2* nbrange;       // [N_max] [start, end) of each Gaussian's pairs
   void* nbsort_ws;
   int nbsorted;
