@@ -350,7 +350,7 @@ def run_batched(args):
     torch.cuda.empty_cache()
 
     t0 = time.time()
-    grid, report = autotune(field, queries, r_max=R_MAX, repeats=2)
+    grid, report = autotune(field, queries, r_max=R_MAX, repeats=4)
     tune_s = time.time() - t0
     idx = make_index(field, queries, grid=grid, headroom=1.25)
     step = TrainStep(field, queries, target, idx, r_max=R_MAX, lr=LR)
@@ -455,7 +455,7 @@ def run_train(args):
     tidx.build(tf, queries)
     target = gpf.gpf_radiance_fwd(tidx, tf, queries, gpf.GPF_SUM, r_max=R_MAX)[0].clone()
     del tidx, tf
-    grid, _ = autotune(field, queries, r_max=R_MAX, repeats=2)
+    grid, _ = autotune(field, queries, r_max=R_MAX, repeats=4)
     idx = make_index(field, queries, grid=grid, headroom=1.25)
     step = TrainStep(field, queries, target, idx, r_max=R_MAX, lr=LR)
     step.capture(warmup=1)                      # one real step, then the recording
@@ -908,7 +908,7 @@ def main():
                          query_cell=float(qc), max_span=int(span), coop_cells=int(coop),
                          split_items=int(parts[3]) if len(parts) > 3 else 0)
     else:
-        tuned, _ = autotune(field, queries, cutoff_sigma=CUTOFF, r_max=R_MAX, repeats=2)
+        tuned, _ = autotune(field, queries, cutoff_sigma=CUTOFF, r_max=R_MAX, repeats=4)
         idx = make_index(field, queries, grid=tuned, headroom=1.25)
     state = gpf.AdamState.zeros_like(field)
     grads = gpf.Field(*(torch.empty_like(t) for t in field.tensors()))

@@ -133,7 +133,9 @@ def make_index(field: Field, queries: Queries, cutoff_sigma: float = 3.0,
 
 def time_step(index: Index, field: Field, queries: Queries, mode: int = 0, r_max: float = 0.02,
               repeats: int = 3, backward: bool = True) -> float:
-    """Median milliseconds of build + forward (+ backward) with `index`."""
+    """Fastest of `repeats` runs of build + forward (+ backward) with `index`,
+    in milliseconds (the fastest run is the one least disturbed by other work
+    on the GPU or host)."""
     from . import api
     out = torch.empty((field.channels, queries.m), device=field.mean.device)
     z = torch.empty((queries.m,), device=field.mean.device)
@@ -153,7 +155,7 @@ def time_step(index: Index, field: Field, queries: Queries, mode: int = 0, r_max
         e1.synchronize()
         if i:                       # the first run pays one-off costs
             times.append(e0.elapsed_time(e1))
-    return float(sorted(times)[len(times) // 2])
+    return float(min(times))
 
 
 def autotune(field: Field, queries: Queries, cutoff_sigma: float = 3.0, mode: int = 0,
@@ -166,8 +168,9 @@ def autotune(field: Field, queries: Queries, cutoff_sigma: float = 3.0, mode: in
     a time: the query cell size (the hit-point grid), then the largest span of
     a Gaussian's box in cells of its level (the cell size of every level),
     then the cooperative-mode threshold of the forward's 32-point tiles,
-    then the work above which a tile is split over several units (0: never).
-    Returns (best GridConfig, report), report = [(knobs, ms), ...] in the
+    then the work above which a tile is split over several units (0: never),
+    and last the query cell again with the other knobs settled. Each trial
+    scores the fastest of `repeats` runs. Returns (best GridConfig, report), report = [(knobs, ms), ...] in the
     order tried. Results are independent of the choice; only speed differs.
     backward=False times build + forward only (a query without gradient,
     such as the GPF_DISK_KDE gather)."""
@@ -191,8 +194,11 @@ def autotune(field: Field, queries: Queries, cutoff_sigma: float = 3.0, mode: in
             torch.cuda.empty_cache()
         return cache[key][0]
 
+    # one knob at a time, then the query cell once more with the others
+    # settled (its first pass saw their initial values)
     for name, options in (("query_cell", query_cells), ("max_span", max_spans),
-                          ("coop_cells", coop_options), ("split_items", split_options)):
+                          ("coop_cells", coop_options), ("split_items", split_options),
+                          ("query_cell", query_cells)):
         scores = {}
         for v in options:
             knobs = dict(best, **{name: v})
