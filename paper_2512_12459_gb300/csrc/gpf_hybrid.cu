@@ -7,20 +7,27 @@
 //
 // The means are listed once each under their cell on the centre level (cells
 // of edge >= the index's ball_radius), hashed like the box lists under a
-// separate key space. One warp per tile of 32 cell-sorted hit points, taking
-// tiles from the work counter:
-//   * ball: the warp walks the centre cells that the tile's box, grown by
-//     ball_r, overlaps; each lane vets one listed Gaussian (its tag, its
-//     centre cell, its mean's distance to the tile's box); survivors are
-//     staged in shared memory and every lane tests and sums them for its own
-//     hit point (a tile whose grown box meets more than kMaxTileCells cells
-//     walks the 3 x 3 x 3 cells around each hit point lane by lane instead);
+// separate key space, and marked in two occupancy bitmaps of those cells (a
+// coarse one of 4 x 4 x 4 cells or more, and one bit per centre cell). One
+// warp per tile of 32 cell-sorted hit points, taking tiles from the work
+// counter:
+//   * ball: the warp fetches the lists of the centre cells that the tile's
+//     box, grown by ball_r, overlaps (32 cells at a time, empty cells
+//     skipped) and spreads their entries over the lanes; each lane vets one
+//     (its tag, its centre cell, its mean's distance to the tile's box);
+//     survivors are staged in shared memory and every lane tests and sums
+//     them for its own hit point (a tile whose grown box meets more than
+//     kMaxTileCells cells walks the 3 x 3 x 3 cells around each hit point
+//     lane by lane instead). Tiles whose boxes list many entries are split
+//     into parts over those entries, and a finish pass adds the parts;
 //   * kNN: the hit points whose ball holds fewer than k_min Gaussians take
-//     the k_min nearest means instead, searched by the whole warp one centre
-//     cell of such points at a time: rings of cells around that cell, each
-//     ring's cells spread over the lanes and their listed means 32 at a time,
-//     every point keeping its own sorted list in shared memory; a cell beyond
-//     every point's k-th distance is skipped, and a point is settled once its
+//     the k_min nearest means instead, searched by the whole warp for one
+//     group of such points at a time (those within one cell of each other):
+//     rings of cells around the group's cells, slice by slice (slices and
+//     cells with no mean skipped by the bitmaps), each slice's cells spread
+//     over the lanes and their listed means 32 at a time, every point
+//     keeping its own sorted list in shared memory; a cell beyond every
+//     point's k-th distance is skipped, and a point is settled once its
 //     k-th distance is within the searched box.
 // The same selection serves the backward (Sec. 4.2, Differentiable
 // Accumulation, with N(x) held fixed): a counting pass writes each hit
@@ -28,7 +35,10 @@
 // point its offset, an emitting pass writes the (Gaussian, hit point) pairs
 // there in the order the selection visits them, and a stable sort by
 // Gaussian leaves every Gaussian's hit points in increasing order: the
-// pairs, and so the backward's sums, do not depend on thread timing.
+// pairs, and so the backward's sums, do not depend on thread timing. A
+// forward asked to (write_counts) leaves the counts and the kNN lists
+// behind, so that the backward that follows needs neither the counting pass
+// nor the kNN search.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <limits.h>
