@@ -20,6 +20,8 @@
 // brute force) the candidates are all Gaussians, in index order.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <cmath>
 #include <stdint.h>
 
 #include "gpf_internal.h"
@@ -52,6 +54,7 @@ struct FwdArgs {
   float eps;
   float kde_scale;         // disk kernel: 1 / (pi r^2)
   float cut, cut2;         // k, k^2
+  float tscale;            // sqrt(3 log2 e) / max(r, 1e-6): the falloff root in base 2
   float* out;              // [C,M]
   float* z;                // [M] or null
   unsigned long long* counts;  // count mode: [candidates, included]
@@ -75,6 +78,28 @@ __device__ __forceinline__ float warp_max(float v) {
 // Pair kernels: the Gaussian weight alone, with the soft falloff psi, or the
 // disk of the photon density estimate.
 constexpr int kKernGauss = 0, kKernFalloff = 1, kKernDisk = 2;
+constexpr float kNegHalfLog2e = -0.72134752044448170368f;   // -log2(e) / 2
+
+// w = exp(-Q/2) psi(|d|) of an included pair as 2^-(Q log2(e)/2 + t'^2), with
+// t' = sqrt(3 log2 e) (|d| - r)/r beyond the falloff radius r (zero within).
+// |d| comes from one reciprocal square root (relative error ~2^-22), which
+// moves the exponent by about 2 t'(t' + r tscale) 2^-22: below 2e-6 relative
+// in w for t' <= 2, and terms with larger t' carry less than 2^-4 of their
+// Gaussian factor.
+template <int KERN>
+__device__ __forceinline__ float pair_exp2(float Q, float dx, float dy, float dz,
+                                           const FwdArgs& a) {
+  float e = Q * kNegHalfLog2e;
+  if (KERN == kKernFalloff) {
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (d2 > a.r2) {
+      // |d| = d2 rsqrt(d2), as staged_weight takes it (same w bit for bit)
+      const float t = fmaf(d2, rsqrtf(d2), -a.r) * a.tscale;
+      e = fmaf(-t, t, e);
+    }
+  }
+  return ex2_approx(e);
+}
 
 // Weight of one pair: w = exp(-Q/2) psi(|d|) when Q <= k^2 (hit = true); for
 // the disk kernel w = 1 when |d| <= r (Eq. kde; 1/(pi r^2) is applied once
@@ -106,17 +131,7 @@ __device__ __forceinline__ float pair_weight(const float* __restrict__ r, float 
   }
   hit = Q <= a.cut2;
   if (!hit) return 0.0f;
-  float e = -0.5f * Q;
-  if (KERN == kKernFalloff) {
-    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    if (d2 > a.r2) {
-      // correctly rounded: the exponent's sensitivity to |d| is 6 t (t + 1) / |d|
-      const float dist = sqrtf(d2);
-      const float t = (dist - a.r) * a.inv_rr;
-      e = fmaf(-3.0f * t, t, e);
-    }
-  }
-  return ex2_approx(e * kLog2e);
+  return pair_exp2<KERN>(Q, dx, dy, dz, a);
 }
 
 // Accumulate one Gaussian record r into this lane's sums (or count it).
@@ -130,6 +145,57 @@ __device__ __forceinline__ void eval_pair(const float* __restrict__ r, float px,
 #pragma unroll
     for (int c = 0; c < C; ++c) L[c] = fmaf(w, r[13 + c], L[c]);
     Z += w;
+  }
+}
+
+// Weight of a staged record r at (px, py, pz) without branches: 0 unless
+// Q <= k^2, else pair_exp2's weight, bit for bit.
+template <int KERN>
+__device__ __forceinline__ float staged_weight(const float* __restrict__ r, float px, float py,
+                                               float pz, const FwdArgs& a) {
+  const float dx = px - r[0], dy = py - r[1], dz = pz - r[2];
+  const float u0 = fmaf(r[4], dx, fmaf(r[5], dy, r[6] * dz));
+  const float u1 = fmaf(r[7], dx, fmaf(r[8], dy, r[9] * dz));
+  const float u2 = fmaf(r[10], dx, fmaf(r[11], dy, r[12] * dz));
+  const float Q = fmaf(u0, u0, fmaf(u1, u1, u2 * u2));
+  float e = Q * kNegHalfLog2e;
+  if (KERN == kKernFalloff) {
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float t = fmaf(d2, rsqrtf(d2), -a.r) * a.tscale;   // not used when d2 <= r^2
+    e = d2 > a.r2 ? fmaf(-t, t, e) : e;
+  }
+  return ex2_approx(Q <= a.cut2 ? e : -INFINITY);             // 2^-inf = +0
+}
+
+// Every staged record of the cooperative mode at this lane's hit point, four
+// at a time as straight-line code. A group may reach past nk (never past the
+// 32 staged slots): those slots hold zeros or earlier finite records, and
+// their weight is forced to 0, so the sums are those of the first nk in order.
+template <int C, int KERN, bool COUNT>
+__device__ __forceinline__ void eval_staged(const float* __restrict__ recs, int nk, float px,
+                                            float py, float pz, const FwdArgs& a, float (&L)[C],
+                                            float& Z, uint32_t& n_eval, uint32_t& n_inc) {
+  constexpr int RS = rec_stride(C);
+  if (COUNT || KERN == kKernDisk) {
+    for (int s = 0; s < nk; ++s) eval_pair<C, KERN, COUNT>(recs + s * RS, px, py, pz, a, L, Z,
+                                                           n_eval, n_inc);
+    return;
+  }
+  constexpr int kGroup = 4;
+  for (int s = 0; s < nk; s += kGroup) {
+    float w[kGroup];
+#pragma unroll
+    for (int j = 0; j < kGroup; ++j) {
+      const float wj = staged_weight<KERN>(recs + (s + j) * RS, px, py, pz, a);
+      w[j] = s + j < nk ? wj : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < kGroup; ++j) {
+      const float* r = recs + (s + j) * RS;
+#pragma unroll
+      for (int c = 0; c < C; ++c) L[c] = fmaf(w[j], r[13 + c], L[c]);
+      Z += w[j];
+    }
   }
 }
 
@@ -196,6 +262,8 @@ fwd_kernel(FwdArgs a) {
 
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   if (index_unusable(a.header)) return;
+  // the staged slots start finite: eval_staged reads whole groups of four
+  for (int i = lane; i < kWarp * RS; i += kWarp) s_rec[wib][i] = 0.0f;
   const int64_t n_act = a.header->n_active;
   const int64_t n_tiles = (a.m + kWarp - 1) / kWarp;
   // split tiles (heavy ones, when the index asks for it) come first as
@@ -378,9 +446,7 @@ fwd_kernel(FwdArgs a) {
             }
             __syncwarp();
             const int nk = __popc(kb);
-            if (active)
-              for (int s = 0; s < nk; ++s)
-                eval_pair<C, KERN, COUNT>(my_rec + s * RS, px, py, pz, a, L, Z, n_eval, n_inc);
+            if (active) eval_staged<C, KERN, COUNT>(my_rec, nk, px, py, pz, a, L, Z, n_eval, n_inc);
             __syncwarp();
             v = vn;
           }
@@ -693,6 +759,7 @@ cudaError_t launch_forward(const IndexDims& d, const IndexBuffers& b, const gpf_
   a.kde_scale = psi ? (float)(1.0 / (M_PI * (double)p.r_max * (double)p.r_max)) : 0.0f;
   a.cut = d.cutoff;
   a.cut2 = isinf(d.cutoff) ? INFINITY : d.cutoff * d.cutoff;
+  a.tscale = (float)((double)a.inv_rr * std::sqrt(3.0 * M_LOG2E));
   a.out = out;
   a.z = z;
   a.counts = counts;
