@@ -230,7 +230,15 @@ typedef struct gpf_grid_config {
                             kernel adds in part order (results still
                             deterministic; they differ from the unsplit sums
                             by summation order only)                         */
-  int32_t reserved2;     /* 0                                                */
+  int32_t tile_order;    /* order of the hit points inside each query-level
+                            cell, which shapes the forward's 32-point tiles:
+                            0 = hit point index order; b = 1 or 2 = by the
+                            Morton order of the 2^b x 2^b x 2^b sub-cells
+                            (level query_level - b), then index order, so
+                            that consecutive hit points form compact boxes.
+                            Needs b <= query_level and at most 32 key bits
+                            (3 b above the cell key). Results depend on it
+                            through summation order only.                    */
 } gpf_grid_config;
 #define GPF_MAX_TILE_PARTS 64
 #define GPF_MAX_SPLIT_UNITS 32768

@@ -65,7 +65,7 @@ class gpf_grid_config(ctypes.Structure):
                 ("hash_bits", c_i32), ("channels", c_i32), ("cutoff_sigma", c_f32), ("brute_force", c_i32),
                 ("coop_cells", c_i32), ("field_storage", c_i32), ("ball_radius", c_f32),
                 ("max_gaussians", c_i64), ("max_queries", c_i64), ("max_pairs", c_i64),
-                ("max_nb_pairs", c_i64), ("split_items", c_i32), ("reserved2", c_i32)]
+                ("max_nb_pairs", c_i64), ("split_items", c_i32), ("tile_order", c_i32)]
 
 
 class gpf_index_stats_t(ctypes.Structure):

@@ -212,6 +212,7 @@ class GridConfig:
     ball_radius: float = 0.0   # > 0: centre entries for GPF_NB_BALL_KNN queries
     max_nb_pairs: int = 0      # capacity of the GPF_NB_BALL_KNN backward's pairs
     split_items: int = 0       # > 0: split forward tiles of more estimated work
+    tile_order: int = 0        # hit points inside a query cell by 2^b sub-cells (b = 0..2)
 
     def c_struct(self) -> _abi.gpf_grid_config:
         return _abi.gpf_grid_config((ctypes.c_float * 3)(*self.origin), float(self.cell_size),
@@ -223,7 +224,7 @@ class GridConfig:
                                     float(self.ball_radius), int(self.max_gaussians),
                                     int(self.max_queries),
                                     int(self.max_pairs), int(self.max_nb_pairs),
-                                    int(self.split_items), 0)
+                                    int(self.split_items), int(self.tile_order))
 
 
 def grid_for_bounds(lo: Sequence[float], hi: Sequence[float], cell_size: float, channels: int,

@@ -327,14 +327,21 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
   if (cfg->max_gaussians >= kMaxSortN || cfg->max_queries >= kMaxSortN ||
       cfg->max_pairs >= kMaxSortN || cfg->max_nb_pairs >= kMaxSortN)
     return fail(GPF_ERR_INVALID_ARG, "capacities must be below 2^30");
-  if (cfg->split_items < 0 || cfg->reserved2 != 0)
-    return fail(GPF_ERR_INVALID_ARG, "split_items must be >= 0 and reserved2 0");
+  if (cfg->split_items < 0)
+    return fail(GPF_ERR_INVALID_ARG, "split_items must be >= 0");
+  if (cfg->tile_order < 0 || cfg->tile_order > 2 || cfg->tile_order > cfg->query_level)
+    return fail(GPF_ERR_INVALID_ARG, "tile_order = %d outside 0..min(2, query_level = %d)",
+                cfg->tile_order, cfg->query_level);
   if (cfg->max_nb_pairs > 0 && !(cfg->ball_radius > 0.0f))
     return fail(GPF_ERR_INVALID_ARG, "max_nb_pairs > 0 needs ball_radius > 0 (centre entries)");
   const uint64_t cells = (uint64_t)cfg->dims[0] * cfg->dims[1] * cfg->dims[2];
   if (cells > (1ull << 28))
     return fail(GPF_ERR_INVALID_ARG, "grid has %llu cells, more than 2^28",
                 (unsigned long long)cells);
+  if ((cells << (3 * cfg->tile_order)) >= (1ull << 32))
+    return fail(GPF_ERR_INVALID_ARG, "tile_order = %d: %llu cells leave no room for %d sub-cell "
+                "bits in a 32-bit sort key", cfg->tile_order, (unsigned long long)cells,
+                3 * cfg->tile_order);
   gpf_index* ix = new (std::nothrow) gpf_index();
   if (!ix) return fail(GPF_ERR_INVALID_ARG, "out of host memory");
   ix->cfg = *cfg;
@@ -389,9 +396,13 @@ gpf_status gpf_index_create(const gpf_grid_config* cfg, gpf_index** out) {
   d.grid.dy = cfg->dims[1];
   d.grid.dz = cfg->dims[2];
   d.grid.n_keys = (uint32_t)cells;
-  d.grid.key_inactive = (uint32_t)cells;
+  // sort keys of the hit points: the query-level cell key, then 3 b bits of
+  // the sub-cell Morton code (b = tile_order); inactive hit points sort last
+  d.grid.qsub = cfg->tile_order;
+  const int sub_bits = 3 * cfg->tile_order;
   int bits = 0;
-  while ((1ull << bits) <= cells) ++bits;
+  while ((1ull << bits) <= (cells << sub_bits)) ++bits;
+  d.grid.key_inactive = (uint32_t)(cells << sub_bits);
   d.grid.key_bits = bits;
   // the backward walks Gaussians ordered by a cell 16 x coarser than the query level
   d.grid.oshift = std::min(cfg->query_level + 4, kCoordBits);

@@ -131,7 +131,8 @@ struct Grid {
   int qlevel;              // K
   int dx, dy, dz;          // query-level dims
   uint32_t n_keys;         // dx * dy * dz
-  uint32_t key_inactive;   // = n_keys
+  int qsub;                // sub-cell bits per axis of the hit-point order (0..2)
+  uint32_t key_inactive;   // = n_keys << 3 qsub, after every active key
   int key_bits;            // bits of a query-level key including the inactive one
   int hash_bits;
   uint32_t n_buckets;      // 2^hash_bits

@@ -311,7 +311,8 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
                                   uint32_t* __restrict__ qcount, DeviceHeader* header) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool active = false, bad = false;
-  uint32_t k = grid.key_inactive;
+  uint32_t k = grid.key_inactive;  // sort key
+  uint32_t kc = 0u;                 // query-level cell key
   uint32_t c0[3] = {0u, 0u, 0u};   // level-0 cell of an active hit point
   if (i < m) {
     // hemisphere gate n . w_o > 0: the float32 sum when it is far enough
@@ -338,7 +339,19 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
       const uint32_t cy = coord0(x[m + i], grid.oy, grid.inv_cell0, grid.max0y);
       const uint32_t cz = coord0(x[2 * m + i], grid.oz, grid.inv_cell0, grid.max0z);
       const int K = grid.qlevel;
-      k = qkey_of(grid, cx >> K, cy >> K, cz >> K);
+      kc = qkey_of(grid, cx >> K, cy >> K, cz >> K);
+      k = kc;
+      if (grid.qsub > 0) {
+        // then the Morton code of the sub-cell on level K - qsub (x in the
+        // lowest bit of each triple), so that a run of 32 hit points covers
+        // a compact part of its cell
+        const int s = K - grid.qsub;
+        uint32_t mort = 0u;
+        for (int b = grid.qsub - 1; b >= 0; --b)
+          mort = (mort << 3) | (((cz >> (s + b)) & 1u) << 2) | (((cy >> (s + b)) & 1u) << 1) |
+                 ((cx >> (s + b)) & 1u);
+        k = (kc << (3 * grid.qsub)) | mort;
+      }
       c0[0] = cx; c0[1] = cy; c0[2] = cz;
     }
     key[i] = k;
@@ -371,8 +384,8 @@ __global__ void query_keys_kernel(Grid grid, const float* __restrict__ x,
   }
   // per-cell counts: one atomic per distinct cell of the warp (neighbouring
   // pixels share query cells)
-  const uint32_t peers = __match_any_sync(kFullMask, active ? k : 0xffffffffu);
-  if (active && (peers & lanemask_lt()) == 0) atomicAdd(&qcount[k], (uint32_t)__popc(peers));
+  const uint32_t peers = __match_any_sync(kFullMask, active ? kc : 0xffffffffu);
+  if (active && (peers & lanemask_lt()) == 0) atomicAdd(&qcount[kc], (uint32_t)__popc(peers));
   __shared__ uint32_t s_cnt[kBlockWarps][4];
   uint32_t v[4] = {active ? 1u : 0u, bad ? 1u : 0u, 0u, 0u};
   block_counts(v, s_cnt);

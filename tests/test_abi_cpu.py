@@ -69,7 +69,9 @@ def _cfg(**kw):
                                  dict(coop_cells=-1), dict(coop_cells=9), dict(field_storage=3),
                                  dict(ball_radius=-1.0), dict(ball_radius=math.inf),
                                  dict(max_pairs=1 << 30), dict(max_queries=1 << 30),
-                                 dict(max_gaussians=1 << 30)])
+                                 dict(max_gaussians=1 << 30), dict(tile_order=-1),
+                                 dict(tile_order=3), dict(tile_order=1),
+                                 dict(tile_order=2, query_level=1)])
 def test_index_create_rejects_bad_configs(lib, bad):
     h = ctypes.c_void_p()
     cfg = _cfg(**bad)

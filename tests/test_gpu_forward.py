@@ -8,7 +8,8 @@ import pytest
 import oracle
 import synth
 from golden_util import load_examples
-from gpu_helpers import (FWD_TOL, INF, fwd_rel_err, gpu_fwd, oracle_fwd, sample_active)
+from gpu_helpers import (FWD_TOL, GRAD_TOL, INF, fwd_rel_err, gpu_fwd, oracle_fwd,
+                         sample_active)
 
 pytestmark = pytest.mark.gpu
 
@@ -269,4 +270,45 @@ def test_split_tiles_equal_unsplit_and_the_oracle(gpf, mode):
     sel = sample_active(qnp, 400, seed=16)
     ref = oracle_fwd(fnp, qnp, mode, 0.02, 3.0, sel)
     err, zero_ok = fwd_rel_err(outs[64][0][:, sel], ref)
+    assert err < FWD_TOL and zero_ok, err
+
+
+def test_tile_order_changes_summation_order_only(gpf):
+    """Hit points ordered inside their query cells by 2^b sub-cells (b = 1, 2)
+    instead of by index: the same pairs (included pair counts equal; the
+    candidates the tile boxes let through differ), outputs and
+    gradients equal to the index order's up to summation order, and parity
+    with the oracle."""
+    import dataclasses
+
+    import torch
+    from paper_2512_12459_gb300.setup_index import make_index
+    fnp, qnp = _caustic(40000, seed=21, w=160, h=128)
+    # anisotropic scales, so that the rotation gradient is not rounding noise
+    rng = np.random.default_rng(21)
+    fnp.logscale = (fnp.logscale + rng.normal(0.0, 0.3, fnp.logscale.shape)).astype(np.float32)
+    field, queries = gpf.Field.from_numpy(fnp), gpf.Queries.from_numpy(qnp)
+    base = make_index(field, queries, query_cell=0.05, split_items=256)
+    orders = [b for b in (0, 1, 2) if b <= base.grid.query_level]
+    assert len(orders) >= 2
+    gout = torch.as_tensor(rng.standard_normal((3, queries.m)).astype(np.float32), device="cuda")
+    res = {}
+    for b in orders:
+        idx = make_index(field, queries, grid=dataclasses.replace(base.grid, tile_order=b))
+        idx.build(field, queries)
+        o, z = gpf.gpf_radiance_fwd(idx, field, queries, gpf.GPF_SUM, r_max=0.02)
+        g = gpf.gpf_radiance_bwd(idx, field, queries, gout, o, z, gpf.GPF_SUM, r_max=0.02)
+        torch.cuda.synchronize()
+        res[b] = (o.cpu().numpy().astype(np.float64), gpf.gpf_count_pairs(idx, field, queries),
+                  [t.cpu().numpy().astype(np.float64) for t in g.tensors()])
+    o0, c0, g0 = res[0]
+    for b in orders[1:]:
+        o, c, g = res[b]
+        assert c["included"] == c0["included"]
+        np.testing.assert_allclose(o, o0, rtol=2e-6, atol=1e-30)
+        for t, t0 in zip(g, g0):
+            assert np.linalg.norm(t - t0) <= GRAD_TOL * np.linalg.norm(t0)
+    sel = sample_active(qnp, 400, seed=22)
+    ref = oracle_fwd(fnp, qnp, oracle.GPF_SUM, 0.02, 3.0, sel)
+    err, zero_ok = fwd_rel_err(res[orders[-1]][0][:, sel], ref)
     assert err < FWD_TOL and zero_ok, err
