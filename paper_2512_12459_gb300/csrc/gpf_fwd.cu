@@ -80,12 +80,18 @@ __device__ __forceinline__ float warp_max(float v) {
 constexpr int kKernGauss = 0, kKernFalloff = 1, kKernDisk = 2;
 constexpr float kNegHalfLog2e = -0.72134752044448170368f;   // -log2(e) / 2
 
+// |d| from d2 = |d|^2 > 0: one reciprocal square root and one Newton step
+// on the square root (residual d2 - s^2 by a fused multiply-add), which
+// leaves about 1 ulp of relative error, as a correctly rounded square root
+// would within an ulp, without its special-case branch.
+__device__ __forceinline__ float dist_of(float d2) {
+  const float y = rsqrtf(d2);
+  const float s = d2 * y;
+  return fmaf(0.5f * y, fmaf(-s, s, d2), s);
+}
+
 // w = exp(-Q/2) psi(|d|) of an included pair as 2^-(Q log2(e)/2 + t'^2), with
 // t' = sqrt(3 log2 e) (|d| - r)/r beyond the falloff radius r (zero within).
-// |d| comes from one reciprocal square root (relative error ~2^-22), which
-// moves the exponent by about 2 t'(t' + r tscale) 2^-22: below 2e-6 relative
-// in w for t' <= 2, and terms with larger t' carry less than 2^-4 of their
-// Gaussian factor.
 template <int KERN>
 __device__ __forceinline__ float pair_exp2(float Q, float dx, float dy, float dz,
                                            const FwdArgs& a) {
@@ -93,8 +99,7 @@ __device__ __forceinline__ float pair_exp2(float Q, float dx, float dy, float dz
   if (KERN == kKernFalloff) {
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     if (d2 > a.r2) {
-      // |d| = d2 rsqrt(d2), as staged_weight takes it (same w bit for bit)
-      const float t = fmaf(d2, rsqrtf(d2), -a.r) * a.tscale;
+      const float t = (dist_of(d2) - a.r) * a.tscale;   // as staged_weight: same w bit for bit
       e = fmaf(-t, t, e);
     }
   }
@@ -161,7 +166,7 @@ __device__ __forceinline__ float staged_weight(const float* __restrict__ r, floa
   float e = Q * kNegHalfLog2e;
   if (KERN == kKernFalloff) {
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float t = fmaf(d2, rsqrtf(d2), -a.r) * a.tscale;   // not used when d2 <= r^2
+    const float t = (dist_of(d2) - a.r) * a.tscale;   // not used when d2 <= r^2
     e = d2 > a.r2 ? fmaf(-t, t, e) : e;
   }
   return ex2_approx(Q <= a.cut2 ? e : -INFINITY);             // 2^-inf = +0
