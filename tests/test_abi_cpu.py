@@ -254,3 +254,26 @@ def test_box_cell_quotients_are_exact_in_float32():
                     r = c - dz * nxy
                     dy = int(f(f(r) + f(0.5)) * inx)
                     assert (dz, dy, r - dy * nx) == (c // nxy, (c % nxy) // nx, c % nx)
+
+
+def test_falloff_distance_newton_step_is_within_an_ulp():
+    """The forward's |d| (dist_of in gpf_fwd.cu): s = d2 y with y a reciprocal
+    square root of relative error up to 2^-22, then s + (y/2)(d2 - s^2) with
+    the residual and the update each rounded once (fused multiply-adds).
+    Emulated in float32 with exact float64 intermediates, it stays within one
+    ulp of the correctly rounded square root and within u = 2^-24 relative
+    of the exact one, for rsqrt errors at both ends of the range and random
+    ones, which is the <= 2u the forward's exponent bound assumes."""
+    rng = np.random.default_rng(7)
+    d2 = (10.0 ** rng.uniform(-10, 3, 100000)).astype(np.float32)
+    d64 = d2.astype(np.float64)
+    root = np.sqrt(d64)
+    for eps in (-2.0 ** -22, 2.0 ** -22, rng.uniform(-2.0 ** -22, 2.0 ** -22, d2.size)):
+        y = (1.0 / root * (1.0 + eps)).astype(np.float32)
+        s = (d64 * y).astype(np.float32)
+        h = (np.float32(0.5) * y).astype(np.float32)
+        res = (d64 - s.astype(np.float64) ** 2).astype(np.float32)
+        s1 = (h.astype(np.float64) * res.astype(np.float64) + s.astype(np.float64)).astype(np.float32)
+        rn = root.astype(np.float32)
+        assert np.all(np.abs(s1.astype(np.float64) - rn) <= np.spacing(rn))
+        assert np.max(np.abs(s1.astype(np.float64) - root) / root) <= 2.0 ** -24 * 1.001
