@@ -92,3 +92,49 @@ def test_planned_grid_keeps_index_order_and_the_struct_carries_tile_order():
     assert g.tile_order == 0 and g.c_struct().tile_order == 0
     g2 = dataclasses.replace(g, tile_order=min(2, g.query_level))
     assert g2.c_struct().tile_order == min(2, g.query_level)
+
+
+def test_autotune_search_order_and_choice(monkeypatch):
+    """The autotuner's search on a synthetic cost (no GPU): one knob at a
+    time in the documented order, then the query cell again with the other
+    knobs settled; every distinct setting is timed once; the result is the
+    cheapest setting it visited."""
+    from paper_2512_12459_gb300 import setup_index
+
+    def cost(k):
+        # the best query cell depends on the span, so the second pass matters
+        best_cell = 0.02 if k["max_span"] == 3 else 0.04
+        return (abs(math.log2(k["query_cell"] / best_cell)) + 2.0 * (k["max_span"] != 3)
+                + 0.1 * (k["coop_cells"] != 8) + 0.05 * (k["split_items"] != 4096))
+
+    class _Idx:
+        def __init__(self, knobs):
+            self.grid = dict(knobs)
+
+    calls = []
+
+    def fake_make_index(field, queries, cutoff_sigma=3.0, headroom=1.25, query_cell=None,
+                        max_span=4, coop_cells=0, split_items=None, **kw):
+        return _Idx(dict(query_cell=query_cell, max_span=max_span, coop_cells=coop_cells,
+                         split_items=split_items))
+
+    def fake_time_step(index, field, queries, mode, r_max, repeats, backward):
+        calls.append(dict(index.grid))
+        return cost(index.grid)
+
+    monkeypatch.setattr(setup_index, "make_index", fake_make_index)
+    monkeypatch.setattr(setup_index, "time_step", fake_time_step)
+    grid, report = setup_index.autotune(None, None, query_cells=(0.01, 0.02, 0.04),
+                                        max_spans=(3, 4), coop_options=(4, 8),
+                                        split_options=(0, 4096))
+    assert grid == {"query_cell": 0.02, "max_span": 3, "coop_cells": 8, "split_items": 4096}
+    # each distinct setting timed once, in the order reported
+    keys = [tuple(sorted(c.items())) for c in calls]
+    assert len(keys) == len(set(keys)) == len(report)
+    assert [k for k, _ in report] == calls
+    # first the query cell (3 settings, at the initial span 4: 0.04 wins),
+    # then span, coop, split, then the cell again (at span 3: 0.02 wins)
+    assert [c["query_cell"] for c in calls[:3]] == [0.01, 0.02, 0.04]
+    assert all(c["max_span"] == 4 for c in calls[:3])
+    assert calls[3]["query_cell"] == 0.04
+    assert min(ms for _, ms in report) == cost(grid)
